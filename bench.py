@@ -1,0 +1,380 @@
+"""Benchmark of the matrix-free ghost-penalty apply y = G x on GB300.
+
+Workload: 3D ball of radius 0.7 (seeded centre offset) in a 64^3 Cartesian mesh
+on [-1,1]^3, FE_Q(3) on Gauss-Lobatto points, gamma = 0.5 for every order;
+x ~ U[-1,1] on the active DoFs.  One step = one y = G x over all ghost faces.
+
+Metric: GDoF/s = active DoFs / apply time (the paper's throughput convention,
+Sec. 3.1), whole job over all ranks.  The inputs (about 12 MB) fit in L2, so
+a 512 MB buffer is written between timed steps to flush it.
+
+Arms
+  default            the CUDA path through the C ABI (FP64 headline; FP32 beside it)
+  --impl reference   the CPU FP64 oracle timed on the host cores (bounded sample)
+
+Multi-GPU: one independent replica per rank (the single-problem apply does not
+shard); value = DoFs of all ranks / max over ranks of the device time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ghost-penalty GDoF/s & %HBM roofline, FP64 vs FP32/batched at stated error"
+WORKLOAD = "ghost-penalty y=Gx, 3D ball r=0.7 in 64^3 cells on [-1,1]^3, FE_Q(3) Gauss-Lobatto, gamma=0.5"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 FMA issue rates of a GB300 SM (flop per clock, FMA = 2) at the 2070 MHz maximum SM clock
+FP64_FLOP_PER_CLK_SM = 4
+FP32_FLOP_PER_CLK_SM = 256
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm --
+
+def _flops_jump(d, k, nf):
+    L = (k + 1) ** (d - 1)
+    # normal jumps: k dot products of length 2k+1 per line; tangential masses: (d-1) passes of
+    # (k+1)x(k+1) on k*(k+1)^(d-2) lines per tangential direction
+    return 2.0 * nf * (k * (2 * k + 1) * L + (d - 1) * k * L * (k + 1))
+
+
+def _flops_paper(d, k, nf):
+    return 2.0 * nf * ((k + 1) ** (d - 1) * (2 * k + 1) ** 2 + (d - 1) * (k + 1) ** d * (2 * k + 1))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_00246_gb300 import build as B
+    B.build()
+    from paper_2503_00246_gb300 import gp, workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pr = W.ball_3d()
+    forms = {}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    clocks = Clocks(local)
+
+    results = {}
+    for prec in ([gp.GP_FP64, gp.GP_FP32] if args.precision == "both" else
+                 [gp.GP_FP64 if args.precision == "fp64" else gp.GP_FP32]):
+        ctx = gp.setup_problem(pr, precision=prec, device=local)
+        w = 8 if prec == gp.GP_FP64 else 4
+        tdt = torch.float64 if prec == gp.GP_FP64 else torch.float32
+        x_np = W.x_vectors(pr, ctx.n_active)[0]
+        x = torch.tensor(x_np, dtype=tdt, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            gp.gp_apply(ctx, x, y)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        gp.gp_profile_enable(ctx, True)
+        if prec == gp.GP_FP64:
+            clocks.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))                 # evict x, y and the tables from L2
+            ev[i][0].record(stream)
+            gp.gp_apply(ctx, x, y)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if ws > 1:
+            dist.barrier()
+        ck = clocks.stop() if prec == gp.GP_FP64 else None
+        ms_jump, ms_lift, calls = gp.gp_profile_read(ctx)
+        gp.gp_profile_enable(ctx, False)
+        t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps   # ms
+        t_max = t_step
+        if ws > 1:
+            tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_max = float(tt.item())
+        d, k, nf = pr.dim, pr.degree, ctx.n_faces
+        jump_ms = ms_jump / calls
+        lift_ms = ms_lift / calls
+        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+        xh = torch.tensor(x_np, dtype=tdt).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for _ in range(max(3, args.warmup // 4)):
+            gp.gp_apply_host(ctx, xh, yh, stream)
+        ne = max(10, args.steps // 10)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ne):
+            gp.gp_apply_host(ctx, xh, yh, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = e0.elapsed_time(e1) / ne
+        # accuracy of this very output against the oracle (outside every timed region)
+        err = None
+        if args.check:
+            from oracle.ghost_penalty import Oracle
+            o = Oracle(pr)
+            ref = o.apply(x_np if prec == gp.GP_FP64 else x_np.astype(np.float32).astype(np.float64))
+            err = float(np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+        flop_jump = _flops_jump(d, k, nf)
+        if prec == gp.GP_FP64:
+            roof = {"bound": "alu", "kernel": "jump_kernel<3,3,double>", "achieved": flop_jump / (jump_ms * 1e-3) / 1e12,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz"}
+        else:
+            roof = {"bound": "alu", "kernel": "jump_kernel<3,3,float>", "achieved": flop_jump / (jump_ms * 1e-3) / 1e12,
+                    "peak": fp32_peak, "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FFMA/clk x 2070 MHz"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        alg_bytes = w * (ctx.n_touched + ctx.n_active)
+        results[prec] = {
+            "value": ws * ctx.n_active / (t_max * 1e-3) / 1e9,
+            "ms_per_step": t_max,
+            "wall_ms_per_step": wall * 1e3 / args.steps,
+            "kernel_ms": {"jump": jump_ms, "lift": lift_ms},
+            "apply_hbm_gbs": alg_bytes / (t_step * 1e-3) / 1e9,
+            "apply_hbm_frac": alg_bytes / (t_step * 1e-3) / 1e9 / hbm,
+            "lift_hbm_gbs": w * ctx.n_active / (lift_ms * 1e-3) / 1e9,
+            "roofline": roof,
+            "e2e_ms": t_e2e,
+            "e2e_value": ws * ctx.n_active / (t_e2e * 1e-3) / 1e9,
+            "h2d": w * ctx.n_active, "d2h": w * ctx.n_active,
+            "rel_err_vs_oracle": err,
+            "clocks": ck,
+            "n_active": ctx.n_active, "n_faces": nf, "n_touched": ctx.n_touched,
+            "paper_flops_per_step": _flops_paper(d, k, nf),
+        }
+        ctx.close()
+
+    head = gp.GP_FP64 if gp.GP_FP64 in results else gp.GP_FP32
+    r = results[head]
+    line = {
+        "metric": METRIC,
+        "value": r["value"],
+        "unit": "GDoF/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if head == gp.GP_FP64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_cells": 64 ** 3, "degree": 3, "n_active_dofs": r["n_active"],
+                   "ghost_faces": r["n_faces"], "touched_dofs": r["n_touched"],
+                   "l2": "512 MB buffer written between timed steps (inputs < L2)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": r["roofline"],
+        "e2e": {"value": r["e2e_value"], "unit": "GDoF/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": 2 * args.steps,
+        "clocks": r["clocks"],
+        "apply_hbm": {"achieved": r["apply_hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": r["apply_hbm_frac"],
+                      "peak_source": peak_src},
+        "kernel_ms": r["kernel_ms"],
+        "rel_err_vs_oracle": r["rel_err_vs_oracle"],
+    }
+    if gp.GP_FP32 in results and head != gp.GP_FP32:
+        f = results[gp.GP_FP32]
+        line["fp32"] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
+                                             "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value")}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU arm --
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(seconds: float):
+    """The oracle, as it stands, on the host cores: full applies for about `seconds`."""
+    from oracle.ghost_penalty import Oracle
+    from paper_2503_00246_gb300 import workloads as W
+    pr = W.ball_3d()
+    o = Oracle(pr)
+    x = W.x_vectors(pr, o.n_active)[0]
+    for a in range(pr.dim):
+        o.patch_index(a)
+        o.A(a)
+    o.apply(x)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.apply(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and reps >= 3:
+            break
+    t = el / reps
+    return {"value": o.n_active / t / 1e9, "unit": "GDoF/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{reps} full applies of the 64^3 k=3 workload ({o.n_faces} faces, explicit "
+                      f"{(2 * 3 + 1) * 16}x{(2 * 3 + 1) * 16} face matrices, numpy FP64), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from oracle.ghost_penalty import Oracle
+    from paper_2503_00246_gb300 import workloads as W
+    pr = W.ball_3d()
+    o = Oracle(pr)
+    x = W.x_vectors(pr, o.n_active)[0]
+    for a in range(pr.dim):
+        o.patch_index(a)
+        o.A(a)
+    t0 = time.perf_counter()
+    o.apply(x)
+    t_full = time.perf_counter() - t0
+    # each step is a bounded sample: a fixed fraction of the faces, so the whole run takes ~60 s
+    budget = 60.0
+    frac = min(1.0, budget / max(1, args.steps + args.warmup) / t_full)
+    sub = {}
+    for a in range(pr.dim):
+        nfa = o.faces[a].shape[0]
+        sub[a] = o.patch_index(a)[: max(1, int(math.ceil(frac * nfa)))]
+    nsub = sum(v.shape[0] for v in sub.values())
+    frac_eff = nsub / o.n_faces
+
+    def step():
+        y = np.zeros(o.n_active)
+        for a, idx in sub.items():
+            yf = x[idx] @ o.A(a).T
+            y += np.bincount(idx.ravel(), weights=yf.ravel(), minlength=o.n_active)
+        return y
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t = (time.perf_counter() - t0) / args.steps
+    value = frac_eff * o.n_active / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_fraction_of_faces": frac_eff},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": _cores(), "kind": "oracle",
+                             "sample": f"{nsub} of {o.n_faces} faces per step (explicit face matrices, numpy FP64); "
+                                       f"DoF throughput scaled by that fraction"},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "fp32", "both"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", dest="check", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * gp.h -- C ABI of the GB300 matrix-free ghost-penalty operator.
+ *
+ * Operation (Sec. 2.2, ghost penalty g_h; Sec. 2.4, tensor-product face
+ * matrix; Sec. 2.5.1, face loop of the operator application):
+ *
+ *   y = G x,   G = sum_{F in F_h} sum_{j=1..k} c_j h^{2j-1} (integral over F of
+ *                  [d_n^j u] [d_n^j v]),
+ *
+ * on an axis-aligned Cartesian mesh of 2D squares / 3D cubes of edge h with
+ * continuous FE_Q(k) elements on Gauss-Lobatto points, for the faces F_h
+ * between two active cells of which at least one is cut by the level set
+ * (phi > 0 inside).  Per face, the matrix factorises as
+ * h^{d-2} (M^ x ... x G^) with the 1D reference mass M^ along the tangential
+ * directions and the 1D penalty G^ = sum_j c_j g_j g_j^T along the normal
+ * (Eq. of G_F = M^h x M^h x G^h_k and its h-scaling).
+ *
+ * Conventions shared by every call
+ *   - Vectors live on the active DoFs: the FE_Q lattice nodes (n*k+1 per
+ *     axis) that belong to at least one active cell, numbered
+ *     lexicographically with x fastest, then compacted
+ *     (gp_active_dof_coords returns their coordinates).
+ *   - x and y are caller-owned DEVICE pointers to contiguous arrays of
+ *     n_active elements (double for GP_FP64, float for GP_FP32), on the
+ *     device that was current during gp_setup.  x and y must not alias.
+ *   - stream is a cudaStream_t (0 = legacy default stream).  Calls only
+ *     enqueue work; they do not synchronise.
+ *   - Every call returns a gp_status and never aborts.  On error,
+ *     gp_last_error() gives a message for that context (or for the calling
+ *     thread when ctx is NULL).
+ *   - A context is not thread-safe: one host thread (or external locking)
+ *     per context.  Concurrent applies on different streams that share a
+ *     context race on its scratch buffer.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_ctx gp_ctx;
+
+typedef enum {
+  GP_OK = 0,
+  GP_EINVAL = 1,        /* bad argument (null pointer, size, degree, mesh) */
+  GP_ENOMEM = 2,        /* host or device allocation failed */
+  GP_ECUDA = 3,         /* a CUDA runtime call failed (message has the error) */
+  GP_EDEVICE = 4,       /* no usable CUDA device, or context built host-only */
+  GP_EUNSUPPORTED = 5   /* valid request outside this build (e.g. k > 8) */
+} gp_status;
+
+enum { GP_FP64 = 0, GP_FP32 = 1 };
+
+/* level-set kinds; phi > 0 inside the domain (Sec. 2) */
+enum {
+  GP_LS_BALLS = 1,      /* union of balls, phi = max_b (r_b - |x - c_b|) */
+  GP_LS_GYROID = 2,     /* phi = sin x cos y + sin y cos z + sin z cos x - iso (3D) */
+  GP_LS_CALLBACK = 3,   /* user function, sampled with a Lipschitz margin */
+  GP_LS_CONST = 4       /* phi = value everywhere */
+};
+
+typedef double (*gp_levelset_fn)(const double* x, void* user);
+
+/* Uniform Cartesian mesh of n[a] cells on [lo[a], hi[a]], a < dim; the cell
+ * edge h = (hi[a]-lo[a])/n[a] must be the same on every axis (Sec. 2: squares
+ * or cubes of size h). */
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int n[3];
+  double lo[3];
+  double hi[3];
+} gp_mesh;
+
+typedef struct {
+  int kind;                 /* GP_LS_* */
+  int nballs;               /* GP_LS_BALLS */
+  const double* centers;    /* nballs x 3 (z ignored in 2D), host memory */
+  const double* radii;      /* nballs, host memory */
+  double iso;               /* GP_LS_GYROID */
+  double value;             /* GP_LS_CONST */
+  gp_levelset_fn fn;        /* GP_LS_CALLBACK */
+  void* user;
+  double lipschitz;         /* GP_LS_CALLBACK: bound on |grad phi| */
+  int samples;              /* sub-intervals per cell edge for sampled kinds (<=0: 4) */
+} gp_levelset;
+
+typedef struct {
+  int degree;               /* k, 1 <= k <= 8 */
+  int nweights;             /* 0, or k: per-order weights c_1..c_k */
+  const double* weights;    /* NULL -> c_j = gamma for every order j */
+  double gamma;             /* default weight */
+  int precision;            /* GP_FP64 or GP_FP32 */
+  int all_faces;            /* 1: penalise every interior face of the active mesh */
+  int device;               /* CUDA device ordinal; -1 = build the host plan only */
+} gp_opts;
+
+/* Classify cells, collect the ghost faces, number the active DoFs, build the
+ * 1D matrices in FP64 and upload the face tables (Sec. 2 / Sec. 2.4 / Sec. 2.6).
+ * mesh, ls and opts are read during the call only.  *out receives a new
+ * context owned by the caller (release with gp_destroy). */
+gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
+                   gp_ctx** out);
+
+/* Release a context and its device memory.  NULL is ignored. */
+void gp_destroy(gp_ctx* ctx);
+
+/* Sizes: active DoFs, ghost faces, DoFs touched by some ghost face, and
+ * number of cells in each class (outside, cut, inside). */
+gp_status gp_num_active_dofs(const gp_ctx* ctx, int64_t* n);
+gp_status gp_num_ghost_faces(const gp_ctx* ctx, int64_t* nf);
+gp_status gp_num_touched_dofs(const gp_ctx* ctx, int64_t* n);
+gp_status gp_cell_counts(const gp_ctx* ctx, int64_t counts[3]);
+
+/* Host copies of the plan, for checks.  Caller-owned host buffers:
+ *   xyz   n_active * dim doubles, coordinates of the active DoFs in order;
+ *   axis / cell  nf entries: normal axis and lexicographic (x fastest)
+ *          index of the lower cell of every ghost face, in face order;
+ *   cls   n_cells int8: 0 outside, 1 cut, 2 inside (lexicographic). */
+gp_status gp_active_dof_coords(const gp_ctx* ctx, double* xyz);
+gp_status gp_ghost_faces(const gp_ctx* ctx, int32_t* axis, int64_t* cell);
+gp_status gp_cell_classes(const gp_ctx* ctx, int8_t* cls);
+
+/* The FP64 1D reference matrices of this context (Sec. 2.4, M^1 and G^1_k):
+ *   mass  (k+1)^2 doubles, M^[a][b] = integral_0^1 phi_a phi_b;
+ *   jumps k*(2k+1) doubles, g_j[b] = jump of the j-th derivative of patch
+ *         basis function b across the face of the patch [0,1] u [1,2];
+ *   scale k doubles, s_j = c_j h^{d-2} (the one FP64 factor per order). */
+gp_status gp_reference_1d(const gp_ctx* ctx, double* mass, double* jumps, double* scale);
+
+/* y = G x (y is overwritten on every active DoF). */
+gp_status gp_apply(gp_ctx* ctx, const void* x, void* y, void* stream);
+
+/* y += G x (only DoFs touched by a ghost face are read and written). */
+gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream);
+
+/* End-to-end form with HOST buffers: copies x (n_active elements of the
+ * context's precision) to the device, applies G, copies y back and waits
+ * for completion.  Uses device buffers owned by the context. */
+gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* stream);
+
+/* Several independent problems, nrhs right-hand sides each:
+ * x[p] and y[p] point to nrhs contiguous vectors of n_active(p) elements
+ * (layout [nrhs][n_active]).  All contexts must share one precision and
+ * device.  y[p] is overwritten. */
+gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs,
+                           const void* const* x, void* const* y, void* stream);
+
+/* Kernel tracing.  While enabled, every apply on ctx records CUDA events on
+ * its stream before the jump kernel, between the two kernels and after the
+ * lift kernel (Sec. 3.1 times each component of the operator separately).
+ * gp_profile_read waits for the recorded events and returns the summed
+ * device time of each kernel in milliseconds (ms[0] jump, ms[1] lift) and the
+ * number of traced applies since the last enable; enabling again resets. */
+gp_status gp_profile_enable(gp_ctx* ctx, int enable);
+gp_status gp_profile_read(gp_ctx* ctx, double ms[2], int64_t* calls);
+
+/* Last error message of ctx (or of the calling thread when ctx is NULL). */
+const char* gp_last_error(const gp_ctx* ctx);
+
+/* Library version string. */
+const char* gp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

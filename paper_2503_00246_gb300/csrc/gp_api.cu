@@ -1,0 +1,355 @@
+// C ABI of the ghost-penalty operator (declarations and contracts in gp.h).
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gp.h"
+#include "gp_launch.h"
+#include "gp_plan.h"
+
+struct gp_ctx {
+  gp::Plan plan;
+  int device = -1;
+  bool on_device = false;
+  size_t elem = 8;
+  int32_t* d_rowtab = nullptr;
+  int32_t* d_fcell = nullptr;
+  int32_t* d_face_of = nullptr;
+  int4* d_segs = nullptr;
+  int2* d_tiles = nullptr;
+  void* d_tp = nullptr;          // per-face scaled jumps (scratch)
+  void* d_xh = nullptr;          // gp_apply_host staging
+  void* d_yh = nullptr;
+  std::string err;
+  // tracing: one event triple per traced apply
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  int64_t nprof = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+gp_status fail(const gp_ctx* c, gp_status s, const std::string& m) {
+  if (c) const_cast<gp_ctx*>(c)->err = m;
+  else g_err = m;
+  return s;
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_device(gp_ctx* c) {
+  void* ptrs[] = {c->d_rowtab, c->d_fcell, c->d_face_of, c->d_segs, c->d_tiles,
+                  c->d_tp, c->d_xh, c->d_yh};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->d_rowtab = c->d_fcell = c->d_face_of = nullptr;
+  c->d_segs = nullptr;
+  c->d_tiles = nullptr;
+  c->d_tp = c->d_xh = c->d_yh = nullptr;
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+}
+
+#define GP_CUDA(ctx, call)                                                            \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st) {
+  const gp::Plan& p = c->plan;
+  gp::ApplyArgs a;
+  a.dim = p.dim;
+  a.k = p.k;
+  a.x = x;
+  a.y = y;
+  a.tp = c->d_tp;
+  a.add = add;
+  a.rowtab = c->d_rowtab;
+  a.fcell = c->d_fcell;
+  for (int i = 0; i < 4; ++i) a.fstart[i] = p.fstart[i];
+  a.la.segs = c->d_segs;
+  a.la.tiles = c->d_tiles;
+  a.la.face_of = c->d_face_of;
+  a.la.n = p.n;
+  a.la.nl = p.nl;
+  a.la.ncell = p.ncell;
+  a.ntiles = add ? p.ntiles_touched : p.ntiles_all;
+  a.g = p.jumps.data();
+  a.m = p.mass.data();
+  a.s = p.scale.data();
+  cudaEvent_t* ev = nullptr;
+  if (c->prof) {
+    const size_t need = 3 * (size_t)(c->nprof + 1);
+    while (c->ev.size() < need) {
+      cudaEvent_t e;
+      GP_CUDA(c, cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+    ev = &c->ev[3 * c->nprof];
+    c->nprof++;
+  }
+  a.ev = ev;
+  cudaError_t e;
+  if (p.precision == GP_FP64)
+    e = p.dim == 2 ? gp::apply_f64_d2(a, st) : gp::apply_f64_d3(a, st);
+  else
+    e = p.dim == 2 ? gp::apply_f32_d2(a, st) : gp::apply_f32_d3(a, st);
+  if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return GP_OK;
+}
+
+gp_status check_apply(const gp_ctx* c, const void* x, const void* y) {
+  if (!c) return fail(nullptr, GP_EINVAL, "null context");
+  if (!c->on_device) return fail(c, GP_EDEVICE, "context was built host-only (device = -1)");
+  if (c->plan.n_active > 0 && (!x || !y)) return fail(c, GP_EINVAL, "null x or y");
+  if (x == y && x != nullptr) return fail(c, GP_EINVAL, "x and y must not alias");
+  return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gp_version(void) { return "gp-gb300 0.1 (sm_103a)"; }
+
+const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, gp_ctx** out) {
+  if (!out) return fail(nullptr, GP_EINVAL, "null output pointer");
+  *out = nullptr;
+  gp_ctx* c = nullptr;
+  try {
+    c = new gp_ctx();
+    std::string err;
+    gp_status s = gp::build_plan(mesh, ls, opts, c->plan, err);
+    if (s != GP_OK) {
+      delete c;
+      return fail(nullptr, s, err);
+    }
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return fail(nullptr, GP_ENOMEM, "host allocation failed while building the plan");
+  }
+  c->elem = c->plan.precision == GP_FP64 ? 8 : 4;
+  c->device = opts->device;
+  if (opts->device >= 0) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      delete c;
+      return fail(nullptr, GP_EDEVICE, "no CUDA device available");
+    }
+    if (opts->device >= ndev) {
+      delete c;
+      return fail(nullptr, GP_EINVAL, "device ordinal out of range");
+    }
+    DeviceGuard g(opts->device);
+    cudaError_t e = g.ok ? cudaSuccess : cudaErrorInvalidDevice;
+    const gp::Plan& p = c->plan;
+    std::vector<int4> segs(p.segs.size() / 4);
+    std::memcpy(segs.data(), p.segs.data(), p.segs.size() * sizeof(int32_t));
+    std::vector<int2> tiles(p.tiles.size() / 2);
+    std::memcpy(tiles.data(), p.tiles.data(), p.tiles.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = upload(&c->d_rowtab, p.rowtab);
+    if (e == cudaSuccess) e = upload(&c->d_fcell, p.face_inv);
+    if (e == cudaSuccess) e = upload(&c->d_face_of, p.face_of);
+    if (e == cudaSuccess) e = upload(&c->d_segs, segs);
+    if (e == cudaSuccess) e = upload(&c->d_tiles, tiles);
+    const size_t tp_bytes = (size_t)p.num_faces() * p.L * p.k * c->elem;
+    if (e == cudaSuccess && tp_bytes > 0) e = cudaMalloc(&c->d_tp, tp_bytes);
+    if (e != cudaSuccess) {
+      std::string m = std::string("device setup: ") + cudaGetErrorString(e);
+      free_device(c);
+      delete c;
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
+    }
+    c->on_device = true;
+  }
+  *out = c;
+  return GP_OK;
+}
+
+void gp_destroy(gp_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->on_device) {
+    DeviceGuard g(ctx->device);
+    free_device(ctx);
+  }
+  delete ctx;
+}
+
+gp_status gp_num_active_dofs(const gp_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return fail(ctx, GP_EINVAL, "null argument");
+  *n = ctx->plan.n_active;
+  return GP_OK;
+}
+
+gp_status gp_num_ghost_faces(const gp_ctx* ctx, int64_t* nf) {
+  if (!ctx || !nf) return fail(ctx, GP_EINVAL, "null argument");
+  *nf = ctx->plan.num_faces();
+  return GP_OK;
+}
+
+gp_status gp_num_touched_dofs(const gp_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return fail(ctx, GP_EINVAL, "null argument");
+  *n = ctx->plan.n_touched;
+  return GP_OK;
+}
+
+gp_status gp_cell_counts(const gp_ctx* ctx, int64_t counts[3]) {
+  if (!ctx || !counts) return fail(ctx, GP_EINVAL, "null argument");
+  for (int i = 0; i < 3; ++i) counts[i] = ctx->plan.cell_counts[i];
+  return GP_OK;
+}
+
+gp_status gp_active_dof_coords(const gp_ctx* ctx, double* xyz) {
+  if (!ctx || !xyz) return fail(ctx, GP_EINVAL, "null argument");
+  gp::active_coords(ctx->plan, xyz);
+  return GP_OK;
+}
+
+gp_status gp_ghost_faces(const gp_ctx* ctx, int32_t* axis, int64_t* cell) {
+  if (!ctx || !axis || !cell) return fail(ctx, GP_EINVAL, "null argument");
+  const gp::Plan& p = ctx->plan;
+  for (int a = 0; a < p.dim; ++a)
+    for (int64_t f = p.fstart[a]; f < p.fstart[a + 1]; ++f) {
+      axis[f] = a;
+      cell[f] = p.face_cell[f];
+    }
+  return GP_OK;
+}
+
+gp_status gp_cell_classes(const gp_ctx* ctx, int8_t* cls) {
+  if (!ctx || !cls) return fail(ctx, GP_EINVAL, "null argument");
+  std::memcpy(cls, ctx->plan.cls.data(), ctx->plan.cls.size());
+  return GP_OK;
+}
+
+gp_status gp_reference_1d(const gp_ctx* ctx, double* mass, double* jumps, double* scale) {
+  if (!ctx || !mass || !jumps || !scale) return fail(ctx, GP_EINVAL, "null argument");
+  const gp::Plan& p = ctx->plan;
+  std::memcpy(mass, p.mass.data(), p.mass.size() * sizeof(double));
+  std::memcpy(jumps, p.jumps.data(), p.jumps.size() * sizeof(double));
+  std::memcpy(scale, p.scale.data(), p.scale.size() * sizeof(double));
+  return GP_OK;
+}
+
+gp_status gp_profile_enable(gp_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, GP_EINVAL, "null context");
+  if (!ctx->on_device) return fail(ctx, GP_EDEVICE, "context was built host-only (device = -1)");
+  ctx->prof = enable != 0;
+  ctx->nprof = 0;
+  return GP_OK;
+}
+
+gp_status gp_profile_read(gp_ctx* ctx, double ms[2], int64_t* calls) {
+  if (!ctx || !ms || !calls) return fail(ctx, GP_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  ms[0] = ms[1] = 0.0;
+  for (int64_t i = 0; i < ctx->nprof; ++i) {
+    cudaEvent_t* e = &ctx->ev[3 * i];
+    GP_CUDA(ctx, cudaEventSynchronize(e[2]));
+    float a = 0.f, b = 0.f;
+    GP_CUDA(ctx, cudaEventElapsedTime(&a, e[0], e[1]));
+    GP_CUDA(ctx, cudaEventElapsedTime(&b, e[1], e[2]));
+    ms[0] += a;
+    ms[1] += b;
+  }
+  *calls = ctx->nprof;
+  return GP_OK;
+}
+
+gp_status gp_apply(gp_ctx* ctx, const void* x, void* y, void* stream) {
+  gp_status s = check_apply(ctx, x, y);
+  if (s != GP_OK) return s;
+  if (ctx->plan.n_active == 0) return GP_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
+  return launch(ctx, x, y, 0, (cudaStream_t)stream);
+}
+
+gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream) {
+  gp_status s = check_apply(ctx, x, y);
+  if (s != GP_OK) return s;
+  if (ctx->plan.n_active == 0 || ctx->plan.num_faces() == 0) return GP_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
+  return launch(ctx, x, y, 1, (cudaStream_t)stream);
+}
+
+gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* stream) {
+  if (!ctx) return fail(nullptr, GP_EINVAL, "null context");
+  if (!ctx->on_device) return fail(ctx, GP_EDEVICE, "context was built host-only (device = -1)");
+  const int64_t n = ctx->plan.n_active;
+  if (n == 0) return GP_OK;
+  if (!x_host || !y_host) return fail(ctx, GP_EINVAL, "null x or y");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
+  const size_t bytes = (size_t)n * ctx->elem;
+  if (!ctx->d_xh) GP_CUDA(ctx, cudaMalloc(&ctx->d_xh, bytes));
+  if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
+  cudaStream_t st = (cudaStream_t)stream;
+  GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
+  gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st);
+  if (s != GP_OK) return s;
+  GP_CUDA(ctx, cudaMemcpyAsync(y_host, ctx->d_yh, bytes, cudaMemcpyDeviceToHost, st));
+  GP_CUDA(ctx, cudaStreamSynchronize(st));
+  return GP_OK;
+}
+
+gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs, const void* const* x,
+                           void* const* y, void* stream) {
+  if (nprob < 0 || nrhs < 1 || (nprob > 0 && (!ctxs || !x || !y)))
+    return fail(nullptr, GP_EINVAL, "bad batched arguments");
+  if (nprob == 0) return GP_OK;
+  const int prec = ctxs[0] ? ctxs[0]->plan.precision : -1;
+  const int dev = ctxs[0] ? ctxs[0]->device : -1;
+  for (int p = 0; p < nprob; ++p) {
+    gp_status s = check_apply(ctxs[p], x[p], y[p]);
+    if (s != GP_OK) return fail(nullptr, s, std::string("problem ") + std::to_string(p) + ": " + ctxs[p]->err);
+    if (ctxs[p]->plan.precision != prec || ctxs[p]->device != dev)
+      return fail(nullptr, GP_EINVAL, "all contexts must share precision and device");
+  }
+  DeviceGuard g(dev);
+  if (!g.ok) return fail(nullptr, GP_ECUDA, "cudaSetDevice failed");
+  for (int p = 0; p < nprob; ++p) {
+    gp_ctx* c = ctxs[p];
+    const int64_t n = c->plan.n_active;
+    if (n == 0) continue;
+    for (int r = 0; r < nrhs; ++r) {
+      const char* xp = (const char*)x[p] + (size_t)r * n * c->elem;
+      char* yp = (char*)y[p] + (size_t)r * n * c->elem;
+      gp_status s = launch(c, xp, yp, 0, (cudaStream_t)stream);
+      if (s != GP_OK) return fail(nullptr, s, c->err);
+    }
+  }
+  return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// Host plan of the ghost-penalty operator (built once per mesh, degree, level set).
+//
+//  * cell classification from the level set phi (> 0 inside), Sec. 2;
+//  * ghost faces: interior faces between two active cells with at least one
+//    cut cell (Sec. 2.2 and the figure of intersected cells);
+//  * active DoFs: FE_Q lattice nodes of active cells, lexicographic with x
+//    fastest (Sec. 2.4, i = i1 + i2 N1 + i3 N1 N2), compacted;
+//  * 1D reference matrices in FP64 (Sec. 2.4, M^1 and G^1_k with their h
+//    scaling), computed here with a collocation differentiation matrix;
+//  * tables for the kernels: per involved cell the compact index of each of
+//    its x-rows, per face its two cells, per (axis, cell) the face id, and
+//    the lift segments/tiles over the active DoFs.
+//
+// Compile with -ffp-contract=off: the classification must round exactly as
+// written so that every implementation of the same rule agrees cell by cell.
+#include "gp_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+namespace gp {
+
+// ---------------------------------------------------------------- 1D data --
+
+// All 1D quantities are computed in long double (80-bit on x86-64, binary128 on
+// aarch64) and rounded once to double: powers of the differentiation matrix
+// lose about 1e-12 of relative accuracy at k = 8 in plain double.
+using R = long double;
+
+// Legendre P_n and P_n' at t in (-1, 1) by the three-term recurrence.
+static void legendre(int n, R t, R& p, R& dp) {
+  R p0 = 1, p1 = t;
+  if (n == 0) { p = 1; dp = 0; return; }
+  for (int m = 2; m <= n; ++m) {
+    R p2 = ((2 * m - 1) * t * p1 - (m - 1) * p0) / m;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (t * p1 - p0) / (t * t - 1);  // P_n' = n (t P_n - P_{n-1}) / (t^2 - 1)
+}
+
+static void gauss_lobatto_01_r(int k, std::vector<R>& x) {
+  x.assign(k + 1, R(0));
+  x[k] = 1;
+  const R pi = 3.141592653589793238462643383279502884L;
+  for (int i = 1; i < k; ++i) {
+    // interior points: roots of P_k', Newton from the Chebyshev-Lobatto guess;
+    // P_k'' from the Legendre equation (1-t^2) P'' = 2 t P' - k(k+1) P
+    R t = -std::cos(pi * i / k);
+    for (int it = 0; it < 200; ++it) {
+      R p, dp;
+      legendre(k, t, p, dp);
+      R d2p = (2 * t * dp - R(k) * (k + 1) * p) / (1 - t * t);
+      R dt = dp / d2p;
+      t -= dt;
+      if (std::fabs(dt) <= 4 * std::numeric_limits<R>::epsilon() * std::fabs(t)) break;
+    }
+    x[i] = (t + 1) / 2;
+  }
+}
+
+void gauss_lobatto_01(int k, std::vector<double>& x) {
+  std::vector<R> xr;
+  gauss_lobatto_01_r(k, xr);
+  x.assign(xr.begin(), xr.end());
+}
+
+static void gauss_legendre_01(int nq, std::vector<R>& x, std::vector<R>& w) {
+  x.assign(nq, R(0));
+  w.assign(nq, R(0));
+  const R pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < nq; ++i) {
+    R t = -std::cos(pi * (i + R(0.75)) / (nq + R(0.5)));
+    R p = 0, dp = 1;
+    for (int it = 0; it < 200; ++it) {
+      legendre(nq, t, p, dp);
+      R dt = p / dp;
+      t -= dt;
+      if (std::fabs(dt) <= 4 * std::numeric_limits<R>::epsilon()) break;
+    }
+    legendre(nq, t, p, dp);
+    x[i] = (t + 1) / 2;
+    w[i] = 1 / ((1 - t * t) * dp * dp);  // 2/((1-t^2)P'^2) scaled to [0,1]
+  }
+}
+
+// M^[a][b] = int_0^1 l_a l_b (Gauss rule with k+1 points, exact for degree 2k),
+// g_j[b] = jump of d^j/dx^j of patch basis b at the face of [0,1] u [1,2]:
+//   b <= k: l_b on K- (evaluated at x = 1), b >= k: l_{b-k} on K+ (at x = 0 of K+).
+// Derivatives come from powers of the collocation differentiation matrix
+// D[i][m] = l_m'(x_i) (barycentric form), so (D^j)[i][m] = l_m^(j)(x_i).
+void reference_1d(int k, const std::vector<double>& /*gl*/, std::vector<double>& mass,
+                  std::vector<double>& jumps) {
+  const int N = k + 1;
+  std::vector<R> gl;
+  gauss_lobatto_01_r(k, gl);
+  std::vector<R> bw(N, R(1));
+  for (int i = 0; i < N; ++i)
+    for (int m = 0; m < N; ++m)
+      if (m != i) bw[i] /= (gl[i] - gl[m]);
+  std::vector<R> D(N * N, R(0));
+  for (int i = 0; i < N; ++i) {
+    R diag = 0;
+    for (int m = 0; m < N; ++m) {
+      if (m == i) continue;
+      R v = (bw[m] / bw[i]) / (gl[i] - gl[m]);
+      D[i * N + m] = v;
+      diag -= v;
+    }
+    D[i * N + i] = diag;
+  }
+  jumps.assign(k * (2 * k + 1), 0.0);
+  std::vector<R> Dj(D), tmp(N * N);
+  for (int j = 1; j <= k; ++j) {
+    for (int b = 0; b <= 2 * k; ++b) {
+      R v = 0;
+      if (b <= k) v += Dj[k * N + b];        // l_b^(j) at the right end of K-
+      if (b >= k) v -= Dj[0 * N + (b - k)];  // l_{b-k}^(j) at the left end of K+
+      jumps[(j - 1) * (2 * k + 1) + b] = (double)v;
+    }
+    for (int i = 0; i < N; ++i)
+      for (int m = 0; m < N; ++m) {
+        R s = 0;
+        for (int q = 0; q < N; ++q) s += Dj[i * N + q] * D[q * N + m];
+        tmp[i * N + m] = s;
+      }
+    Dj.swap(tmp);
+  }
+  std::vector<R> xq, wq;
+  gauss_legendre_01(N, xq, wq);
+  std::vector<R> V(N * N);  // V[q][m] = l_m(x_q), product form
+  for (int q = 0; q < N; ++q)
+    for (int m = 0; m < N; ++m) {
+      R v = 1;
+      for (int i = 0; i < N; ++i)
+        if (i != m) v *= (xq[q] - gl[i]) / (gl[m] - gl[i]);
+      V[q * N + m] = v;
+    }
+  mass.assign(N * N, 0.0);
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      R s = 0;
+      for (int q = 0; q < N; ++q) s += wq[q] * V[q * N + a] * V[q * N + b];
+      mass[a * N + b] = (double)s;
+    }
+}
+
+// -------------------------------------------------------- classification --
+
+static int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+static void classify_balls(const Plan& p, const gp_levelset* ls, int n, std::vector<int8_t>& cls) {
+  const int d = p.dim;
+  const double h = p.h;
+  int64_t nc = p.ncell;
+  std::vector<uint8_t> any_in(nc, 0), all_out(nc, 1);
+  for (int bidx = 0; bidx < ls->nballs; ++bidx) {
+    const double* c = ls->centers + 3 * bidx;
+    const double r = ls->radii[bidx];
+    const double r2 = r * r;
+    // per-axis squared near/far distances
+    std::vector<double> n2[3], f2[3];
+    for (int a = 0; a < d; ++a) {
+      n2[a].resize(n);
+      f2[a].resize(n);
+      for (int i = 0; i < n; ++i) {
+        double lo = p.lo[a] + i * h;
+        double hi = p.lo[a] + (i + 1.0) * h;
+        double near = std::max(std::max(lo - c[a], c[a] - hi), 0.0);
+        double far = std::max(std::fabs(lo - c[a]), std::fabs(hi - c[a]));
+        n2[a][i] = near * near;
+        f2[a][i] = far * far;
+      }
+    }
+    for (int64_t cell = 0; cell < nc; ++cell) {
+      int ix = (int)(cell % n), iy = (int)((cell / n) % n), iz = (int)(cell / ((int64_t)n * n));
+      double dmin2 = n2[0][ix] + n2[1][iy];
+      double dmax2 = f2[0][ix] + f2[1][iy];
+      if (d == 3) {
+        dmin2 = dmin2 + n2[2][iz];
+        dmax2 = dmax2 + f2[2][iz];
+      }
+      if (dmax2 < r2) any_in[cell] = 1;
+      if (!(dmin2 >= r2)) all_out[cell] = 0;
+    }
+  }
+  for (int64_t cell = 0; cell < nc; ++cell)
+    cls[cell] = any_in[cell] ? INSIDE : (all_out[cell] ? OUTSIDE : CUT);
+}
+
+// Sampled classification with a Lipschitz margin: phi on an (m+1)^d lattice
+// per cell; inside if min > margin, outside if max < -margin, else cut.
+static void classify_sampled(const Plan& p, const gp_levelset* ls, int n, double domain_hi0,
+                             std::vector<int8_t>& cls) {
+  const int d = p.dim;
+  const int m = ls->samples > 0 ? ls->samples : 4;
+  const double hs = (domain_hi0 - p.lo[0]) / ((double)n * m);
+  const int ns = n * m + 1;
+  double lip = ls->kind == GP_LS_GYROID ? std::sqrt(6.0) : ls->lipschitz;
+  const double margin = lip * hs * std::sqrt((double)d) / 2.0;
+  std::vector<double> co[3];
+  for (int a = 0; a < d; ++a) {
+    co[a].resize(ns);
+    for (int s = 0; s < ns; ++s) co[a][s] = p.lo[a] + s * hs;
+  }
+  std::vector<double> sn[3], cs[3];
+  if (ls->kind == GP_LS_GYROID) {
+    for (int a = 0; a < 3; ++a) {
+      sn[a].resize(ns);
+      cs[a].resize(ns);
+      for (int s = 0; s < ns; ++s) {
+        sn[a][s] = std::sin(co[a][s]);
+        cs[a][s] = std::cos(co[a][s]);
+      }
+    }
+  }
+  auto phi = [&](int sx, int sy, int sz) -> double {
+    if (ls->kind == GP_LS_GYROID)
+      return ((sn[0][sx] * cs[1][sy] + sn[1][sy] * cs[2][sz]) + sn[2][sz] * cs[0][sx]) - ls->iso;
+    double pt[3] = {co[0][sx], co[1][sy], d == 3 ? co[2][sz] : 0.0};
+    return ls->fn(pt, ls->user);
+  };
+  const int64_t nc = p.ncell;
+  for (int64_t cell = 0; cell < nc; ++cell) {
+    int ix = (int)(cell % n), iy = (int)((cell / n) % n), iz = d == 3 ? (int)(cell / ((int64_t)n * n)) : 0;
+    double mn = std::numeric_limits<double>::infinity(), mx = -mn;
+    int zr = d == 3 ? m : 0;
+    for (int c = 0; c <= zr; ++c)
+      for (int b = 0; b <= m; ++b)
+        for (int a = 0; a <= m; ++a) {
+          double v = phi(ix * m + a, iy * m + b, iz * m + c);
+          mn = std::min(mn, v);
+          mx = std::max(mx, v);
+        }
+    cls[cell] = (mx < -margin) ? OUTSIDE : ((mn > margin) ? INSIDE : CUT);
+  }
+}
+
+// ----------------------------------------------------------- numbering --
+
+int64_t Plan::compact(int X, int64_t row) const {
+  int64_t base = row_start[row];
+  for (int r = run_off[row]; r < run_off[row + 1]; ++r) {
+    int X0 = runs[2 * r], X1 = runs[2 * r + 1];
+    if (X >= X0 && X <= X1) return base + (X - X0);
+    if (X > X1) base += X1 - X0 + 1;
+  }
+  return -1;
+}
+
+// cell indices along one axis whose closure contains lattice coordinate Y
+static int adjacent_cells(int Y, int k, int n, int out[2]) {
+  int c = Y / k, cnt = 0;
+  if (Y % k == 0 && c - 1 >= 0) out[cnt++] = c - 1;
+  if (c < n) out[cnt++] = c;
+  return cnt;
+}
+
+// Per lattice row: x-runs of nodes that belong to a cell flagged in `mask`.
+static void row_runs(const Plan& p, const std::vector<uint8_t>& mask, int64_t row,
+                     std::vector<int>& out) {
+  const int n = p.n, k = p.k;
+  int Y = (int)(row % p.nl), Z = p.dim == 3 ? (int)(row / p.nl) : 0;
+  int cy[2], cz[2] = {0, 0};
+  int ny = adjacent_cells(Y, k, n, cy);
+  int nz = p.dim == 3 ? adjacent_cells(Z, k, n, cz) : 1;
+  out.clear();
+  int open0 = -1, open1 = -1;
+  for (int ci = 0; ci < n; ++ci) {
+    bool on = false;
+    for (int a = 0; a < ny && !on; ++a)
+      for (int b = 0; b < nz && !on; ++b) {
+        int64_t cell = ci + (int64_t)n * (cy[a] + (int64_t)n * cz[b]);
+        on = mask[cell] != 0;
+      }
+    if (!on) continue;
+    int X0 = ci * k, X1 = ci * k + k;
+    if (open0 >= 0 && X0 <= open1) {
+      open1 = X1;
+    } else {
+      if (open0 >= 0) { out.push_back(open0); out.push_back(open1); }
+      open0 = X0;
+      open1 = X1;
+    }
+  }
+  if (open0 >= 0) { out.push_back(open0); out.push_back(open1); }
+}
+
+void active_coords(const Plan& p, double* xyz) {
+  const int d = p.dim, k = p.k;
+  int64_t c = 0;
+  auto coord = [&](int a, int X) {
+    int ci = X / k, q = X % k;
+    return p.lo[a] + (ci + p.gl[q]) * p.h;
+  };
+  for (int64_t row = 0; row < p.nrows; ++row) {
+    int Y = (int)(row % p.nl), Z = d == 3 ? (int)(row / p.nl) : 0;
+    for (int r = p.run_off[row]; r < p.run_off[row + 1]; ++r)
+      for (int X = p.runs[2 * r]; X <= p.runs[2 * r + 1]; ++X) {
+        xyz[c * d + 0] = coord(0, X);
+        xyz[c * d + 1] = coord(1, Y);
+        if (d == 3) xyz[c * d + 2] = coord(2, Z);
+        ++c;
+      }
+  }
+}
+
+// ---------------------------------------------------------------- plan --
+
+gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, Plan& p,
+                     std::string& err) {
+  if (!mesh || !ls || !opts) { err = "null argument"; return GP_EINVAL; }
+  const int d = mesh->dim;
+  if (d != 2 && d != 3) { err = "dim must be 2 or 3"; return GP_EINVAL; }
+  const int k = opts->degree;
+  if (k < 1) { err = "degree must be >= 1"; return GP_EINVAL; }
+  if (k > KMAX) { err = "degree > 8 is not built"; return GP_EUNSUPPORTED; }
+  if (opts->precision != GP_FP64 && opts->precision != GP_FP32) { err = "bad precision"; return GP_EINVAL; }
+  const int n = mesh->n[0];
+  for (int a = 0; a < d; ++a) {
+    if (mesh->n[a] != n) { err = "the mesh must have the same number of cells per axis"; return GP_EINVAL; }
+    if (!(mesh->hi[a] > mesh->lo[a])) { err = "empty mesh box"; return GP_EINVAL; }
+  }
+  if (n < 1 || (int64_t)n * k + 1 > (1 << 24)) { err = "bad cell count"; return GP_EINVAL; }
+  const double h = (mesh->hi[0] - mesh->lo[0]) / n;
+  for (int a = 1; a < d; ++a) {
+    double ha = (mesh->hi[a] - mesh->lo[a]) / n;
+    if (std::fabs(ha - h) > 1e-12 * h) { err = "cells must be squares/cubes (equal h per axis)"; return GP_EINVAL; }
+  }
+  if (opts->nweights != 0 && opts->nweights != k) { err = "nweights must be 0 or k"; return GP_EINVAL; }
+  if (opts->nweights == k && !opts->weights) { err = "weights is NULL"; return GP_EINVAL; }
+
+  p.dim = d;
+  p.n = n;
+  p.k = k;
+  p.precision = opts->precision;
+  for (int a = 0; a < 3; ++a) p.lo[a] = a < d ? mesh->lo[a] : 0.0;
+  p.h = h;
+  p.nl = n * k + 1;
+  p.ncell = ipow(n, d);
+  p.nrows = ipow(p.nl, d - 1);
+  p.L = (int)ipow(k + 1, d - 1);
+  if (p.ncell > (int64_t)1 << 31) { err = "too many cells"; return GP_EINVAL; }
+
+  // ---- classification
+  p.cls.assign(p.ncell, OUTSIDE);
+  switch (ls->kind) {
+    case GP_LS_CONST:
+      std::fill(p.cls.begin(), p.cls.end(), ls->value > 0 ? INSIDE : OUTSIDE);
+      break;
+    case GP_LS_BALLS:
+      if (ls->nballs < 1 || !ls->centers || !ls->radii) { err = "balls need centers and radii"; return GP_EINVAL; }
+      classify_balls(p, ls, n, p.cls);
+      break;
+    case GP_LS_GYROID:
+      if (d != 3) { err = "the gyroid level set is 3D"; return GP_EINVAL; }
+      classify_sampled(p, ls, n, mesh->hi[0], p.cls);
+      break;
+    case GP_LS_CALLBACK:
+      if (!ls->fn || !(ls->lipschitz > 0)) { err = "callback level set needs fn and lipschitz > 0"; return GP_EINVAL; }
+      classify_sampled(p, ls, n, mesh->hi[0], p.cls);
+      break;
+    default:
+      err = "unknown level-set kind";
+      return GP_EINVAL;
+  }
+  for (int c = 0; c < 3; ++c) p.cell_counts[c] = 0;
+  for (int64_t c = 0; c < p.ncell; ++c) p.cell_counts[(int)p.cls[c]]++;
+
+  // ---- ghost faces, sorted by axis then lower cell
+  p.face_cell.clear();
+  const int64_t stride[3] = {1, n, (int64_t)n * n};
+  for (int a = 0; a < d; ++a) {
+    p.fstart[a] = (int32_t)p.face_cell.size();
+    for (int64_t c = 0; c < p.ncell; ++c) {
+      int ia = (int)((c / stride[a]) % n);
+      if (ia + 1 >= n) continue;
+      int8_t c0 = p.cls[c], c1 = p.cls[c + stride[a]];
+      if (c0 == OUTSIDE || c1 == OUTSIDE) continue;
+      if (opts->all_faces || c0 == CUT || c1 == CUT) p.face_cell.push_back(c);
+    }
+  }
+  p.fstart[d] = (int32_t)p.face_cell.size();
+  for (int a = d + 1; a < 4; ++a) p.fstart[a] = p.fstart[d];
+  const int64_t nf = p.num_faces();
+  if (nf > (int64_t)1 << 30) { err = "too many faces"; return GP_EINVAL; }
+
+  // ---- involved cells (the two cells of every face)
+  std::vector<int32_t> inv_of(p.ncell, -1);
+  std::vector<uint8_t> involved(p.ncell, 0);
+  for (int a = 0; a < d; ++a)
+    for (int64_t f = p.fstart[a]; f < p.fstart[a + 1]; ++f) {
+      involved[p.face_cell[f]] = 1;
+      involved[p.face_cell[f] + stride[a]] = 1;
+    }
+  p.inv_cells.clear();
+  for (int64_t c = 0; c < p.ncell; ++c)
+    if (involved[c]) {
+      inv_of[c] = (int32_t)p.inv_cells.size();
+      p.inv_cells.push_back(c);
+    }
+  p.face_inv.resize(2 * nf);
+  p.face_of.assign((size_t)d * p.ncell, -1);
+  for (int a = 0; a < d; ++a)
+    for (int64_t f = p.fstart[a]; f < p.fstart[a + 1]; ++f) {
+      int64_t c = p.face_cell[f];
+      p.face_inv[2 * f] = inv_of[c];
+      p.face_inv[2 * f + 1] = inv_of[c + stride[a]];
+      p.face_of[(size_t)a * p.ncell + c] = (int32_t)f;
+    }
+
+  // ---- numbering: active runs per lattice row
+  std::vector<uint8_t> active(p.ncell);
+  for (int64_t c = 0; c < p.ncell; ++c) active[c] = p.cls[c] != OUTSIDE;
+  p.row_start.assign(p.nrows, 0);
+  p.run_off.assign(p.nrows + 1, 0);
+  p.runs.clear();
+  std::vector<int> tmp;
+  int64_t total = 0;
+  for (int64_t row = 0; row < p.nrows; ++row) {
+    row_runs(p, active, row, tmp);
+    p.row_start[row] = total;
+    for (size_t i = 0; i < tmp.size(); i += 2) {
+      p.runs.push_back(tmp[i]);
+      p.runs.push_back(tmp[i + 1]);
+      total += tmp[i + 1] - tmp[i] + 1;
+    }
+    p.run_off[row + 1] = (int32_t)(p.runs.size() / 2);
+  }
+  p.n_active = total;
+  if (total >= ((int64_t)1 << 31) - 1) { err = "too many active DoFs for 32-bit indices"; return GP_EUNSUPPORTED; }
+
+  // ---- row table of the involved cells
+  const int L = p.L;
+  const int64_t ninv = (int64_t)p.inv_cells.size();
+  p.rowtab.resize((size_t)ninv * L);
+  for (int64_t i = 0; i < ninv; ++i) {
+    int64_t c = p.inv_cells[i];
+    int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+    for (int t = 0; t < L; ++t) {
+      int ty = t % (k + 1), tz = t / (k + 1);
+      int64_t row = (int64_t)(cj * k + ty) + (d == 3 ? (int64_t)p.nl * (cl * k + tz) : 0);
+      int64_t cidx = p.compact(ci * k, row);
+      if (cidx < 0) { err = "internal: involved cell node not active"; return GP_EINVAL; }
+      p.rowtab[(size_t)i * L + t] = (int32_t)cidx;
+    }
+  }
+
+  // ---- lift segments: active runs split into touched / untouched pieces
+  std::vector<int32_t> seg_t, seg_z;
+  std::vector<int> trun;
+  int64_t touched = 0;
+  auto emit = [&](std::vector<int32_t>& dst, int64_t c0, int X0, int64_t row, int len, int flag) {
+    while (len > 0) {
+      int l = std::min(len, SEG_MAX);
+      dst.push_back((int32_t)c0);
+      dst.push_back(X0);
+      dst.push_back((int32_t)row);
+      dst.push_back(l | (flag << 16));
+      c0 += l;
+      X0 += l;
+      len -= l;
+    }
+  };
+  for (int64_t row = 0; row < p.nrows; ++row) {
+    if (p.run_off[row] == p.run_off[row + 1]) continue;
+    row_runs(p, involved, row, trun);
+    int64_t c = p.row_start[row];
+    size_t tr = 0;
+    for (int r = p.run_off[row]; r < p.run_off[row + 1]; ++r) {
+      int X = p.runs[2 * r], X1 = p.runs[2 * r + 1];
+      while (X <= X1) {
+        while (tr < trun.size() && trun[tr + 1] < X) tr += 2;
+        if (tr < trun.size() && trun[tr] <= X) {
+          int e = std::min(X1, trun[tr + 1]);
+          emit(seg_t, c, X, row, e - X + 1, 1);
+          touched += e - X + 1;
+          c += e - X + 1;
+          X = e + 1;
+        } else {
+          int e = (tr < trun.size()) ? std::min(X1, trun[tr] - 1) : X1;
+          emit(seg_z, c, X, row, e - X + 1, 0);
+          c += e - X + 1;
+          X = e + 1;
+        }
+      }
+    }
+  }
+  p.n_touched = touched;
+  p.segs = seg_t;
+  const int32_t nseg_t = (int32_t)(seg_t.size() / 4);
+  p.segs.insert(p.segs.end(), seg_z.begin(), seg_z.end());
+  const int32_t nseg = (int32_t)(p.segs.size() / 4);
+  p.tiles.clear();
+  auto pack = [&](int32_t s0, int32_t s1) {
+    int32_t first = s0, cnt = 0, nodes = 0;
+    for (int32_t s = s0; s < s1; ++s) {
+      int len = p.segs[4 * s + 3] & 0xffff;
+      if (nodes + len > TILE_NODES) {
+        p.tiles.push_back(first);
+        p.tiles.push_back(cnt);
+        first = s;
+        cnt = 0;
+        nodes = 0;
+      }
+      cnt++;
+      nodes += len;
+    }
+    if (cnt > 0) { p.tiles.push_back(first); p.tiles.push_back(cnt); }
+  };
+  pack(0, nseg_t);
+  p.ntiles_touched = (int32_t)(p.tiles.size() / 2);
+  pack(nseg_t, nseg);
+  p.ntiles_all = (int32_t)(p.tiles.size() / 2);
+
+  // ---- 1D reference data and the per-order scale c_j h^(d-2)
+  gauss_lobatto_01(k, p.gl);
+  reference_1d(k, p.gl, p.mass, p.jumps);
+  p.scale.resize(k);
+  const double hd = d == 3 ? h : 1.0;
+  for (int j = 0; j < k; ++j) {
+    double c = opts->nweights == k ? opts->weights[j] : opts->gamma;
+    p.scale[j] = c * hd;
+  }
+  return GP_OK;
+}
+
+}  // namespace gp

@@ -1,0 +1,69 @@
+// Host-side plan of the ghost-penalty operator: classification, face list,
+// active-DoF numbering, 1D reference matrices and the tables the kernels read.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gp.h"
+
+namespace gp {
+
+constexpr int KMAX = 8;
+constexpr int SEG_MAX = 64;      // nodes per lift segment
+constexpr int TILE_NODES = 256;  // nodes per lift tile (= threads of the lift kernel)
+
+enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
+
+struct Plan {
+  int dim = 0, n = 0, k = 0, precision = GP_FP64;
+  double lo[3] = {0, 0, 0};
+  double h = 0;
+  int nl = 0;                     // lattice nodes per axis, n*k+1
+  int64_t ncell = 0;              // n^dim
+  int64_t nrows = 0;              // lattice rows along x, nl^(dim-1)
+  int L = 0;                      // tangential nodes per face, (k+1)^(dim-1)
+
+  std::vector<int8_t> cls;        // cell classes, lexicographic (x fastest)
+  int64_t cell_counts[3] = {0, 0, 0};
+
+  // ghost faces, sorted by normal axis then lower cell
+  int32_t fstart[4] = {0, 0, 0, 0};
+  std::vector<int64_t> face_cell; // lower cell (lexicographic index)
+  std::vector<int32_t> face_inv;  // 2 per face: involved-cell index of K-, K+
+  std::vector<int64_t> inv_cells; // involved cells (sorted)
+  std::vector<int32_t> rowtab;    // ninv x L: compact index of (ci*k, row tau) per involved cell
+  std::vector<int32_t> face_of;   // dim x ncell: face id of (axis, lower cell), -1 if none
+
+  // active-DoF numbering: per lattice row, active x-runs and the compact start
+  int64_t n_active = 0, n_touched = 0;
+  std::vector<int64_t> row_start; // nrows
+  std::vector<int32_t> run_off;   // nrows+1, offsets into runs
+  std::vector<int32_t> runs;      // (X0, X1) inclusive pairs
+
+  // lift work: segments (c0, X0, row, len | touched<<16) and tiles (first, count)
+  std::vector<int32_t> segs;
+  std::vector<int32_t> tiles;
+  int32_t ntiles_touched = 0, ntiles_all = 0;
+
+  // FP64 1D reference data
+  std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
+  std::vector<double> mass;       // (k+1)^2
+  std::vector<double> jumps;      // k x (2k+1)
+  std::vector<double> scale;      // k: c_j h^(dim-2)
+
+  int64_t num_faces() const { return (int64_t)face_cell.size(); }
+  int64_t compact(int X, int64_t row) const;
+};
+
+gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
+                     Plan& p, std::string& err);
+void active_coords(const Plan& p, double* xyz);
+
+// 1D precompute (exposed for the unit tests through gp_reference_1d)
+void gauss_lobatto_01(int k, std::vector<double>& x);
+void reference_1d(int k, const std::vector<double>& gl, std::vector<double>& mass,
+                  std::vector<double>& jumps);
+
+}  // namespace gp

@@ -1,0 +1,315 @@
+"""Thin Python binding of the C ABI in include/gp.h (ctypes).
+
+Argument marshalling only: every step of y = G x runs in libgp.so.  The
+functions keep the C names.  Device vectors are passed as torch CUDA tensors
+(or raw device pointers); the library never sees a torch type.  Importing
+this module loads the in-tree library and fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgp.so")
+
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_EDEVICE, GP_EUNSUPPORTED = range(6)
+GP_FP64, GP_FP32 = 0, 1
+GP_LS_BALLS, GP_LS_GYROID, GP_LS_CALLBACK, GP_LS_CONST = 1, 2, 3, 4
+_STATUS = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ECUDA", 4: "GP_EDEVICE",
+           5: "GP_EUNSUPPORTED"}
+
+
+class GpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gp_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+LEVELSET_FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
+
+
+class gp_levelset(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nballs", C.c_int), ("centers", C.POINTER(C.c_double)),
+                ("radii", C.POINTER(C.c_double)), ("iso", C.c_double), ("value", C.c_double),
+                ("fn", LEVELSET_FN), ("user", C.c_void_p), ("lipschitz", C.c_double),
+                ("samples", C.c_int)]
+
+
+class gp_opts(C.Structure):
+    _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
+                ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
+                ("device", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgp.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python -m paper_2503_00246_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    i64p = C.POINTER(C.c_int64)
+    sig = {
+        "gp_setup": ([C.POINTER(gp_mesh), C.POINTER(gp_levelset), C.POINTER(gp_opts), C.POINTER(P)], C.c_int),
+        "gp_destroy": ([P], None),
+        "gp_num_active_dofs": ([P, i64p], C.c_int),
+        "gp_num_ghost_faces": ([P, i64p], C.c_int),
+        "gp_num_touched_dofs": ([P, i64p], C.c_int),
+        "gp_cell_counts": ([P, i64p], C.c_int),
+        "gp_active_dof_coords": ([P, C.POINTER(C.c_double)], C.c_int),
+        "gp_ghost_faces": ([P, C.POINTER(C.c_int32), i64p], C.c_int),
+        "gp_cell_classes": ([P, C.POINTER(C.c_int8)], C.c_int),
+        "gp_reference_1d": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+        "gp_apply": ([P, P, P, P], C.c_int),
+        "gp_apply_add": ([P, P, P, P], C.c_int),
+        "gp_apply_host": ([P, P, P, P], C.c_int),
+        "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
+        "gp_profile_enable": ([P, C.c_int], C.c_int),
+        "gp_profile_read": ([P, C.POINTER(C.c_double), i64p], C.c_int),
+        "gp_last_error": ([P], C.c_char_p),
+        "gp_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+# names declared in include/gp.h, used by the tests to check the exports
+ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_faces",
+               "gp_num_touched_dofs", "gp_cell_counts", "gp_active_dof_coords", "gp_ghost_faces",
+               "gp_cell_classes", "gp_reference_1d", "gp_apply", "gp_apply_add", "gp_apply_host",
+               "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
+               "gp_version")
+
+
+def _check(status, ctx=None):
+    if status != GP_OK:
+        msg = lib.gp_last_error(ctx.handle if ctx is not None else None)
+        raise GpError(status, (msg or b"").decode())
+
+
+class Context:
+    """Owns a gp_ctx handle (gp_destroy on close / garbage collection)."""
+
+    def __init__(self, handle, precision, dim, degree):
+        self.handle = handle
+        self.precision = precision
+        self.dim = dim
+        self.degree = degree
+        n = C.c_int64()
+        _check(lib.gp_num_active_dofs(handle, C.byref(n)), self)
+        self.n_active = n.value
+        _check(lib.gp_num_ghost_faces(handle, C.byref(n)), self)
+        self.n_faces = n.value
+        _check(lib.gp_num_touched_dofs(handle, C.byref(n)), self)
+        self.n_touched = n.value
+
+    def close(self):
+        if self.handle:
+            lib.gp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype_np(self):
+        return np.float64 if self.precision == GP_FP64 else np.float32
+
+
+def gp_setup(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts) -> Context:
+    h = C.c_void_p()
+    _check(lib.gp_setup(C.byref(mesh), C.byref(levelset), C.byref(opts), C.byref(h)))
+    return Context(h.value, opts.precision, mesh.dim, opts.degree)
+
+
+def gp_destroy(ctx: Context):
+    ctx.close()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _check_vec(ctx, t, nrhs=1):
+    if isinstance(t, int):
+        return
+    import torch
+    want = torch.float64 if ctx.precision == GP_FP64 else torch.float32
+    if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != nrhs * ctx.n_active:
+        raise GpError(GP_EINVAL, f"expected a contiguous CUDA {want} tensor of {nrhs * ctx.n_active} "
+                                 f"elements, got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+
+def gp_apply(ctx: Context, x, y, stream=None):
+    _check_vec(ctx, x)
+    _check_vec(ctx, y)
+    _check(lib.gp_apply(ctx.handle, _ptr(x), _ptr(y), _stream(stream)), ctx)
+
+
+def gp_apply_add(ctx: Context, x, y, stream=None):
+    _check_vec(ctx, x)
+    _check_vec(ctx, y)
+    _check(lib.gp_apply_add(ctx.handle, _ptr(x), _ptr(y), _stream(stream)), ctx)
+
+
+def gp_apply_host(ctx: Context, x: np.ndarray, y: np.ndarray | None = None, stream=0):
+    """End-to-end apply on host arrays (numpy or pinned torch CPU tensors)."""
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=ctx.dtype_np)
+        if y is None:
+            y = np.empty_like(x)
+        assert x.size == ctx.n_active and y.size == ctx.n_active and y.dtype == x.dtype
+        xp, yp = x.ctypes.data, y.ctypes.data
+    else:
+        xp, yp = x.data_ptr(), y.data_ptr()
+    _check(lib.gp_apply_host(ctx.handle, xp, yp, stream if isinstance(stream, int) else stream.cuda_stream), ctx)
+    return y
+
+
+def gp_apply_batched(ctxs, nrhs, xs, ys, stream=None):
+    n = len(ctxs)
+    for c, x, y in zip(ctxs, xs, ys):
+        _check_vec(c, x, nrhs)
+        _check_vec(c, y, nrhs)
+    H = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    Y = (C.c_void_p * n)(*[_ptr(y) for y in ys])
+    _check(lib.gp_apply_batched(H, n, nrhs, X, Y, _stream(stream)))
+
+
+def gp_num_active_dofs(ctx: Context) -> int:
+    return ctx.n_active
+
+
+def gp_num_ghost_faces(ctx: Context) -> int:
+    return ctx.n_faces
+
+
+def gp_num_touched_dofs(ctx: Context) -> int:
+    return ctx.n_touched
+
+
+def gp_cell_counts(ctx: Context) -> np.ndarray:
+    out = np.zeros(3, dtype=np.int64)
+    _check(lib.gp_cell_counts(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_int64))), ctx)
+    return out
+
+
+def gp_active_dof_coords(ctx: Context) -> np.ndarray:
+    out = np.zeros((ctx.n_active, ctx.dim), dtype=np.float64)
+    _check(lib.gp_active_dof_coords(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+    return out
+
+
+def gp_ghost_faces(ctx: Context):
+    axis = np.zeros(ctx.n_faces, dtype=np.int32)
+    cell = np.zeros(ctx.n_faces, dtype=np.int64)
+    _check(lib.gp_ghost_faces(ctx.handle, axis.ctypes.data_as(C.POINTER(C.c_int32)),
+                              cell.ctypes.data_as(C.POINTER(C.c_int64))), ctx)
+    return axis, cell
+
+
+def gp_cell_classes(ctx: Context, n_cells: int) -> np.ndarray:
+    out = np.zeros(n_cells, dtype=np.int8)
+    _check(lib.gp_cell_classes(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_int8))), ctx)
+    return out
+
+
+def gp_reference_1d(ctx: Context):
+    k = ctx.degree
+    m = np.zeros((k + 1) * (k + 1))
+    g = np.zeros(k * (2 * k + 1))
+    s = np.zeros(k)
+    dp = C.POINTER(C.c_double)
+    _check(lib.gp_reference_1d(ctx.handle, m.ctypes.data_as(dp), g.ctypes.data_as(dp),
+                               s.ctypes.data_as(dp)), ctx)
+    return m.reshape(k + 1, k + 1), g.reshape(k, 2 * k + 1), s
+
+
+def gp_profile_enable(ctx: Context, enable: bool = True):
+    _check(lib.gp_profile_enable(ctx.handle, 1 if enable else 0), ctx)
+
+
+def gp_profile_read(ctx: Context):
+    """(ms_jump, ms_lift, calls): summed kernel times of the traced applies."""
+    ms = (C.c_double * 2)()
+    calls = C.c_int64()
+    _check(lib.gp_profile_read(ctx.handle, ms, C.byref(calls)), ctx)
+    return ms[0], ms[1], calls.value
+
+
+def gp_last_error(ctx: Context | None = None) -> str:
+    return (lib.gp_last_error(ctx.handle if ctx else None) or b"").decode()
+
+
+def gp_version() -> str:
+    return lib.gp_version().decode()
+
+
+# ------------------------------------------------------------ marshalling --
+
+def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0):
+    """gp_mesh / gp_levelset / gp_opts for a workloads.Problem (kept alive in the tuple)."""
+    mesh = gp_mesh()
+    mesh.dim = pr.dim
+    for a in range(3):
+        mesh.n[a] = pr.n if a < pr.dim else 1
+        mesh.lo[a] = pr.lo if a < pr.dim else 0.0
+        mesh.hi[a] = pr.hi if a < pr.dim else 1.0
+    ls = gp_levelset()
+    ls.kind = pr.ls_kind
+    keep = []
+    if pr.ls_kind == GP_LS_BALLS:
+        cen = np.ascontiguousarray(np.asarray(pr.centers, dtype=np.float64).reshape(-1, 3))
+        rad = np.ascontiguousarray(np.asarray(pr.radii, dtype=np.float64))
+        keep += [cen, rad]
+        ls.nballs = rad.size
+        ls.centers = cen.ctypes.data_as(C.POINTER(C.c_double))
+        ls.radii = rad.ctypes.data_as(C.POINTER(C.c_double))
+    ls.iso = pr.iso
+    ls.value = pr.ls_value
+    ls.samples = 4
+    opts = gp_opts()
+    opts.degree = pr.degree
+    opts.gamma = pr.gamma
+    if pr.weights is not None:
+        w = np.ascontiguousarray(np.asarray(pr.weights, dtype=np.float64))
+        keep.append(w)
+        opts.nweights = w.size
+        opts.weights = w.ctypes.data_as(C.POINTER(C.c_double))
+    opts.precision = precision
+    opts.all_faces = 1 if pr.all_faces else 0
+    opts.device = device
+    return mesh, ls, opts, keep
+
+
+def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0) -> Context:
+    mesh, ls, opts, keep = structs_for(pr, precision, device)
+    return gp_setup(mesh, ls, opts)

@@ -1,0 +1,163 @@
+"""C-ABI library checks that need no GPU: exports, host plan vs the oracle,
+1D reference data vs an independent construction, argument errors."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+from numpy.polynomial import Legendre
+
+from oracle.basis import gauss_lobatto_nodes
+from oracle.ghost_penalty import Oracle
+from paper_2503_00246_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "gp.h")
+
+
+def test_library_exports_every_declared_symbol(gplib):
+    src = open(HEADER).read()
+    declared = set(re.findall(r"^\s*(?:gp_status|void|const char\*)\s+(gp_\w+)\s*\(", src, re.M))
+    assert declared == set(gplib.ABI_SYMBOLS)
+    lib = ctypes.CDLL(gplib.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert "sm_103a" in gplib.gp_version()
+
+
+PROBLEMS = [
+    lambda: W.disc_2d(),
+    lambda: W.small_ball(2, 24, 5, seed=3),
+    lambda: W.small_ball(3, 9, 2, seed=5),
+    lambda: W.small_ball(3, 14, 1, radius=0.45, seed=6),
+    lambda: W.ball_3d(),
+    lambda: W.gyroid_3d(k=2, n=24),
+    lambda: W.box_problem(3, 4, 2, all_faces=True),
+    lambda: W.box_problem(2, 5, 3, all_faces=False),
+]
+
+
+@pytest.mark.parametrize("make", PROBLEMS)
+def test_host_plan_matches_oracle(gplib, make):
+    pr = make()
+    ctx = gplib.setup_problem(pr, device=-1)
+    o = Oracle(pr)
+    assert ctx.n_active == o.n_active
+    assert ctx.n_faces == o.n_faces
+    ax, cell = gplib.gp_ghost_faces(ctx)
+    assert np.array_equal(np.stack([ax, cell], 1), o.face_list())
+    cls = gplib.gp_cell_classes(ctx, pr.n ** pr.dim)
+    assert np.array_equal(cls, o.cls.transpose().ravel())
+    np.testing.assert_allclose(gplib.gp_active_dof_coords(ctx), o.num.coords(), rtol=0, atol=1e-14 * max(abs(pr.lo), abs(pr.hi)))
+    counts = gplib.gp_cell_counts(ctx)
+    assert list(counts) == [int((o.cls == c).sum()) for c in range(3)]
+    if o.n_faces:
+        touched = np.unique(np.concatenate([o.patch_index(a).ravel() for a in range(pr.dim)]))
+        assert ctx.n_touched == touched.size
+    else:
+        assert ctx.n_touched == 0
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_reference_1d_against_independent_fits(gplib, k):
+    pr = W.small_ball(3, 6, k, seed=2, weights=W.paper_weights(0.5, k))
+    ctx = gplib.setup_problem(pr, device=-1)
+    M, g, s = gplib.gp_reference_1d(ctx)
+    xi = gauss_lobatto_nodes(k)
+    polys = []
+    for m in range(k + 1):
+        e = np.zeros(k + 1)
+        e[m] = 1
+        polys.append(Legendre.fit(xi, e, k, domain=[0, 1]))
+    Mref = np.array([[((pa * pb).integ()(1.0) - (pa * pb).integ()(0.0)) for pb in polys] for pa in polys])
+    np.testing.assert_allclose(M, Mref, rtol=1e-12, atol=1e-14)
+    hi = [Legendre.fit(1 + xi, np.eye(k + 1)[m], k, domain=[1, 2]) for m in range(k + 1)]
+    for j in range(1, k + 1):
+        gref = np.zeros(2 * k + 1)
+        for b in range(2 * k + 1):
+            if b <= k:
+                gref[b] += polys[b].deriv(j)(1.0)
+            if b >= k:
+                gref[b] -= hi[b - k].deriv(j)(1.0)
+        np.testing.assert_allclose(g[j - 1], gref, rtol=1e-9, atol=1e-9 * np.abs(gref).max())
+        # symmetry of the patch under reflection about the face: g_j[2k-b] = (-1)^(j+1) g_j[b]
+        np.testing.assert_allclose(g[j - 1][::-1], (-1) ** (j + 1) * g[j - 1],
+                                   rtol=1e-10, atol=1e-10 * np.abs(g[j - 1]).max())
+    np.testing.assert_allclose(s, np.array(W.paper_weights(0.5, k)) * pr.h, rtol=1e-15)
+
+
+def test_setup_errors(gplib):
+    pr = W.small_ball(3, 6, 3)
+    mesh, ls, opts, keep = gplib.structs_for(pr, device=-1)
+    for field, val, status in (("degree", 9, gplib.GP_EUNSUPPORTED), ("degree", 0, gplib.GP_EINVAL),
+                               ("precision", 7, gplib.GP_EINVAL), ("nweights", 2, gplib.GP_EINVAL)):
+        old = getattr(opts, field)
+        setattr(opts, field, val)
+        with pytest.raises(gplib.GpError) as e:
+            gplib.gp_setup(mesh, ls, opts)
+        assert e.value.status == status
+        setattr(opts, field, old)
+    mesh.dim = 4
+    with pytest.raises(gplib.GpError):
+        gplib.gp_setup(mesh, ls, opts)
+    mesh.dim = 3
+    mesh.hi[1] = 3.0  # non-cubic cells
+    with pytest.raises(gplib.GpError):
+        gplib.gp_setup(mesh, ls, opts)
+
+
+def test_host_only_context_refuses_apply(gplib):
+    ctx = gplib.setup_problem(W.small_ball(2, 8, 2), device=-1)
+    st = gplib.lib.gp_apply(ctx.handle, 16, 32, None)
+    assert st == gplib.GP_EDEVICE
+    assert "host-only" in gplib.gp_last_error(ctx)
+
+
+@pytest.mark.parametrize("k", [2, 4, 6, 8])
+def test_reference_1d_high_precision(gplib, k):
+    """Jumps g_j and mass M^ within 2e-15 (relative per row) of a 60-digit evaluation."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    xi = gauss_lobatto_nodes(k)
+    xm = []
+    for v in xi:
+        if v in (0.0, 1.0):
+            xm.append(mp.mpf(v))
+            continue
+        f = lambda s: mp.diff(lambda u: mp.legendre(k, u), s)   # noqa: E731
+        xm.append((mp.findroot(f, mp.mpf(2 * v - 1)) + 1) / 2)
+
+    def lag(nodes, m):
+        coef = [mp.mpf(1)]
+        for i, xq in enumerate(nodes):
+            if i == m:
+                continue
+            a0, a1 = -xq / (nodes[m] - xq), 1 / (nodes[m] - xq)
+            new = [mp.mpf(0)] * (len(coef) + 1)
+            for p, c in enumerate(coef):
+                new[p] += c * a0
+                new[p + 1] += c * a1
+            coef = new
+        return coef                                              # monomial coefficients
+
+    def deriv(coef, x, j):
+        return sum(mp.factorial(p) / mp.factorial(p - j) * c * x ** (p - j)
+                   for p, c in enumerate(coef) if p >= j)
+
+    lo = [lag(xm, m) for m in range(k + 1)]
+    hi = [lag([1 + u for u in xm], m) for m in range(k + 1)]
+    ctx = gplib.setup_problem(W.small_ball(3, 6, k, seed=2), device=-1)
+    M, g, _ = gplib.gp_reference_1d(ctx)
+    for j in range(1, k + 1):
+        ref = np.array([float((deriv(lo[b], 1, j) if b <= k else 0) - (deriv(hi[b - k], 1, j) if b >= k else 0))
+                        for b in range(2 * k + 1)])
+        assert np.abs(g[j - 1] - ref).max() <= 2e-15 * np.abs(ref).max(), j
+    Mref = np.zeros((k + 1, k + 1))
+    for a in range(k + 1):
+        for b in range(k + 1):
+            prod = [mp.mpf(0)] * (2 * k + 1)
+            for p, ca in enumerate(lo[a]):
+                for q, cb in enumerate(lo[b]):
+                    prod[p + q] += ca * cb
+            Mref[a, b] = float(sum(c / (p + 1) for p, c in enumerate(prod)))
+    assert np.abs(M - Mref).max() <= 2e-15 * np.abs(Mref).max()

@@ -1,0 +1,216 @@
+"""GPU parity: y = G x through the C ABI against the FP64 CPU oracle.
+
+Tolerances (the operator's stated accuracy targets):
+  FP64 path  ||y - y_ref|| / ||y_ref|| <= 1e-12 and |y_i - y_ref,i| <= 1e-12 ||y_ref||_inf
+  FP32 path  ||y - y_ref|| / ||y_ref|| <= 1e-5  and |y_i - y_ref,i| <= 1e-5  ||y_ref||_inf
+The FP32 path is compared with the oracle applied to x rounded to FP32, so the
+check measures the operator, not the rounding of its input.
+"""
+import numpy as np
+import pytest
+
+from oracle.ghost_penalty import Oracle
+from paper_2503_00246_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def _dev(torch, x, prec):
+    dt = torch.float64 if prec == 0 else torch.float32
+    return torch.tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+
+
+def _apply(gp, torch, ctx, x, prec, add_to=None):
+    xd = _dev(torch, x, prec)
+    if add_to is None:
+        yd = torch.full_like(xd, float("nan"))   # every active DoF must be written
+        gp.gp_apply(ctx, xd, yd)
+    else:
+        yd = _dev(torch, add_to, prec)
+        gp.gp_apply_add(ctx, xd, yd)
+    torch.cuda.synchronize()
+    return yd.double().cpu().numpy()
+
+
+def _ref_input(x, prec):
+    return x if prec == 0 else x.astype(np.float32).astype(np.float64)
+
+
+def _close(y, ref, prec):
+    tol = TOL[prec]
+    assert np.all(np.isfinite(y))
+    nr = np.linalg.norm(ref)
+    assert np.linalg.norm(y - ref) <= tol * nr, np.linalg.norm(y - ref) / nr
+    assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
+
+
+SMALL = [(2, k, 16) for k in range(1, 9)] + [(3, k, 9) for k in range(1, 6)] + [(3, 6, 7), (3, 7, 6),
+                                                                              (3, 8, 6)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim,k,n", SMALL)
+def test_small_meshes_all_degrees(gplib, cuda, dim, k, n, prec):
+    pr = W.small_ball(dim, n, k, radius=0.62, seed=100 + 10 * dim + k)
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    assert (ctx.n_active, ctx.n_faces) == (o.n_active, o.n_faces) and o.n_faces > 0
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    y = _apply(gplib, cuda, ctx, x, prec)
+    _close(y, o.apply(_ref_input(x, prec)), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_paper_weights_and_multiple_balls(gplib, cuda, prec):
+    pr = W.small_ball(3, 12, 4, seed=7, weights=W.paper_weights(0.5, 4))
+    pr.centers = np.array([[-0.3, 0.1, 0.0], [0.35, -0.2, 0.1]])
+    pr.radii = np.array([0.45, 0.4])
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_disc_2d_k2(gplib, cuda, prec):
+    pr = W.disc_2d()
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ball_3d_k3_full(gplib, cuda, prec):
+    """64^3 ball, k = 3: every output compared (the benchmark's launch configuration)."""
+    pr = W.ball_3d()
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
+    if prec == 0:
+        # annihilation of a seeded global polynomial of degree <= k (||G|| from power iteration)
+        ex, co = W.poly_coeffs(pr)
+        xp = W.poly_eval(ex, co, gplib.gp_active_dof_coords(ctx))
+        v = np.random.default_rng(0).standard_normal(ctx.n_active)
+        for _ in range(30):
+            w = _apply(gplib, cuda, ctx, v, 0)
+            gn = np.linalg.norm(w)
+            v = w / gn
+        r = np.linalg.norm(_apply(gplib, cuda, ctx, xp, 0))
+        assert r <= 1e-10 * gn * np.linalg.norm(xp), r / (gn * np.linalg.norm(xp))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_add_and_determinism(gplib, cuda, prec):
+    pr = W.small_ball(3, 16, 3, seed=8)
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    rng = np.random.default_rng(4)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    y0 = rng.uniform(-1, 1, ctx.n_active)
+    y = _apply(gplib, cuda, ctx, x, prec, add_to=y0)
+    ref = _ref_input(y0, prec) + o.apply(_ref_input(x, prec))
+    tol = TOL[prec]
+    assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
+    a = _apply(gplib, cuda, ctx, x, prec)
+    b = _apply(gplib, cuda, ctx, x, prec)
+    assert np.array_equal(a, b)   # fixed summation order: bitwise reproducible
+
+
+@pytest.mark.parametrize("dim,k,m", [(2, 3, 2), (3, 2, 1), (3, 3, 3)])
+def test_kink_energy_on_gpu(gplib, cuda, dim, k, m):
+    """x^T G x of u = ((x_a - x_P)_+)^m * 1 equals c_m h^(2m-1) (m!)^2 |plane| (no oracle)."""
+    import math
+    n, h = 6, 0.3
+    pr = W.box_problem(dim, n, k, all_faces=True, lo=0.0, hi=n * h)
+    ctx = gplib.setup_problem(pr, precision=0)
+    xyz = gplib.gp_active_dof_coords(ctx)
+    u = np.maximum(xyz[:, dim - 1] - 3 * h, 0.0) ** m
+    y = _apply(gplib, cuda, ctx, u, 0)
+    ref = 0.5 * h ** (2 * m - 1) * math.factorial(m) ** 2 * (n * h) ** (dim - 1)
+    assert abs(u @ y - ref) <= 1e-11 * ref
+
+
+def test_no_ghost_faces(gplib, cuda):
+    pr = W.box_problem(3, 4, 2, all_faces=False)      # every cell inside: nothing to penalise
+    ctx = gplib.setup_problem(pr, precision=0)
+    assert ctx.n_faces == 0 and ctx.n_active == 9 ** 3
+    x = np.ones(ctx.n_active)
+    assert np.array_equal(_apply(gplib, cuda, ctx, x, 0), np.zeros(ctx.n_active))
+    y0 = np.arange(ctx.n_active, dtype=np.float64)
+    assert np.array_equal(_apply(gplib, cuda, ctx, x, 0, add_to=y0), y0)
+
+
+def test_single_face_mesh(gplib, cuda):
+    pr = W.box_problem(3, 2, 4, all_faces=True)        # 2x2x2 cells, 12 faces
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=0)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    _close(_apply(gplib, cuda, ctx, x, 0), o.apply(x), 0)
+
+
+def test_host_buffers_end_to_end(gplib, cuda):
+    pr = W.small_ball(3, 12, 2, seed=9)
+    ctx = gplib.setup_problem(pr, precision=0)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    y_host = gplib.gp_apply_host(ctx, x)
+    y_dev = _apply(gplib, cuda, ctx, x, 0)
+    assert np.array_equal(y_host, y_dev)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched(gplib, cuda, prec):
+    probs = [W.small_ball(3, 10, 2, seed=21), W.small_ball(3, 13, 4, seed=22),
+             W.small_ball(3, 8, 6, seed=23)]
+    nrhs = 2
+    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    xs = [W.x_vectors(p, c.n_active, nrhs) for p, c in zip(probs, ctxs)]
+    xd = [_dev(cuda, x.ravel(), prec) for x in xs]
+    yd = [cuda.full_like(a, float("nan")) for a in xd]
+    gplib.gp_apply_batched(ctxs, nrhs, xd, yd)
+    cuda.cuda.synchronize()
+    for p, c, x, y in zip(probs, ctxs, xs, yd):
+        o = Oracle(p)
+        yy = y.double().cpu().numpy().reshape(nrhs, -1)
+        for r in range(nrhs):
+            _close(yy[r], o.apply(_ref_input(x[r], prec)), prec)
+
+
+def test_argument_errors(gplib, cuda):
+    pr = W.small_ball(2, 8, 2)
+    ctx = gplib.setup_problem(pr, precision=0)
+    xd = cuda.zeros(ctx.n_active, dtype=cuda.float64, device="cuda")
+    assert gplib.lib.gp_apply(ctx.handle, xd.data_ptr(), xd.data_ptr(), None) == gplib.GP_EINVAL
+    assert gplib.lib.gp_apply(ctx.handle, None, xd.data_ptr(), None) == gplib.GP_EINVAL
+    with pytest.raises(gplib.GpError):
+        gplib.gp_apply(ctx, xd.float(), xd)
+
+
+def _sampled(gplib, cuda, pr, prec, nsample=3000):
+    o = Oracle(pr)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    assert (ctx.n_active, ctx.n_faces) == (o.n_active, o.n_faces)
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    y = _apply(gplib, cuda, ctx, x, prec)
+    rng = np.random.default_rng(12)
+    touched = np.unique(o.patch_index(0)[rng.integers(0, o.faces[0].shape[0], 400)].ravel())
+    rows = np.unique(np.concatenate([rng.integers(0, ctx.n_active, nsample), touched]))
+    ref = o.apply_rows(_ref_input(x, prec), rows)
+    tol = TOL[prec]
+    scale = np.abs(ref).max()
+    assert np.abs(y[rows] - ref).max() <= tol * scale
+    assert np.all(np.isfinite(y))
+    return y
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ball_96_k4_sampled(gplib, cuda, prec):
+    _sampled(gplib, cuda, W.ball_3d_sweep(4), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gyroid_128_k4_sampled(gplib, cuda, prec):
+    _sampled(gplib, cuda, W.gyroid_3d(), prec)
