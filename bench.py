@@ -120,6 +120,34 @@ def _flops_paper(d, k, nf):
     return 2.0 * nf * ((k + 1) ** (d - 1) * (2 * k + 1) ** 2 + (d - 1) * (k + 1) ** d * (2 * k + 1))
 
 
+WORKLOADS = {
+    "ball64_k3": lambda W: W.ball_3d(),
+    "disc32_k2": lambda W: W.disc_2d(),
+    "gyroid128_k4": lambda W: W.gyroid_3d(),
+    **{f"ball96_k{k}": (lambda W, k=k: W.ball_3d_sweep(k)) for k in range(1, 9)},
+}
+
+
+def run_profile(args):
+    """A few untimed applies of one workload and precision: the command ncu captures."""
+    import torch
+
+    from paper_2503_00246_gb300 import build as B
+    B.build()
+    from paper_2503_00246_gb300 import gp, workloads as W
+    pr = WORKLOADS[args.workload](W)
+    prec = gp.GP_FP64 if args.precision in ("fp64", "both") else gp.GP_FP32
+    ctx = gp.setup_problem(pr, precision=prec, device=0)
+    tdt = torch.float64 if prec == gp.GP_FP64 else torch.float32
+    x = torch.tensor(W.x_vectors(pr, ctx.n_active)[0], dtype=tdt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.reps):
+        gp.gp_apply(ctx, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "n_active": ctx.n_active,
+                      "n_faces": ctx.n_faces, "n_touched": ctx.n_touched, "applies": args.reps}))
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -369,8 +397,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--workload", default="ball64_k3", choices=sorted(WORKLOADS))
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "profile":
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

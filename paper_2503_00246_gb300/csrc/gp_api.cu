@@ -13,12 +13,11 @@ struct gp_ctx {
   int device = -1;
   bool on_device = false;
   size_t elem = 8;
-  int32_t* d_rowtab = nullptr;
-  int32_t* d_fcell = nullptr;
-  int32_t* d_face_of = nullptr;
-  int4* d_segs = nullptr;
-  int2* d_tiles = nullptr;
-  void* d_tp = nullptr;          // per-face scaled jumps (scratch)
+  int32_t* d_frows = nullptr;
+  int32_t* d_lwin = nullptr;
+  int32_t* d_lrow = nullptr;
+  int2* d_zruns = nullptr;
+  void* d_tp = nullptr;          // per-face outputs W_F (scratch)
   void* d_xh = nullptr;          // gp_apply_host staging
   void* d_yh = nullptr;
   std::string err;
@@ -62,13 +61,12 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_device(gp_ctx* c) {
-  void* ptrs[] = {c->d_rowtab, c->d_fcell, c->d_face_of, c->d_segs, c->d_tiles,
-                  c->d_tp, c->d_xh, c->d_yh};
+  void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow,
+                  c->d_zruns, c->d_tp, c->d_xh, c->d_yh};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  c->d_rowtab = c->d_fcell = c->d_face_of = nullptr;
-  c->d_segs = nullptr;
-  c->d_tiles = nullptr;
+  c->d_frows = c->d_lwin = c->d_lrow = nullptr;
+  c->d_zruns = nullptr;
   c->d_tp = c->d_xh = c->d_yh = nullptr;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
@@ -91,16 +89,15 @@ gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st) {
   a.y = y;
   a.tp = c->d_tp;
   a.add = add;
-  a.rowtab = c->d_rowtab;
-  a.fcell = c->d_fcell;
+  a.frows = c->d_frows;
+  for (int i = 0; i < 4; ++i) a.rbase[i] = p.rbase[i];
   for (int i = 0; i < 4; ++i) a.fstart[i] = p.fstart[i];
-  a.la.segs = c->d_segs;
-  a.la.tiles = c->d_tiles;
-  a.la.face_of = c->d_face_of;
-  a.la.n = p.n;
-  a.la.nl = p.nl;
-  a.la.ncell = p.ncell;
-  a.ntiles = add ? p.ntiles_touched : p.ntiles_all;
+  a.la.lwin = c->d_lwin;
+  a.la.lrow = c->d_lrow;
+  a.la.nlift = (int32_t)p.num_lift_cells();
+  a.la.n_active = (int32_t)p.n_active;
+  a.zruns = c->d_zruns;
+  a.nzruns = add ? 0 : (int32_t)p.num_zero_runs();
   a.g = p.jumps.data();
   a.m = p.mass.data();
   a.s = p.scale.data();
@@ -172,16 +169,13 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     DeviceGuard g(opts->device);
     cudaError_t e = g.ok ? cudaSuccess : cudaErrorInvalidDevice;
     const gp::Plan& p = c->plan;
-    std::vector<int4> segs(p.segs.size() / 4);
-    std::memcpy(segs.data(), p.segs.data(), p.segs.size() * sizeof(int32_t));
-    std::vector<int2> tiles(p.tiles.size() / 2);
-    std::memcpy(tiles.data(), p.tiles.data(), p.tiles.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = upload(&c->d_rowtab, p.rowtab);
-    if (e == cudaSuccess) e = upload(&c->d_fcell, p.face_inv);
-    if (e == cudaSuccess) e = upload(&c->d_face_of, p.face_of);
-    if (e == cudaSuccess) e = upload(&c->d_segs, segs);
-    if (e == cudaSuccess) e = upload(&c->d_tiles, tiles);
-    const size_t tp_bytes = (size_t)p.num_faces() * p.L * p.k * c->elem;
+    std::vector<int2> zruns(p.zruns.size() / 2);
+    std::memcpy(zruns.data(), p.zruns.data(), p.zruns.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = upload(&c->d_frows, p.frows);
+    if (e == cudaSuccess) e = upload(&c->d_lwin, p.lwin);
+    if (e == cudaSuccess) e = upload(&c->d_lrow, p.lrow);
+    if (e == cudaSuccess) e = upload(&c->d_zruns, zruns);
+    const size_t tp_bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * c->elem;  // face outputs W_F
     if (e == cudaSuccess && tp_bytes > 0) e = cudaMalloc(&c->d_tp, tp_bytes);
     if (e != cudaSuccess) {
       std::string m = std::string("device setup: ") + cudaGetErrorString(e);

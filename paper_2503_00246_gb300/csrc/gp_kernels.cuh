@@ -1,18 +1,18 @@
 // Face kernels of the ghost-penalty operator y = G x on sm_103a.
 //
 // Per face F with normal axis a (Sec. 2.4), G_F = h^{d-2} (M^ x ... x G^) with
-// G^ = sum_j c_j g_j g_j^T of rank k.  The apply is split as G = J^T W J:
+// G^ = sum_j c_j g_j g_j^T of rank k.  The face kernel computes the face output
 //
-//   jump kernel (J, then W):  t_F[j, tau] = g_j . x_F(:, tau)            normal lines
-//                             T_F[tau, j] = s_j (M^ x M^) t_F[j, .]      tangential mass
-//   lift kernel (J^T):        y_I = sum_{F contains I} sum_j g_j[b_F(I)] T_F[tau_F(I), j]
+//   t_F[j, tau] = g_j . x_F(:, tau)                    normal lines (k jump values)
+//   T_F[tau, j] = s_j (M^ x M^) t_F[j, .]              tangential reference masses
+//   W_F[b, tau] = sum_j g_j[b] T_F[tau, j]             normal expansion
 //
-// which reorders the three-step face apply of Sec. 2.5.1 (normal G, then the
-// two tangential masses) so the normal contraction acts through the k jump
-// vectors on both sides of the tangential step.  The lift is a gather: every
-// active DoF is written by exactly one thread, which sums the contributions of
-// the faces that contain it in a fixed order.  No atomics, bitwise
-// reproducible, and the zero fill of y for the overwrite form rides along.
+// i.e. the three-step face apply of Sec. 2.5.1 with the normal step split in
+// two around the tangential masses (G^ has rank k), and stores W_F in the
+// patch's lexicographic order.  The lift kernel then adds, for every touched
+// DoF, the W_F entries of the faces that contain it in a fixed order: a
+// gather, so no atomics and bitwise reproducible.  For the overwrite form,
+// extra CTAs of the face launch write the zeros of the untouched active DoFs.
 #pragma once
 
 #include <cstdint>
@@ -26,7 +26,50 @@ struct Shape {
   static constexpr int NN = 2 * K + 1;                               // nodes on a normal line
   static constexpr int FB = (256 / L) > 0 ? (256 / L) : 1;           // faces per CTA
   static constexpr int NT = FB * L;                                  // threads per CTA
+  // a row T_F[tau][0..k-1] is padded to KP values so it moves as 16-byte vectors
+  static constexpr int KP = (K <= 2) ? K : ((K <= 4) ? 4 : 8);
 };
+
+// Row of KP values at src (16-byte aligned when KP >= 4; 8-byte when KP == 2).
+template <typename T, int KP>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&v)[KP]) {
+  if constexpr (sizeof(T) == 4 && KP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < KP / 4; ++i) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(src) + i);
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && KP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < KP / 2; ++i) {
+      const double2 q = __ldg(reinterpret_cast<const double2*>(src) + i);
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && KP == 2) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(src));
+    v[0] = q.x; v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < KP; ++i) v[i] = __ldg(src + i);
+  }
+}
+
+template <typename T, int KP>
+__device__ __forceinline__ void store_row(T* __restrict__ dst, const T (&v)[KP]) {
+  if constexpr (sizeof(T) == 4 && KP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < KP / 4; ++i)
+      reinterpret_cast<float4*>(dst)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if constexpr (sizeof(T) == 8 && KP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < KP / 2; ++i) reinterpret_cast<double2*>(dst)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  } else if constexpr (sizeof(T) == 4 && KP == 2) {
+    reinterpret_cast<float2*>(dst)[0] = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < KP; ++i) dst[i] = v[i];
+  }
+}
 
 // Kernel constants (passed by value; they sit in the constant bank).
 template <typename T, int K>
@@ -37,231 +80,318 @@ struct Consts {
 };
 
 struct FaceArgs {
-  const int32_t* rowtab;  // [ninv][L] compact index of each x-row start of a cell
-  const int32_t* fcell;   // [nf][2] involved-cell index of K-, K+
+  const int32_t* frows;   // per-face row starts of the patch (see rbase)
+  int64_t rbase[4];       // first row entry of each axis' faces
   int32_t fstart[4];      // first face of each axis; fstart[D] = nf
-  int32_t bstart[4];      // first CTA of each axis; bstart[D] = grid size
+  int32_t bstart[4];      // first CTA of each axis (after the zero-fill CTAs); bstart[D] = grid
+  const int2* zruns;      // (c0, len <= 256) runs of untouched active DoFs
+  int32_t nzruns;         // 0 for the add form
+  int32_t nzblocks;       // zero-fill CTAs at the front of the grid
 };
 
+constexpr int ZGROUP = 16;  // zero runs per zero-fill CTA
+
+
 struct LiftArgs {
-  const int4* segs;       // (c0, X0, row, len | touched << 16)
-  const int2* tiles;      // (first segment, count), <= 256 nodes each
-  const int32_t* face_of; // [D][ncell] face id or -1
-  int32_t n;              // cells per axis
-  int32_t nl;             // lattice nodes per axis
-  int64_t ncell;
+  const int32_t* lwin;    // [nlift][NW] candidate face ids of each owner cell (-1 if none)
+  const int32_t* lrow;    // [KR][nlift] compact index of node (ci k, cj k + q, cl k + r)
+  int32_t nlift;
+  int32_t n_active;
 };
 
 // ----------------------------------------------------------------- jump --
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(Shape<D, K>::NT)
-jump_kernel(const T* __restrict__ x, T* __restrict__ tp, const FaceArgs fa,
+jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, const FaceArgs fa,
             const __grid_constant__ Consts<T, K> c) {
   using S = Shape<D, K>;
   constexpr int L = S::L, FB = S::FB, NN = S::NN, K1 = K + 1;
   __shared__ T buf[FB][K][L];
 
-  // axis of this CTA's faces (constant indices only: no local-memory copy of fa)
   const int blk = blockIdx.x;
+  if (blk < fa.nzblocks) {
+    // zero fill of the active DoFs outside every face patch (overwrite form only):
+    // ZGROUP runs of <= 256 elements, descriptors fetched in parallel
+    __shared__ int2 zr[ZGROUP];
+    const int r0 = blk * ZGROUP;
+    const int nr = min(ZGROUP, fa.nzruns - r0);
+    if ((int)threadIdx.x < nr) zr[threadIdx.x] = __ldg(fa.zruns + r0 + threadIdx.x);
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+      const int2 run = zr[r];
+      for (int i = threadIdx.x; i < run.y; i += S::NT) y[run.x + i] = T(0);
+    }
+    return;
+  }
+  // axis of this CTA's faces (constant indices only: no local-memory copy of fa)
   int axis = 0, fbase = fa.fstart[0], fend = fa.fstart[1], bbase = fa.bstart[0];
-  if (D >= 2 && blk >= fa.bstart[1]) { axis = 1; fbase = fa.fstart[1]; fend = fa.fstart[2]; bbase = fa.bstart[1]; }
-  if (D >= 3 && blk >= fa.bstart[2]) { axis = 2; fbase = fa.fstart[2]; fend = fa.fstart[3]; bbase = fa.bstart[2]; }
+  int64_t rbase = fa.rbase[0];
+  if (D >= 2 && blk >= fa.bstart[1]) {
+    axis = 1; fbase = fa.fstart[1]; fend = fa.fstart[2]; bbase = fa.bstart[1]; rbase = fa.rbase[1];
+  }
+  if (D >= 3 && blk >= fa.bstart[2]) {
+    axis = 2; fbase = fa.fstart[2]; fend = fa.fstart[3]; bbase = fa.bstart[2]; rbase = fa.rbase[2];
+  }
   const int f0 = fbase + (blk - bbase) * FB;
   const int t = threadIdx.x;
   const int fl = t / L, tau = t - fl * L;
   const int f = f0 + fl;
+  const bool valid = f < fend;
+  __shared__ T sm[K1][K1];
+  __shared__ T sb2[(D == 3) ? FB : 1][K][L];
+  for (int i = t; i < K1 * K1; i += S::NT) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
 
-  // ---- normal lines: gather 2k+1 values, contract with the k jump vectors
-  if (f < fend) {
-    const int lo = __ldg(fa.fcell + 2 * f), hi = __ldg(fa.fcell + 2 * f + 1);
-    const int32_t* rlo = fa.rowtab + (size_t)lo * L;
-    const int32_t* rhi = fa.rowtab + (size_t)hi * L;
-    T v[NN];
+  // ---- gather this thread's normal line (2k+1 values)
+  T v[NN];
+  if (valid) {
     if (axis == 0) {
-      const int32_t base = __ldg(rlo + tau);
+      const int32_t base = __ldg(fa.frows + rbase + (int64_t)(f - fbase) * L + tau);
 #pragma unroll
       for (int b = 0; b < NN; ++b) v[b] = __ldg(x + base + b);
     } else {
-      // tau = tx + (K+1) tr; the normal index b selects the row of K- (b <= k) or K+ (b > k)
+      // tau = tx + (K+1) tr; row b of the patch at outer tangential index tr
+      constexpr int R = (D == 3) ? NN * K1 : NN;
       const int tx = (D == 3) ? tau % K1 : tau;
       const int tr = (D == 3) ? tau / K1 : 0;
-      const int rstride = (D == 3 && axis == 2) ? K1 : 1;
-      const int roff = (D == 3) ? ((axis == 1) ? K1 * tr : tr) : 0;
+      const int32_t* rows = fa.frows + rbase + (int64_t)(f - fbase) * R + NN * tr;
 #pragma unroll
-      for (int b = 0; b < NN; ++b) {
-        const int32_t* rt = (b <= K) ? rlo : rhi;
-        const int bc = (b <= K) ? b : b - K;
-        v[b] = __ldg(x + __ldg(rt + roff + rstride * bc) + tx);
-      }
+      for (int b = 0; b < NN; ++b) v[b] = __ldg(x + __ldg(rows + b) + tx);
     }
+  } else {
+#pragma unroll
+    for (int b = 0; b < NN; ++b) v[b] = T(0);
+  }
+  // ---- contract with the k jump vectors
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < NN; ++b) acc = fma(c.g[j][b], v[b], acc);
+    buf[fl][j][tau] = acc;
+  }
+  __syncthreads();
+
+  // ---- tangential reference masses: tau = t1 + (k+1) t2, each thread keeps its rows of M^
+  T out[K];
+  if constexpr (D == 3) {
+    const int t1 = tau % K1, t2 = tau / K1;
+    T m1[K1];
+#pragma unroll
+    for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int b = 0; b < NN; ++b) acc = fma(c.g[j][b], v[b], acc);
-      buf[fl][j][tau] = acc;
-    }
-  }
-  __syncthreads();
-
-  // ---- tangential reference masses, one 1D line per thread
-  if constexpr (D == 3) {
-    constexpr int NL = FB * K * K1;
-    // along the first tangential index: lines (fl, j, t2)
-    for (int ln = t; ln < NL; ln += S::NT) {
-      const int ff = ln / (K * K1), rem = ln - ff * (K * K1);
-      const int j = rem / K1, t2 = rem - j * K1;
-      T u[K1];
-#pragma unroll
-      for (int q = 0; q < K1; ++q) u[q] = buf[ff][j][q + K1 * t2];
-#pragma unroll
-      for (int p = 0; p < K1; ++p) {
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < K1; ++q) acc = fma(c.m[p][q], u[q], acc);
-        buf[ff][j][p + K1 * t2] = acc;
-      }
+      for (int q = 0; q < K1; ++q) acc = fma(m1[q], buf[fl][j][q + K1 * t2], acc);
+      sb2[fl][j][tau] = acc;
     }
     __syncthreads();
-    // along the second tangential index: lines (fl, j, t1)
-    for (int ln = t; ln < NL; ln += S::NT) {
-      const int ff = ln / (K * K1), rem = ln - ff * (K * K1);
-      const int j = rem / K1, t1 = rem - j * K1;
-      T u[K1];
 #pragma unroll
-      for (int q = 0; q < K1; ++q) u[q] = buf[ff][j][t1 + K1 * q];
+    for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
 #pragma unroll
-      for (int p = 0; p < K1; ++p) {
-        T acc = T(0);
+    for (int j = 0; j < K; ++j) {
+      T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < K1; ++q) acc = fma(c.m[p][q], u[q], acc);
-        buf[ff][j][t1 + K1 * p] = acc;
-      }
+      for (int q = 0; q < K1; ++q) acc = fma(m1[q], sb2[fl][j][t1 + K1 * q], acc);
+      out[j] = acc;
     }
-    __syncthreads();
   } else {
-    constexpr int NL = FB * K;
-    for (int ln = t; ln < NL; ln += S::NT) {
-      const int ff = ln / K, j = ln - ff * K;
-      T u[K1];
+    T m1[K1];
 #pragma unroll
-      for (int q = 0; q < K1; ++q) u[q] = buf[ff][j][q];
+    for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
 #pragma unroll
-      for (int p = 0; p < K1; ++p) {
-        T acc = T(0);
+    for (int j = 0; j < K; ++j) {
+      T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < K1; ++q) acc = fma(c.m[p][q], u[q], acc);
-        buf[ff][j][p] = acc;
-      }
+      for (int q = 0; q < K1; ++q) acc = fma(m1[q], buf[fl][j][q], acc);
+      out[j] = acc;
     }
-    __syncthreads();
   }
 
-  // ---- scaled jumps T_F[tau][j], k contiguous values per thread
-  if (f < fend) {
-    T* out = tp + ((size_t)f * L + tau) * K;
+  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored in patch order
+  if (valid) {
+    T sj[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) out[j] = c.s[j] * buf[fl][j][tau];
+    for (int j = 0; j < K; ++j) sj[j] = c.s[j] * out[j];
+    constexpr int P = NN * L;
+    T* dst = tp + (size_t)f * P;
+    int pos0, pstride;
+    if (axis == 0) {            // patch index b + NN * tau
+      pos0 = NN * tau;
+      pstride = 1;
+    } else if (D == 2 || axis == 1) {
+      // 3D normal y: tx + K1 (b + NN tz); 2D normal y: tx + K1 b
+      const int tx = (D == 3) ? tau % K1 : tau;
+      const int tz = (D == 3) ? tau / K1 : 0;
+      pos0 = tx + K1 * NN * tz;
+      pstride = K1;
+    } else {                    // normal z: tx + K1 (ty + K1 b)
+      pos0 = tau;
+      pstride = K1 * K1;
+    }
+#pragma unroll
+    for (int b = 0; b < NN; ++b) {
+      T wv = T(0);
+#pragma unroll
+      for (int j = 0; j < K; ++j) wv = fma(c.g[j][b], sj[j], wv);
+      dst[pos0 + pstride * b] = wv;
+    }
   }
 }
 
 // ----------------------------------------------------------------- lift --
-template <int D, int K, typename T>
-__global__ void __launch_bounds__(256)
-lift_kernel(const T* __restrict__ tp, T* __restrict__ y, const int add, const LiftArgs la,
-            const __grid_constant__ Consts<T, K> c) {
-  constexpr int L = Shape<D, K>::L, K1 = K + 1;
-  __shared__ int4 sseg[256];
-  __shared__ int spre[257];
-  const int2 tile = la.tiles[blockIdx.x];
-  const int ns = tile.y;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) sseg[i] = la.segs[tile.x + i];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    // exclusive prefix of segment lengths (one warp, ns <= 256)
-    int carry = 0;
-    for (int base = 0; base < ns; base += 32) {
-      const int i = base + threadIdx.x;
-      int v = (i < ns) ? (sseg[i].w & 0xffff) : 0;
-      int incl = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)threadIdx.x >= o) incl += u;
-      }
-      if (i < ns) spre[i] = carry + incl - v;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (threadIdx.x == 0) spre[ns] = carry;
+// Owner cell c = (ci, cj, cl) holds the lattice nodes (ci k + p, cj k + q, cl k + r),
+// p, q, r in [0, k).  The faces with normal a whose patch holds such a node have
+// lower cell c + (s_a - 2) e_a + (s_1 - 1) e_t1 + (s_2 - 1) e_t2 with s_a in {0,1,2}
+// (0 only when p_a = 0) and s_t in {0,1} (0 only when p_t = 0); the node sits at
+// normal index b = p_a + (2 - s_a) k and tangential index tau_t = p_t + (1 - s_t) k.
+//
+// One thread takes one x-row (q, r) of an owner cell: its k nodes p = 0..k-1 are
+// contiguous in y.  The row type (q == 0, r == 0) fixes at compile time which of
+// the 36 candidate faces can reach the row (p = 0 is the only node on the lower x
+// face).  For normal x the k outputs come from one row of T_F with compile-time
+// jump coefficients; for normal y / z from k consecutive rows.  Each node sums its
+// contributions in the fixed order (axis, s_a, s_1, s_2, j): bitwise reproducible.
+// The host sorts owner cells by candidate-face pattern; a CTA walks row types in
+// order so a warp mostly holds one row type of same-pattern cells.
+template <int D, int K>
+struct LiftShape {
+  static constexpr int KR = (D == 3) ? K * K : K;   // x-rows per owner cell
+  static constexpr int CB0 = 256 / KR;
+  static constexpr int CB = CB0 < 1 ? 1 : CB0;      // owner cells per CTA
+  static constexpr int NT = 256;
+  static constexpr int NW = (D == 3) ? 36 : 12;     // candidate faces per cell
+  static constexpr int NTYPE = (D == 3) ? 4 : 2;
+  // rows of type m (bit 0: q == 0, bit 1: r == 0)
+  __host__ __device__ static constexpr int count(int m) {
+    int c = 1;
+    for (int i = 0; i < D - 1; ++i)
+      if (!((m >> i) & 1)) c *= (K - 1);
+    return c;
   }
-  __syncthreads();
-  const int t = threadIdx.x;
-  if (t >= spre[ns]) return;
-  int lo = 0, hi = ns - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (spre[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  const int4 s = sseg[lo];
-  const int o = t - spre[lo];
-  const int ci = s.x + o;
-  if (((s.w >> 16) & 1) == 0) {  // DoF outside every face patch
-    y[ci] = T(0);
-    return;
-  }
-  int P[3];
-  P[0] = s.y + o;
-  if (D == 3) {
-    P[1] = s.z % la.nl;
-    P[2] = s.z / la.nl;
-  } else {
-    P[1] = s.z;
-    P[2] = 0;
-  }
-  const int n = la.n;
-  T acc = T(0);
+};
+
+// FP32: branch-free over the candidate faces (a missing face reads face 0 and adds
+// zeros), so all loads of the row are in flight at once.  FP64: the adds of a
+// missing face are skipped, because FP64 issue is the scarce resource here.
+template <int D, int K, typename T, int M>
+__device__ __forceinline__ void lift_row(const T* __restrict__ wp, const int* win, const int q, const int r,
+                                         T (&acc)[K], unsigned& found) {
+  constexpr int K1 = K + 1, NN = 2 * K + 1;
+  constexpr int P = NN * Shape<D, K>::L;
+  constexpr bool SKIP = sizeof(T) == 8;
+  constexpr bool QZ = (M & 1) != 0;   // q == 0
+  constexpr bool RZ = (M & 2) != 0;   // r == 0 (3D)
+  constexpr unsigned ALL = (1u << K) - 1u;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int t1 = (a == 0) ? 1 : 0;
-    const int t2 = (a == 2) ? 1 : 2;
-    // faces with normal a whose patch holds this node: lower cell ia with
-    // ia*k <= P[a] <= ia*k + 2k, tangential cells it with it*k <= P[t] <= it*k + k
-    const int ca = P[a] / K, pa = P[a] - ca * K;
-    const int ia0 = (pa == 0) ? ca - 2 : ca - 1;
-    const int c1 = P[t1] / K, p1 = P[t1] - c1 * K;
-    const int j10 = (p1 == 0) ? c1 - 1 : c1;
-    int j20 = 0, j21 = 0, c2 = 0;
-    if (D == 3) {
-      c2 = P[t2] / K;
-      const int p2 = P[t2] - c2 * K;
-      j20 = (p2 == 0) ? c2 - 1 : c2;
-      j21 = c2;
-    }
-    for (int ia = ia0; ia <= ca; ++ia) {
-      if (ia < 0 || ia > n - 2) continue;
-      const int b = P[a] - ia * K;
-      for (int i1 = j10; i1 <= c1; ++i1) {
-        if (i1 < 0 || i1 > n - 1) continue;
-        const int tau1 = P[t1] - i1 * K;
-        for (int i2 = j20; i2 <= j21; ++i2) {
-          if (D == 3 && (i2 < 0 || i2 > n - 1)) continue;
-          const int tau2 = (D == 3) ? P[t2] - i2 * K : 0;
-          int cc[3];
-          cc[a] = ia;
-          cc[t1] = i1;
-          if (D == 3) cc[t2] = i2;
-          int64_t lin = cc[0] + (int64_t)n * cc[1];
-          if (D == 3) lin += (int64_t)n * n * cc[2];
-          const int f = __ldg(la.face_of + a * la.ncell + lin);
-          if (f < 0) continue;
-          const T* src = tp + ((size_t)f * L + tau1 + K1 * tau2) * K;
+    // zero-ness of the normal coordinate and of the two tangential coordinates
+    const bool nz = (a == 0) ? true : ((a == 1) ? QZ : RZ);
+    const bool xz = (a == 0) ? QZ : true;         // first tangential: y (a = 0) or x
+    const bool yz = (a == 0) ? RZ : ((a == 1) ? RZ : QZ);
 #pragma unroll
-          for (int j = 0; j < K; ++j) acc = fma(c.g[j][b], __ldg(src + j), acc);
+    for (int sa = 0; sa < 3; ++sa) {
+      if (a != 0 && sa == 0 && !nz) continue;
+#pragma unroll
+      for (int s1 = 0; s1 < 2; ++s1) {
+        if (s1 == 0 && !xz) continue;
+#pragma unroll
+        for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
+          if (D == 3 && s2 == 0 && !yz) continue;
+          const int w = (D == 3) ? a * 12 + sa * 4 + s1 * 2 + s2 : a * 6 + sa * 2 + s1;
+          const int f = win[w];
+          const bool ok = f >= 0;
+          if (SKIP && !ok) continue;
+          const T* src = wp + (size_t)(ok ? f : 0) * P;
+          // patch position of node p and how many of the row's nodes the face reaches
+          int pos, cnt;
+          if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face
+            const int tq = q + (1 - s1) * K;
+            const int tr = (D == 3) ? r + (1 - s2) * K : 0;
+            pos = (2 - sa) * K + NN * (tq + K1 * tr);
+            cnt = (sa == 0) ? 1 : K;
+          } else if (a == 1) {      // x index p + (1 - s1) k, normal b = q + (2 - s_a) k
+            const int bb = q + (2 - sa) * K;
+            const int tz = (D == 3) ? r + (1 - s2) * K : 0;
+            pos = (1 - s1) * K + K1 * (bb + NN * tz);
+            cnt = (s1 == 0) ? 1 : K;
+          } else {                  // normal z: x index p + (1 - s1) k, y index q + (1 - s2) k
+            const int ty = q + (1 - s2) * K;
+            const int bb = r + (2 - sa) * K;
+            pos = (1 - s1) * K + K1 * (ty + K1 * bb);
+            cnt = (s1 == 0) ? 1 : K;
+          }
+          if (!ok) pos = 0;
+#pragma unroll
+          for (int p = 0; p < K; ++p) {
+            if (p < cnt) {
+              const T v = __ldg(src + pos + p);
+              acc[p] += (SKIP || ok) ? v : T(0);
+            }
+          }
+          if (ok) found |= (cnt == 1) ? 1u : ALL;
         }
       }
     }
   }
-  y[ci] = add ? y[ci] + acc : acc;
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256)
+lift_kernel(const T* __restrict__ tp, T* __restrict__ y, const int add, const LiftArgs la,
+            const __grid_constant__ Consts<T, K> c) {
+  using S = LiftShape<D, K>;
+  constexpr int NW = S::NW, CB = S::CB;
+  __shared__ int win[CB][NW + 1];
+  const int cell0 = blockIdx.x * CB;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < NW * CB; idx += S::NT) {
+    const int ln = idx / NW, w = idx - ln * NW;
+    win[ln][w] = (cell0 + ln < la.nlift) ? __ldg(la.lwin + (size_t)cell0 * NW + idx) : -1;
+  }
+  __syncthreads();
+  // one pass: item -> (row type m, cell, row of that type); items sorted by type
+  constexpr int E1 = CB * S::count(0);
+  constexpr int E2 = E1 + CB * S::count(1);
+  constexpr int E3 = E2 + CB * S::count(2);
+  constexpr int ITEMS = CB * S::KR;
+  for (int g = t; g < ITEMS; g += S::NT) {
+    int m, local;
+    if (g < E1) { m = 0; local = g; }
+    else if (g < E2 || S::NTYPE == 2) { m = 1; local = g - E1; }
+    else if (g < E3) { m = 2; local = g - E2; }
+    else { m = 3; local = g - E3; }
+    const int cnt = S::count(m);
+    const int ci = local / cnt;
+    int rem = local - ci * cnt;
+    const int cell = cell0 + ci;
+    if (cell >= la.nlift) continue;
+    int q = 0, r = 0;
+    if constexpr (K > 1) {
+      if (!(m & 1)) { q = 1 + rem % (K - 1); rem /= (K - 1); }
+      if (D == 3 && !(m & 2)) { r = 1 + rem % (K - 1); }
+    }
+    const int row = q + (D == 3 ? K * r : 0);
+    const int base = __ldg(la.lrow + (size_t)row * la.nlift + cell);
+    T acc[K];
+#pragma unroll
+    for (int p = 0; p < K; ++p) acc[p] = T(0);
+    unsigned found = 0;
+    switch (m) {
+      case 0: lift_row<D, K, T, 0>(tp, win[ci], q, r, acc, found); break;
+      case 1: lift_row<D, K, T, 1>(tp, win[ci], q, r, acc, found); break;
+      case 2: lift_row<D, K, T, 2>(tp, win[ci], q, r, acc, found); break;
+      default: lift_row<D, K, T, 3>(tp, win[ci], q, r, acc, found); break;
+    }
+    if (base < 0) continue;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      if (!((found >> p) & 1u)) continue;
+      const int idx = base + p;
+      if (idx >= la.n_active) continue;
+      y[idx] = add ? y[idx] + acc[p] : acc[p];
+    }
+  }
 }
 
 }  // namespace gp

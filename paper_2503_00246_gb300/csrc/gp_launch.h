@@ -14,11 +14,12 @@ struct ApplyArgs {
   void* y = nullptr;         // device, n_active elements
   void* tp = nullptr;        // device scratch, nf * L * k elements
   int add = 0;               // 0: y = Gx, 1: y += Gx
-  const int32_t* rowtab = nullptr;
-  const int32_t* fcell = nullptr;
+  const int32_t* frows = nullptr;
+  int64_t rbase[4] = {0, 0, 0, 0};
   int32_t fstart[4] = {0, 0, 0, 0};
   LiftArgs la{};
-  int32_t ntiles = 0;        // lift CTAs to launch
+  const int2* zruns = nullptr;
+  int32_t nzruns = 0;        // zero runs to fill (0 for the add form)
   const double* g = nullptr; // host FP64: k x (2k+1)
   const double* m = nullptr; // host FP64: (k+1)^2
   const double* s = nullptr; // host FP64: k
@@ -41,21 +42,28 @@ cudaError_t run_apply(const ApplyArgs& A, cudaStream_t st) {
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = (T)A.m[p * (K + 1) + q];
   for (int j = 0; j < K; ++j) c.s[j] = (T)A.s[j];
   FaceArgs fa;
-  fa.rowtab = A.rowtab;
-  fa.fcell = A.fcell;
-  int32_t nb = 0;
+  fa.frows = A.frows;
+  for (int a = 0; a < 4; ++a) fa.rbase[a] = A.rbase[a];
+  fa.zruns = A.zruns;
+  fa.nzruns = A.nzruns;
+  fa.nzblocks = (A.nzruns + ZGROUP - 1) / ZGROUP;
+  int32_t nb = fa.nzblocks;
   for (int a = 0; a < 4; ++a) fa.fstart[a] = A.fstart[a];
   for (int a = 0; a < D; ++a) {
     fa.bstart[a] = nb;
     nb += (A.fstart[a + 1] - A.fstart[a] + S::FB - 1) / S::FB;
   }
   for (int a = D; a < 4; ++a) fa.bstart[a] = nb;
+  const int32_t nblk = nb;
+  const bool faces = A.fstart[D] > 0;
+  using LS = LiftShape<D, K>;
+  const int32_t nlb = (A.la.nlift + LS::CB - 1) / LS::CB;
   if (A.ev) cudaEventRecord(A.ev[0], st);
-  if (nb > 0)
-    jump_kernel<D, K, T><<<nb, S::NT, 0, st>>>((const T*)A.x, (T*)A.tp, fa, c);
+  if (nblk > 0)
+    jump_kernel<D, K, T><<<nblk, S::NT, 0, st>>>((const T*)A.x, (T*)A.tp, (T*)A.y, fa, c);
   if (A.ev) cudaEventRecord(A.ev[1], st);
-  if (A.ntiles > 0)
-    lift_kernel<D, K, T><<<A.ntiles, 256, 0, st>>>((const T*)A.tp, (T*)A.y, A.add, A.la, c);
+  if (nlb > 0 && faces)
+    lift_kernel<D, K, T><<<nlb, LS::NT, 0, st>>>((const T*)A.tp, (T*)A.y, A.add, A.la, c);
   if (A.ev) cudaEventRecord(A.ev[2], st);
   return cudaGetLastError();
 }

@@ -9,7 +9,7 @@
 //    scaling), computed here with a collocation differentiation matrix;
 //  * tables for the kernels: per involved cell the compact index of each of
 //    its x-rows, per face its two cells, per (axis, cell) the face id, and
-//    the lift segments/tiles over the active DoFs.
+//    the lift owner cells and the zero runs of the active DoFs.
 //
 // Compile with -ffp-contract=off: the classification must round exactly as
 // written so that every implementation of the same rule agrees cell by cell.
@@ -453,22 +453,43 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
     }
   }
 
-  // ---- lift segments: active runs split into touched / untouched pieces
-  std::vector<int32_t> seg_t, seg_z;
+  // ---- per-face row starts (the gather reads them with one coalesced load per face)
+  {
+    const int K1 = k + 1, NN = 2 * k + 1;
+    const int R0 = L, R1 = d == 3 ? NN * K1 : NN;
+    int64_t off = 0;
+    for (int a = 0; a < d; ++a) {
+      p.rbase[a] = off;
+      off += (int64_t)(p.fstart[a + 1] - p.fstart[a]) * (a == 0 ? R0 : R1);
+    }
+    for (int a = d; a < 4; ++a) p.rbase[a] = off;
+    p.frows.assign(off, 0);
+    for (int a = 0; a < d; ++a)
+      for (int64_t f = p.fstart[a]; f < p.fstart[a + 1]; ++f) {
+        const int32_t* rlo = &p.rowtab[(size_t)p.face_inv[2 * f] * L];
+        const int32_t* rhi = &p.rowtab[(size_t)p.face_inv[2 * f + 1] * L];
+        if (a == 0) {
+          int32_t* dst = &p.frows[p.rbase[0] + (f - p.fstart[0]) * R0];
+          for (int t = 0; t < L; ++t) dst[t] = rlo[t];
+        } else {
+          int32_t* dst = &p.frows[p.rbase[a] + (f - p.fstart[a]) * R1];
+          const int outer = d == 3 ? K1 : 1;
+          for (int tr = 0; tr < outer; ++tr)
+            for (int b = 0; b < NN; ++b) {
+              const int32_t* rt = b <= k ? rlo : rhi;
+              const int bc = b <= k ? b : b - k;
+              // a = 1: rows (b, tz) -> b + K1 tz ; a = 2: rows (ty, b) -> ty + K1 b
+              const int ri = d == 2 ? bc : (a == 1 ? bc + K1 * tr : tr + K1 * bc);
+              dst[b + NN * tr] = rt[ri];
+            }
+        }
+      }
+  }
+
+  // ---- touched DoFs (nodes of involved cells) and the zero runs (active, untouched)
   std::vector<int> trun;
   int64_t touched = 0;
-  auto emit = [&](std::vector<int32_t>& dst, int64_t c0, int X0, int64_t row, int len, int flag) {
-    while (len > 0) {
-      int l = std::min(len, SEG_MAX);
-      dst.push_back((int32_t)c0);
-      dst.push_back(X0);
-      dst.push_back((int32_t)row);
-      dst.push_back(l | (flag << 16));
-      c0 += l;
-      X0 += l;
-      len -= l;
-    }
-  };
+  p.zruns.clear();
   for (int64_t row = 0; row < p.nrows; ++row) {
     if (p.run_off[row] == p.run_off[row + 1]) continue;
     row_runs(p, involved, row, trun);
@@ -478,47 +499,121 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
       int X = p.runs[2 * r], X1 = p.runs[2 * r + 1];
       while (X <= X1) {
         while (tr < trun.size() && trun[tr + 1] < X) tr += 2;
+        int e;
         if (tr < trun.size() && trun[tr] <= X) {
-          int e = std::min(X1, trun[tr + 1]);
-          emit(seg_t, c, X, row, e - X + 1, 1);
+          e = std::min(X1, trun[tr + 1]);
           touched += e - X + 1;
-          c += e - X + 1;
-          X = e + 1;
         } else {
-          int e = (tr < trun.size()) ? std::min(X1, trun[tr] - 1) : X1;
-          emit(seg_z, c, X, row, e - X + 1, 0);
-          c += e - X + 1;
-          X = e + 1;
+          e = (tr < trun.size()) ? std::min(X1, trun[tr] - 1) : X1;
+          int64_t c0 = c;
+          int len = e - X + 1;
+          // extend the previous run when contiguous in compact order, then split at ZRUN_MAX
+          while (len > 0) {
+            if (!p.zruns.empty() && (int64_t)p.zruns[p.zruns.size() - 2] + p.zruns.back() == c0 &&
+                p.zruns.back() < ZRUN_MAX) {
+              int l = std::min(len, ZRUN_MAX - p.zruns.back());
+              p.zruns.back() += l;
+              c0 += l;
+              len -= l;
+            } else {
+              int l = std::min(len, ZRUN_MAX);
+              p.zruns.push_back((int32_t)c0);
+              p.zruns.push_back(l);
+              c0 += l;
+              len -= l;
+            }
+          }
         }
+        c += e - X + 1;
+        X = e + 1;
       }
     }
   }
   p.n_touched = touched;
-  p.segs = seg_t;
-  const int32_t nseg_t = (int32_t)(seg_t.size() / 4);
-  p.segs.insert(p.segs.end(), seg_z.begin(), seg_z.end());
-  const int32_t nseg = (int32_t)(p.segs.size() / 4);
-  p.tiles.clear();
-  auto pack = [&](int32_t s0, int32_t s1) {
-    int32_t first = s0, cnt = 0, nodes = 0;
-    for (int32_t s = s0; s < s1; ++s) {
-      int len = p.segs[4 * s + 3] & 0xffff;
-      if (nodes + len > TILE_NODES) {
-        p.tiles.push_back(first);
-        p.tiles.push_back(cnt);
-        first = s;
-        cnt = 0;
-        nodes = 0;
-      }
-      cnt++;
-      nodes += len;
+  // ---- lift cells: owners floor(X/k) of the touched nodes, coordinates in [0, n]
+  {
+    const int n1 = n + 1;
+    const int64_t nown = ipow(n1, d);
+    std::vector<uint8_t> own(nown, 0);
+    for (int64_t i = 0; i < ninv; ++i) {
+      int64_t c = p.inv_cells[i];
+      int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+      for (int dz = 0; dz <= (d == 3 ? 1 : 0); ++dz)
+        for (int dy = 0; dy <= 1; ++dy)
+          for (int dx = 0; dx <= 1; ++dx)
+            own[(ci + dx) + (int64_t)n1 * ((cj + dy) + (int64_t)n1 * (cl + dz))] = 1;
     }
-    if (cnt > 0) { p.tiles.push_back(first); p.tiles.push_back(cnt); }
-  };
-  pack(0, nseg_t);
-  p.ntiles_touched = (int32_t)(p.tiles.size() / 2);
-  pack(nseg_t, nseg);
-  p.ntiles_all = (int32_t)(p.tiles.size() / 2);
+    // candidate-face pattern of an owner cell c: bit (a, s_a, s_1, s_2) set when the face with
+    // normal a and lower cell c + (s_a-2) e_a + (s_1-1) e_t1 + (s_2-1) e_t2 exists
+    const int nw = d == 3 ? 12 : 6;
+    p.lwin_width = d * nw;
+    auto window = [&](const int co0[3], int32_t* out) {
+      for (int a = 0; a < d; ++a) {
+        const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+        for (int w = 0; w < nw; ++w) {
+          int sa = d == 3 ? w / 4 : w / 2, s1 = d == 3 ? (w % 4) / 2 : w % 2, s2 = d == 3 ? w % 2 : 1;
+          int co[3] = {co0[0], co0[1], co0[2]};
+          co[a] += sa - 2;
+          co[t1] += s1 - 1;
+          if (d == 3) co[t2] += s2 - 1;
+          bool ok = co[a] >= 0 && co[a] <= n - 2 && co[t1] >= 0 && co[t1] <= n - 1;
+          if (d == 3) ok = ok && co[t2] >= 0 && co[t2] <= n - 1;
+          int32_t f = -1;
+          if (ok) {
+            int64_t lin = co[0] + (int64_t)n * co[1] + (d == 3 ? (int64_t)n * n * co[2] : 0);
+            f = p.face_of[(size_t)a * p.ncell + lin];
+          }
+          out[a * nw + w] = f;
+        }
+      }
+    };
+    auto pattern = [&](const int co0[3]) -> uint64_t {
+      int32_t win[36];
+      window(co0, win);
+      uint64_t m = 0;
+      for (int i = 0; i < d * nw; ++i)
+        if (win[i] >= 0) m |= (uint64_t)1 << i;
+      return m;
+    };
+    std::vector<std::pair<uint64_t, int64_t>> order;
+    for (int64_t o = 0; o < nown; ++o) {
+      if (!own[o]) continue;
+      int co[3] = {(int)(o % n1), (int)((o / n1) % n1), d == 3 ? (int)(o / ((int64_t)n1 * n1)) : 0};
+      order.emplace_back(pattern(co), o);
+    }
+    // FP64: same-pattern cells share a warp, so the lift issues (almost) only useful
+    // FP64 work.  FP32: keep the lexicographic order, so a warp's loads and stores
+    // stay in neighbouring memory (FP32 issue is cheap on this GPU).
+    if (opts->precision == GP_FP64)
+      std::stable_sort(order.begin(), order.end(),
+                       [](const std::pair<uint64_t, int64_t>& x, const std::pair<uint64_t, int64_t>& y) {
+                         return x.first < y.first;
+                       });
+    const int KR = (int)ipow(k, d - 1);   // rows q (, r) in [0, k) of an owner cell
+    const int64_t nlift = (int64_t)order.size();
+    p.lcell.assign(4 * nlift, 0);
+    p.lrow.assign((size_t)KR * nlift, -1);
+    p.lwin.assign((size_t)p.lwin_width * nlift, -1);
+    for (int64_t i = 0; i < nlift; ++i) {
+      int64_t o = order[i].second;
+      int ci = (int)(o % n1), cj = (int)((o / n1) % n1), cl = d == 3 ? (int)(o / ((int64_t)n1 * n1)) : 0;
+      p.lcell[4 * i + 0] = ci;
+      p.lcell[4 * i + 1] = cj;
+      p.lcell[4 * i + 2] = cl;
+      const int co[3] = {ci, cj, cl};
+      window(co, &p.lwin[(size_t)p.lwin_width * i]);
+      for (int t = 0; t < KR; ++t) {
+        int q = t % k, r = t / k;
+        int Y = cj * k + q, Z = cl * k + r, X = ci * k;
+        int64_t cidx = -1;
+        if (Y < p.nl && (d == 2 || Z < p.nl) && X < p.nl) {
+          int64_t row = (int64_t)Y + (d == 3 ? (int64_t)p.nl * Z : 0);
+          cidx = p.compact(X, row);
+        }
+        p.lrow[(size_t)t * nlift + i] = (int32_t)cidx;
+      }
+    }
+  }
 
   // ---- 1D reference data and the per-order scale c_j h^(d-2)
   gauss_lobatto_01(k, p.gl);

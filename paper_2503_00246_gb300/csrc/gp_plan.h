@@ -11,8 +11,8 @@
 namespace gp {
 
 constexpr int KMAX = 8;
-constexpr int SEG_MAX = 64;      // nodes per lift segment
-constexpr int TILE_NODES = 256;  // nodes per lift tile (= threads of the lift kernel)
+constexpr int ZRUN_MAX = 256;       // elements per zero run (one CTA pass)
+constexpr int LIFT_CELLS = 32;      // owner cells per lift CTA (one per lane)
 
 enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
 
@@ -34,6 +34,10 @@ struct Plan {
   std::vector<int32_t> face_inv;  // 2 per face: involved-cell index of K-, K+
   std::vector<int64_t> inv_cells; // involved cells (sorted)
   std::vector<int32_t> rowtab;    // ninv x L: compact index of (ci*k, row tau) per involved cell
+  // per-face row starts of the patch: axis 0: L rows (one per normal line, 2k+1 long);
+  // axis a > 0: (2k+1)*(k+1)^(d-2) rows (normal index b, outer tangential index), k+1 long
+  std::vector<int32_t> frows;
+  int64_t rbase[4] = {0, 0, 0, 0};
   std::vector<int32_t> face_of;   // dim x ncell: face id of (axis, lower cell), -1 if none
 
   // active-DoF numbering: per lattice row, active x-runs and the compact start
@@ -42,10 +46,17 @@ struct Plan {
   std::vector<int32_t> run_off;   // nrows+1, offsets into runs
   std::vector<int32_t> runs;      // (X0, X1) inclusive pairs
 
-  // lift work: segments (c0, X0, row, len | touched<<16) and tiles (first, count)
-  std::vector<int32_t> segs;
-  std::vector<int32_t> tiles;
-  int32_t ntiles_touched = 0, ntiles_all = 0;
+  // lift work: owner cells (ci, cj, cl, 0) with coordinates in [0, n], sorted by the
+  // pattern of faces whose patch reaches them; lrow[row][cell] is the compact index of
+  // node (ci*k, cj*k+q, cl*k+r), row = q + k r, or -1 if that node is inactive
+  std::vector<int32_t> lcell;
+  std::vector<int32_t> lrow;
+  std::vector<int32_t> lwin;      // nlift x (3*12 | 2*6): candidate face ids (-1 if none)
+  int lwin_width = 0;
+  // zero fill of the active DoFs outside every face patch: runs (c0, len <= 256)
+  std::vector<int32_t> zruns;
+  int64_t num_lift_cells() const { return (int64_t)lcell.size() / 4; }
+  int64_t num_zero_runs() const { return (int64_t)zruns.size() / 2; }
 
   // FP64 1D reference data
   std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
