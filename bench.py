@@ -9,7 +9,8 @@ Sec. 3.1), whole job over all ranks.  The inputs (about 12 MB) fit in L2, so
 a 512 MB buffer is written between timed steps to flush it.
 
 Arms
-  default            the CUDA path through the C ABI (FP64 headline; FP32 beside it)
+  default            the CUDA path through the C ABI: FP64-accuracy headline (float-float
+                     arithmetic on FP64 data), native FP64 and FP32 beside it
   --impl reference   the CPU FP64 oracle timed on the host cores (bounded sample)
 
 Multi-GPU: one independent replica per rank (the single-problem apply does not
@@ -109,11 +110,13 @@ class Clocks:
 
 # ---------------------------------------------------------------- GPU arm --
 
-def _flops_jump(d, k, nf):
+def _flops_face(d, k, nf):
+    """Flops of the face kernel as written: per normal line k dot products of length 2k+1
+    (jumps), (d-1) tangential passes of k (k+1)-term dot products, k scalings, and the
+    (2k+1) k-term normal expansion."""
     L = (k + 1) ** (d - 1)
-    # normal jumps: k dot products of length 2k+1 per line; tangential masses: (d-1) passes of
-    # (k+1)x(k+1) on k*(k+1)^(d-2) lines per tangential direction
-    return 2.0 * nf * (k * (2 * k + 1) * L + (d - 1) * k * L * (k + 1))
+    per_line = k * (2 * k + 1) + (d - 1) * k * (k + 1) + k + (2 * k + 1) * k
+    return 2.0 * nf * L * per_line
 
 
 def _flops_paper(d, k, nf):
@@ -136,9 +139,9 @@ def run_profile(args):
     B.build()
     from paper_2503_00246_gb300 import gp, workloads as W
     pr = WORKLOADS[args.workload](W)
-    prec = gp.GP_FP64 if args.precision in ("fp64", "both") else gp.GP_FP32
+    prec = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF, "both": gp.GP_FP64_FF}[args.precision]
     ctx = gp.setup_problem(pr, precision=prec, device=0)
-    tdt = torch.float64 if prec == gp.GP_FP64 else torch.float32
+    tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     x = torch.tensor(W.x_vectors(pr, ctx.n_active)[0], dtype=tdt, device="cuda")
     y = torch.empty_like(x)
     for _ in range(args.reps):
@@ -169,14 +172,16 @@ def run_gpu(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
     fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    ff_peak = fp32_peak / 15.0
     clocks = Clocks(local)
 
     results = {}
-    for prec in ([gp.GP_FP64, gp.GP_FP32] if args.precision == "both" else
-                 [gp.GP_FP64 if args.precision == "fp64" else gp.GP_FP32]):
+    names = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF}
+    precs = ([gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32] if args.precision == "both" else [names[args.precision]])
+    for prec in precs:
         ctx = gp.setup_problem(pr, precision=prec, device=local)
-        w = 8 if prec == gp.GP_FP64 else 4
-        tdt = torch.float64 if prec == gp.GP_FP64 else torch.float32
+        w = 4 if prec == gp.GP_FP32 else 8
+        tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
         x_np = W.x_vectors(pr, ctx.n_active)[0]
         x = torch.tensor(x_np, dtype=tdt, device=dev)
         y = torch.empty_like(x)
@@ -188,7 +193,7 @@ def run_gpu(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         gp.gp_profile_enable(ctx, True)
-        if prec == gp.GP_FP64:
+        if prec == precs[0]:
             clocks.start()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -201,7 +206,7 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
         if ws > 1:
             dist.barrier()
-        ck = clocks.stop() if prec == gp.GP_FP64 else None
+        ck = clocks.stop() if prec == precs[0] else None
         ms_jump, ms_lift, calls = gp.gp_profile_read(ctx)
         gp.gp_profile_enable(ctx, False)
         t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps   # ms
@@ -231,15 +236,16 @@ def run_gpu(args):
         if args.check:
             from oracle.ghost_penalty import Oracle
             o = Oracle(pr)
-            ref = o.apply(x_np if prec == gp.GP_FP64 else x_np.astype(np.float32).astype(np.float64))
+            ref = o.apply(x_np if prec != gp.GP_FP32 else x_np.astype(np.float32).astype(np.float64))
             err = float(np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref))
-        flop_jump = _flops_jump(d, k, nf)
-        if prec == gp.GP_FP64:
-            roof = {"bound": "alu", "kernel": "jump_kernel<3,3,double>", "achieved": flop_jump / (jump_ms * 1e-3) / 1e12,
-                    "peak": fp64_peak, "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz"}
-        else:
-            roof = {"bound": "alu", "kernel": "jump_kernel<3,3,float>", "achieved": flop_jump / (jump_ms * 1e-3) / 1e12,
-                    "peak": fp32_peak, "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FFMA/clk x 2070 MHz"}
+        flop_face = _flops_face(d, k, nf)
+        kname = {gp.GP_FP64: "double", gp.GP_FP32: "float", gp.GP_FP64_FF: "ff64"}[prec]
+        roof = {"bound": "alu", "kernel": f"face_kernel<3,3,{kname}>",
+                "achieved": flop_face / (jump_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "peak": {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: ff_peak}[prec],
+                "peak_source": {gp.GP_FP64: "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz x 2 flop",
+                                gp.GP_FP32: "derived: 152 SM x 128 FP32 FMA/clk x 2070 MHz x 2 flop",
+                                gp.GP_FP64_FF: "derived: FP32 peak / 15 FP32 ops per float-float FMA"}[prec]}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
         alg_bytes = w * (ctx.n_touched + ctx.n_active)
@@ -262,8 +268,10 @@ def run_gpu(args):
         }
         ctx.close()
 
-    head = gp.GP_FP64 if gp.GP_FP64 in results else gp.GP_FP32
+    order = [p for p in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32) if p in results]
+    head = order[0]
     r = results[head]
+    dtypes = {gp.GP_FP64: "f64", gp.GP_FP32: "f32", gp.GP_FP64_FF: "ff64 (float-float arithmetic on f64 data)"}
     line = {
         "metric": METRIC,
         "value": r["value"],
@@ -275,7 +283,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if head == gp.GP_FP64 else "f32",
+        "dtype": dtypes[head],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_cells": 64 ** 3, "degree": 3, "n_active_dofs": r["n_active"],
                    "ghost_faces": r["n_faces"], "touched_dofs": r["n_touched"],
@@ -291,10 +299,11 @@ def run_gpu(args):
         "kernel_ms": r["kernel_ms"],
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
     }
-    if gp.GP_FP32 in results and head != gp.GP_FP32:
-        f = results[gp.GP_FP32]
-        line["fp32"] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
-                                             "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value")}
+    tags = {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff64"}
+    for p in order[1:]:
+        f = results[p]
+        line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
+                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -393,7 +402,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
-    ap.add_argument("--precision", default="both", choices=["fp64", "fp32", "both"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "fp32", "ff", "both"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")

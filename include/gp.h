@@ -21,7 +21,7 @@
  *     lexicographically with x fastest, then compacted
  *     (gp_active_dof_coords returns their coordinates).
  *   - x and y are caller-owned DEVICE pointers to contiguous arrays of
- *     n_active elements (double for GP_FP64, float for GP_FP32), on the
+ *     n_active elements (double for GP_FP64 and GP_FP64_FF, float for GP_FP32), on the
  *     device that was current during gp_setup.  x and y must not alias.
  *   - stream is a cudaStream_t (0 = legacy default stream).  Calls only
  *     enqueue work; they do not synchronise.
@@ -53,7 +53,12 @@ typedef enum {
   GP_EUNSUPPORTED = 5   /* valid request outside this build (e.g. k > 8) */
 } gp_status;
 
-enum { GP_FP64 = 0, GP_FP32 = 1 };
+/* Arithmetic of the operator.  GP_FP64: x, y double, FP64 arithmetic.
+ * GP_FP32: x, y float, FP32 arithmetic.  GP_FP64_FF: x, y double, computed in
+ * float-float pairs (hi + lo, about 2^-48 relative per operation) on the FP32
+ * pipes; entries of x must lie in the float exponent range (|x| below 2^-126
+ * reads as 0, at or above 2^128 as infinity). */
+enum { GP_FP64 = 0, GP_FP32 = 1, GP_FP64_FF = 2 };
 
 /* level-set kinds; phi > 0 inside the domain (Sec. 2) */
 enum {
@@ -93,7 +98,7 @@ typedef struct {
   int nweights;             /* 0, or k: per-order weights c_1..c_k */
   const double* weights;    /* NULL -> c_j = gamma for every order j */
   double gamma;             /* default weight */
-  int precision;            /* GP_FP64 or GP_FP32 */
+  int precision;            /* GP_FP64, GP_FP32 or GP_FP64_FF */
   int all_faces;            /* 1: penalise every interior face of the active mesh */
   int device;               /* CUDA device ordinal; -1 = build the host plan only */
 } gp_opts;

@@ -116,6 +116,8 @@ gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st) {
   cudaError_t e;
   if (p.precision == GP_FP64)
     e = p.dim == 2 ? gp::apply_f64_d2(a, st) : gp::apply_f64_d3(a, st);
+  else if (p.precision == GP_FP64_FF)
+    e = p.dim == 2 ? gp::apply_ff_d2(a, st) : gp::apply_ff_d3(a, st);
   else
     e = p.dim == 2 ? gp::apply_f32_d2(a, st) : gp::apply_f32_d3(a, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -154,7 +156,7 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     delete c;
     return fail(nullptr, GP_ENOMEM, "host allocation failed while building the plan");
   }
-  c->elem = c->plan.precision == GP_FP64 ? 8 : 4;
+  c->elem = c->plan.precision == GP_FP32 ? 4 : 8;   // element size of x and y
   c->device = opts->device;
   if (opts->device >= 0) {
     int ndev = 0;
@@ -175,7 +177,9 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     if (e == cudaSuccess) e = upload(&c->d_lwin, p.lwin);
     if (e == cudaSuccess) e = upload(&c->d_lrow, p.lrow);
     if (e == cudaSuccess) e = upload(&c->d_zruns, zruns);
-    const size_t tp_bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * c->elem;  // face outputs W_F
+    // face outputs W_F: float, double, or a (hi, lo) float pair per value
+    const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
+    const size_t tp_bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
     if (e == cudaSuccess && tp_bytes > 0) e = cudaMalloc(&c->d_tp, tp_bytes);
     if (e != cudaSuccess) {
       std::string m = std::string("device setup: ") + cudaGetErrorString(e);

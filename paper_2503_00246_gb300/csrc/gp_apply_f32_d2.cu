@@ -1,6 +1,6 @@
-// Instantiations of the face kernels for float, dimension 2, degrees 1..8.
+// Instantiations of the face kernels: FP32, dimension 2, degrees 1..8.
 #include "gp_launch.h"
 
 namespace gp {
-cudaError_t apply_f32_d2(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(2, float, a, st) }
+cudaError_t apply_f32_d2(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(2, ArF32, a, st) }
 }  // namespace gp

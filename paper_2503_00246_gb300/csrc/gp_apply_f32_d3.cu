@@ -1,6 +1,6 @@
-// Instantiations of the face kernels for float, dimension 3, degrees 1..8.
+// Instantiations of the face kernels: FP32, dimension 3, degrees 1..8.
 #include "gp_launch.h"
 
 namespace gp {
-cudaError_t apply_f32_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, float, a, st) }
+cudaError_t apply_f32_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArF32, a, st) }
 }  // namespace gp

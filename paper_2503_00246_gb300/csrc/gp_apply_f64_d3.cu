@@ -1,6 +1,6 @@
-// Instantiations of the face kernels for double, dimension 3, degrees 1..8.
+// Instantiations of the face kernels: FP64, dimension 3, degrees 1..8.
 #include "gp_launch.h"
 
 namespace gp {
-cudaError_t apply_f64_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, double, a, st) }
+cudaError_t apply_f64_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArF64, a, st) }
 }  // namespace gp

@@ -1,0 +1,6 @@
+// Instantiations of the face kernels: float-float on FP64 data, dimension 2, degrees 1..8.
+#include "gp_launch.h"
+
+namespace gp {
+cudaError_t apply_ff_d2(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(2, ArFF, a, st) }
+}  // namespace gp

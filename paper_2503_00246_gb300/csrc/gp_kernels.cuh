@@ -13,10 +13,16 @@
 // DoF, the W_F entries of the faces that contain it in a fixed order: a
 // gather, so no atomics and bitwise reproducible.  For the overwrite form,
 // extra CTAs of the face launch write the zeros of the untouched active DoFs.
+//
+// Template parameter A (gp_arith.cuh) picks the arithmetic: FP32, FP64, or
+// float-float on FP64 data.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
+
+#include "gp_arith.cuh"
 
 namespace gp {
 
@@ -24,59 +30,17 @@ template <int D, int K>
 struct Shape {
   static constexpr int L = (D == 2) ? (K + 1) : (K + 1) * (K + 1);  // tangential nodes per face
   static constexpr int NN = 2 * K + 1;                               // nodes on a normal line
+  static constexpr int P = NN * L;                                   // patch nodes per face
   static constexpr int FB = (256 / L) > 0 ? (256 / L) : 1;           // faces per CTA
   static constexpr int NT = FB * L;                                  // threads per CTA
-  // a row T_F[tau][0..k-1] is padded to KP values so it moves as 16-byte vectors
-  static constexpr int KP = (K <= 2) ? K : ((K <= 4) ? 4 : 8);
 };
 
-// Row of KP values at src (16-byte aligned when KP >= 4; 8-byte when KP == 2).
-template <typename T, int KP>
-__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&v)[KP]) {
-  if constexpr (sizeof(T) == 4 && KP % 4 == 0) {
-#pragma unroll
-    for (int i = 0; i < KP / 4; ++i) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(src) + i);
-      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
-    }
-  } else if constexpr (sizeof(T) == 8 && KP % 2 == 0) {
-#pragma unroll
-    for (int i = 0; i < KP / 2; ++i) {
-      const double2 q = __ldg(reinterpret_cast<const double2*>(src) + i);
-      v[2 * i] = q.x; v[2 * i + 1] = q.y;
-    }
-  } else if constexpr (sizeof(T) == 4 && KP == 2) {
-    const float2 q = __ldg(reinterpret_cast<const float2*>(src));
-    v[0] = q.x; v[1] = q.y;
-  } else {
-#pragma unroll
-    for (int i = 0; i < KP; ++i) v[i] = __ldg(src + i);
-  }
-}
-
-template <typename T, int KP>
-__device__ __forceinline__ void store_row(T* __restrict__ dst, const T (&v)[KP]) {
-  if constexpr (sizeof(T) == 4 && KP % 4 == 0) {
-#pragma unroll
-    for (int i = 0; i < KP / 4; ++i)
-      reinterpret_cast<float4*>(dst)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-  } else if constexpr (sizeof(T) == 8 && KP % 2 == 0) {
-#pragma unroll
-    for (int i = 0; i < KP / 2; ++i) reinterpret_cast<double2*>(dst)[i] = make_double2(v[2 * i], v[2 * i + 1]);
-  } else if constexpr (sizeof(T) == 4 && KP == 2) {
-    reinterpret_cast<float2*>(dst)[0] = make_float2(v[0], v[1]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < KP; ++i) dst[i] = v[i];
-  }
-}
-
 // Kernel constants (passed by value; they sit in the constant bank).
-template <typename T, int K>
+template <typename V, int K>
 struct Consts {
-  T g[K][2 * K + 1];  // jump of the j-th derivative of patch basis b (row j-1)
-  T m[K + 1][K + 1];  // reference mass matrix
-  T s[K];             // c_j h^{d-2}
+  V g[K][2 * K + 1];  // jump of the j-th derivative of patch basis b (row j-1)
+  V m[K + 1][K + 1];  // reference mass matrix
+  V s[K];             // c_j h^{d-2}
 };
 
 struct FaceArgs {
@@ -91,7 +55,6 @@ struct FaceArgs {
 
 constexpr int ZGROUP = 16;  // zero runs per zero-fill CTA
 
-
 struct LiftArgs {
   const int32_t* lwin;    // [nlift][NW] candidate face ids of each owner cell (-1 if none)
   const int32_t* lrow;    // [KR][nlift] compact index of node (ci k, cj k + q, cl k + r)
@@ -99,14 +62,20 @@ struct LiftArgs {
   int32_t n_active;
 };
 
-// ----------------------------------------------------------------- jump --
-template <int D, int K, typename T>
+// ----------------------------------------------------------------- face --
+// One thread per (face, normal line tau); FB faces per CTA.
+template <int D, int K, class A>
 __global__ void __launch_bounds__(Shape<D, K>::NT)
-jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, const FaceArgs fa,
-            const __grid_constant__ Consts<T, K> c) {
+face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
+            typename A::IO* __restrict__ y, const FaceArgs fa,
+            const __grid_constant__ Consts<typename A::V, K> c) {
   using S = Shape<D, K>;
+  using V = typename A::V;
+  using IO = typename A::IO;
   constexpr int L = S::L, FB = S::FB, NN = S::NN, K1 = K + 1;
-  __shared__ T buf[FB][K][L];
+  __shared__ V buf[FB][K][L];
+  __shared__ V sb2[(D == 3) ? FB : 1][K][L];
+  __shared__ V sm[K1][K1];
 
   const int blk = blockIdx.x;
   if (blk < fa.nzblocks) {
@@ -119,7 +88,7 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
       const int2 run = zr[r];
-      for (int i = threadIdx.x; i < run.y; i += S::NT) y[run.x + i] = T(0);
+      for (int i = threadIdx.x; i < run.y; i += S::NT) y[run.x + i] = IO(0);
     }
     return;
   }
@@ -137,17 +106,15 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
   const int fl = t / L, tau = t - fl * L;
   const int f = f0 + fl;
   const bool valid = f < fend;
-  __shared__ T sm[K1][K1];
-  __shared__ T sb2[(D == 3) ? FB : 1][K][L];
   for (int i = t; i < K1 * K1; i += S::NT) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
 
   // ---- gather this thread's normal line (2k+1 values)
-  T v[NN];
+  V v[NN];
   if (valid) {
     if (axis == 0) {
       const int32_t base = __ldg(fa.frows + rbase + (int64_t)(f - fbase) * L + tau);
 #pragma unroll
-      for (int b = 0; b < NN; ++b) v[b] = __ldg(x + base + b);
+      for (int b = 0; b < NN; ++b) v[b] = from_io(__ldg(x + base + b), (V*)nullptr);
     } else {
       // tau = tx + (K+1) tr; row b of the patch at outer tangential index tr
       constexpr int R = (D == 3) ? NN * K1 : NN;
@@ -155,34 +122,34 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
       const int tr = (D == 3) ? tau / K1 : 0;
       const int32_t* rows = fa.frows + rbase + (int64_t)(f - fbase) * R + NN * tr;
 #pragma unroll
-      for (int b = 0; b < NN; ++b) v[b] = __ldg(x + __ldg(rows + b) + tx);
+      for (int b = 0; b < NN; ++b) v[b] = from_io(__ldg(x + __ldg(rows + b) + tx), (V*)nullptr);
     }
   } else {
 #pragma unroll
-    for (int b = 0; b < NN; ++b) v[b] = T(0);
+    for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
   }
   // ---- contract with the k jump vectors
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    T acc = T(0);
+    V acc = vzero<V>();
 #pragma unroll
-    for (int b = 0; b < NN; ++b) acc = fma(c.g[j][b], v[b], acc);
+    for (int b = 0; b < NN; ++b) acc = vfma(c.g[j][b], v[b], acc);
     buf[fl][j][tau] = acc;
   }
   __syncthreads();
 
   // ---- tangential reference masses: tau = t1 + (k+1) t2, each thread keeps its rows of M^
-  T out[K];
+  V out[K];
   if constexpr (D == 3) {
     const int t1 = tau % K1, t2 = tau / K1;
-    T m1[K1];
+    V m1[K1];
 #pragma unroll
     for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      T acc = T(0);
+      V acc = vzero<V>();
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = fma(m1[q], buf[fl][j][q + K1 * t2], acc);
+      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], buf[fl][j][q + K1 * t2], acc);
       sb2[fl][j][tau] = acc;
     }
     __syncthreads();
@@ -190,31 +157,30 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
     for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      T acc = T(0);
+      V acc = vzero<V>();
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = fma(m1[q], sb2[fl][j][t1 + K1 * q], acc);
+      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], sb2[fl][j][t1 + K1 * q], acc);
       out[j] = acc;
     }
   } else {
-    T m1[K1];
+    V m1[K1];
 #pragma unroll
     for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      T acc = T(0);
+      V acc = vzero<V>();
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = fma(m1[q], buf[fl][j][q], acc);
+      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], buf[fl][j][q], acc);
       out[j] = acc;
     }
   }
 
   // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored in patch order
   if (valid) {
-    T sj[K];
+    V sj[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) sj[j] = c.s[j] * out[j];
-    constexpr int P = NN * L;
-    T* dst = tp + (size_t)f * P;
+    for (int j = 0; j < K; ++j) sj[j] = vfma(c.s[j], out[j], vzero<V>());
+    V* dst = wp + (size_t)f * S::P;
     int pos0, pstride;
     if (axis == 0) {            // patch index b + NN * tau
       pos0 = NN * tau;
@@ -231,9 +197,9 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
     }
 #pragma unroll
     for (int b = 0; b < NN; ++b) {
-      T wv = T(0);
+      V wv = vzero<V>();
 #pragma unroll
-      for (int j = 0; j < K; ++j) wv = fma(c.g[j][b], sj[j], wv);
+      for (int j = 0; j < K; ++j) wv = vfma(c.g[j][b], sj[j], wv);
       dst[pos0 + pstride * b] = wv;
     }
   }
@@ -247,13 +213,10 @@ jump_kernel(const T* __restrict__ x, T* __restrict__ tp, T* __restrict__ y, cons
 // normal index b = p_a + (2 - s_a) k and tangential index tau_t = p_t + (1 - s_t) k.
 //
 // One thread takes one x-row (q, r) of an owner cell: its k nodes p = 0..k-1 are
-// contiguous in y.  The row type (q == 0, r == 0) fixes at compile time which of
-// the 36 candidate faces can reach the row (p = 0 is the only node on the lower x
-// face).  For normal x the k outputs come from one row of T_F with compile-time
-// jump coefficients; for normal y / z from k consecutive rows.  Each node sums its
-// contributions in the fixed order (axis, s_a, s_1, s_2, j): bitwise reproducible.
-// The host sorts owner cells by candidate-face pattern; a CTA walks row types in
-// order so a warp mostly holds one row type of same-pattern cells.
+// contiguous in y and read contiguous entries of each face output.  The row type
+// (q == 0, r == 0) fixes at compile time which of the 36 candidate faces can reach
+// the row (p = 0 is the only node on the lower x face).  Each node sums its
+// contributions in the fixed order (axis, s_a, s_1, s_2): bitwise reproducible.
 template <int D, int K>
 struct LiftShape {
   static constexpr int KR = (D == 3) ? K * K : K;   // x-rows per owner cell
@@ -271,15 +234,18 @@ struct LiftShape {
   }
 };
 
-// FP32: branch-free over the candidate faces (a missing face reads face 0 and adds
-// zeros), so all loads of the row are in flight at once.  FP64: the adds of a
-// missing face are skipped, because FP64 issue is the scarce resource here.
-template <int D, int K, typename T, int M>
-__device__ __forceinline__ void lift_row(const T* __restrict__ wp, const int* win, const int q, const int r,
-                                         T (&acc)[K], unsigned& found) {
+// Native FP64: the adds of a missing face are skipped (FP64 issue is the scarce
+// resource on GB300; the host groups owner cells with the same candidate-face
+// pattern so that the skips are warp-uniform).  FP32 and float-float: branch-free
+// (a missing face reads face 0 and adds zeros), so all loads of the row are in
+// flight at once.
+template <int D, int K, class A, int M>
+__device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, const int* win, const int q,
+                                         const int r, typename A::V (&acc)[K], unsigned& found) {
+  using V = typename A::V;
   constexpr int K1 = K + 1, NN = 2 * K + 1;
-  constexpr int P = NN * Shape<D, K>::L;
-  constexpr bool SKIP = sizeof(T) == 8;
+  constexpr int P = Shape<D, K>::P;
+  constexpr bool SKIP = std::is_same<V, double>::value;
   constexpr bool QZ = (M & 1) != 0;   // q == 0
   constexpr bool RZ = (M & 2) != 0;   // r == 0 (3D)
   constexpr unsigned ALL = (1u << K) - 1u;
@@ -302,7 +268,7 @@ __device__ __forceinline__ void lift_row(const T* __restrict__ wp, const int* wi
           const int f = win[w];
           const bool ok = f >= 0;
           if (SKIP && !ok) continue;
-          const T* src = wp + (size_t)(ok ? f : 0) * P;
+          const V* src = wp + (size_t)(ok ? f : 0) * P;
           // patch position of node p and how many of the row's nodes the face reaches
           int pos, cnt;
           if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face
@@ -325,8 +291,8 @@ __device__ __forceinline__ void lift_row(const T* __restrict__ wp, const int* wi
 #pragma unroll
           for (int p = 0; p < K; ++p) {
             if (p < cnt) {
-              const T v = __ldg(src + pos + p);
-              acc[p] += (SKIP || ok) ? v : T(0);
+              const V v = src[pos + p];
+              acc[p] = vadd(acc[p], (SKIP || ok) ? v : vzero<V>());
             }
           }
           if (ok) found |= (cnt == 1) ? 1u : ALL;
@@ -336,11 +302,13 @@ __device__ __forceinline__ void lift_row(const T* __restrict__ wp, const int* wi
   }
 }
 
-template <int D, int K, typename T>
+template <int D, int K, class A>
 __global__ void __launch_bounds__(256)
-lift_kernel(const T* __restrict__ tp, T* __restrict__ y, const int add, const LiftArgs la,
-            const __grid_constant__ Consts<T, K> c) {
+lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
+            const LiftArgs la) {
   using S = LiftShape<D, K>;
+  using V = typename A::V;
+  using IO = typename A::IO;
   constexpr int NW = S::NW, CB = S::CB;
   __shared__ int win[CB][NW + 1];
   const int cell0 = blockIdx.x * CB;
@@ -373,15 +341,15 @@ lift_kernel(const T* __restrict__ tp, T* __restrict__ y, const int add, const Li
     }
     const int row = q + (D == 3 ? K * r : 0);
     const int base = __ldg(la.lrow + (size_t)row * la.nlift + cell);
-    T acc[K];
+    V acc[K];
 #pragma unroll
-    for (int p = 0; p < K; ++p) acc[p] = T(0);
+    for (int p = 0; p < K; ++p) acc[p] = vzero<V>();
     unsigned found = 0;
     switch (m) {
-      case 0: lift_row<D, K, T, 0>(tp, win[ci], q, r, acc, found); break;
-      case 1: lift_row<D, K, T, 1>(tp, win[ci], q, r, acc, found); break;
-      case 2: lift_row<D, K, T, 2>(tp, win[ci], q, r, acc, found); break;
-      default: lift_row<D, K, T, 3>(tp, win[ci], q, r, acc, found); break;
+      case 0: lift_row<D, K, A, 0>(wp, win[ci], q, r, acc, found); break;
+      case 1: lift_row<D, K, A, 1>(wp, win[ci], q, r, acc, found); break;
+      case 2: lift_row<D, K, A, 2>(wp, win[ci], q, r, acc, found); break;
+      default: lift_row<D, K, A, 3>(wp, win[ci], q, r, acc, found); break;
     }
     if (base < 0) continue;
 #pragma unroll
@@ -389,7 +357,8 @@ lift_kernel(const T* __restrict__ tp, T* __restrict__ y, const int add, const Li
       if (!((found >> p) & 1u)) continue;
       const int idx = base + p;
       if (idx >= la.n_active) continue;
-      y[idx] = add ? y[idx] + acc[p] : acc[p];
+      const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), acc[p]) : acc[p];
+      y[idx] = to_io(outv, (IO*)nullptr);
     }
   }
 }

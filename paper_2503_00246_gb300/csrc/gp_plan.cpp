@@ -322,7 +322,10 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
   const int k = opts->degree;
   if (k < 1) { err = "degree must be >= 1"; return GP_EINVAL; }
   if (k > KMAX) { err = "degree > 8 is not built"; return GP_EUNSUPPORTED; }
-  if (opts->precision != GP_FP64 && opts->precision != GP_FP32) { err = "bad precision"; return GP_EINVAL; }
+  if (opts->precision != GP_FP64 && opts->precision != GP_FP32 && opts->precision != GP_FP64_FF) {
+    err = "bad precision";
+    return GP_EINVAL;
+  }
   const int n = mesh->n[0];
   for (int a = 0; a < d; ++a) {
     if (mesh->n[a] != n) { err = "the mesh must have the same number of cells per axis"; return GP_EINVAL; }
@@ -582,8 +585,8 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
       order.emplace_back(pattern(co), o);
     }
     // FP64: same-pattern cells share a warp, so the lift issues (almost) only useful
-    // FP64 work.  FP32: keep the lexicographic order, so a warp's loads and stores
-    // stay in neighbouring memory (FP32 issue is cheap on this GPU).
+    // FP64 work.  FP32 and float-float: keep the lexicographic order, so a warp's loads
+    // and stores stay in neighbouring memory (FP32 issue is cheap on this GPU).
     if (opts->precision == GP_FP64)
       std::stable_sort(order.begin(), order.end(),
                        [](const std::pair<uint64_t, int64_t>& x, const std::pair<uint64_t, int64_t>& y) {

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgp.so")
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_EDEVICE, GP_EUNSUPPORTED = range(6)
-GP_FP64, GP_FP32 = 0, 1
+GP_FP64, GP_FP32, GP_FP64_FF = 0, 1, 2
 GP_LS_BALLS, GP_LS_GYROID, GP_LS_CALLBACK, GP_LS_CONST = 1, 2, 3, 4
 _STATUS = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ECUDA", 4: "GP_EDEVICE",
            5: "GP_EUNSUPPORTED"}
@@ -129,7 +129,7 @@ class Context:
 
     @property
     def dtype_np(self):
-        return np.float64 if self.precision == GP_FP64 else np.float32
+        return np.float32 if self.precision == GP_FP32 else np.float64
 
 
 def gp_setup(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts) -> Context:
@@ -161,7 +161,7 @@ def _check_vec(ctx, t, nrhs=1):
     if isinstance(t, int):
         return
     import torch
-    want = torch.float64 if ctx.precision == GP_FP64 else torch.float32
+    want = torch.float32 if ctx.precision == GP_FP32 else torch.float64
     if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != nrhs * ctx.n_active:
         raise GpError(GP_EINVAL, f"expected a contiguous CUDA {want} tensor of {nrhs * ctx.n_active} "
                                  f"elements, got {t.dtype} {tuple(t.shape)} on {t.device}")

@@ -3,6 +3,7 @@
 Tolerances (the operator's stated accuracy targets):
   FP64 path  ||y - y_ref|| / ||y_ref|| <= 1e-12 and |y_i - y_ref,i| <= 1e-12 ||y_ref||_inf
   FP32 path  ||y - y_ref|| / ||y_ref|| <= 1e-5  and |y_i - y_ref,i| <= 1e-5  ||y_ref||_inf
+  float-float path (FP64 data, FP32 pairs): the FP64 tolerances
 The FP32 path is compared with the oracle applied to x rounded to FP32, so the
 check measures the operator, not the rounding of its input.
 """
@@ -14,11 +15,12 @@ from paper_2503_00246_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5}
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-12}
+PRECS = [0, 1, 2]
 
 
 def _dev(torch, x, prec):
-    dt = torch.float64 if prec == 0 else torch.float32
+    dt = torch.float32 if prec == 1 else torch.float64
     return torch.tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
 
 
@@ -35,7 +37,7 @@ def _apply(gp, torch, ctx, x, prec, add_to=None):
 
 
 def _ref_input(x, prec):
-    return x if prec == 0 else x.astype(np.float32).astype(np.float64)
+    return x if prec != 1 else x.astype(np.float32).astype(np.float64)
 
 
 def _close(y, ref, prec):
@@ -50,7 +52,7 @@ SMALL = [(2, k, 16) for k in range(1, 9)] + [(3, k, 9) for k in range(1, 6)] + [
                                                                               (3, 8, 6)]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dim,k,n", SMALL)
 def test_small_meshes_all_degrees(gplib, cuda, dim, k, n, prec):
     pr = W.small_ball(dim, n, k, radius=0.62, seed=100 + 10 * dim + k)
@@ -62,7 +64,7 @@ def test_small_meshes_all_degrees(gplib, cuda, dim, k, n, prec):
     _close(y, o.apply(_ref_input(x, prec)), prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_paper_weights_and_multiple_balls(gplib, cuda, prec):
     pr = W.small_ball(3, 12, 4, seed=7, weights=W.paper_weights(0.5, 4))
     pr.centers = np.array([[-0.3, 0.1, 0.0], [0.35, -0.2, 0.1]])
@@ -73,7 +75,7 @@ def test_paper_weights_and_multiple_balls(gplib, cuda, prec):
     _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_disc_2d_k2(gplib, cuda, prec):
     pr = W.disc_2d()
     o = Oracle(pr)
@@ -82,7 +84,7 @@ def test_disc_2d_k2(gplib, cuda, prec):
     _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_ball_3d_k3_full(gplib, cuda, prec):
     """64^3 ball, k = 3: every output compared (the benchmark's launch configuration)."""
     pr = W.ball_3d()
@@ -90,20 +92,20 @@ def test_ball_3d_k3_full(gplib, cuda, prec):
     ctx = gplib.setup_problem(pr, precision=prec)
     x = W.x_vectors(pr, ctx.n_active)[0]
     _close(_apply(gplib, cuda, ctx, x, prec), o.apply(_ref_input(x, prec)), prec)
-    if prec == 0:
+    if prec != 1:
         # annihilation of a seeded global polynomial of degree <= k (||G|| from power iteration)
         ex, co = W.poly_coeffs(pr)
         xp = W.poly_eval(ex, co, gplib.gp_active_dof_coords(ctx))
         v = np.random.default_rng(0).standard_normal(ctx.n_active)
         for _ in range(30):
-            w = _apply(gplib, cuda, ctx, v, 0)
+            w = _apply(gplib, cuda, ctx, v, prec)
             gn = np.linalg.norm(w)
             v = w / gn
-        r = np.linalg.norm(_apply(gplib, cuda, ctx, xp, 0))
+        r = np.linalg.norm(_apply(gplib, cuda, ctx, xp, prec))
         assert r <= 1e-10 * gn * np.linalg.norm(xp), r / (gn * np.linalg.norm(xp))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_apply_add_and_determinism(gplib, cuda, prec):
     pr = W.small_ball(3, 16, 3, seed=8)
     o = Oracle(pr)
@@ -161,7 +163,7 @@ def test_host_buffers_end_to_end(gplib, cuda):
     assert np.array_equal(y_host, y_dev)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_batched(gplib, cuda, prec):
     probs = [W.small_ball(3, 10, 2, seed=21), W.small_ball(3, 13, 4, seed=22),
              W.small_ball(3, 8, 6, seed=23)]
@@ -206,11 +208,11 @@ def _sampled(gplib, cuda, pr, prec, nsample=3000):
     return y
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_ball_96_k4_sampled(gplib, cuda, prec):
     _sampled(gplib, cuda, W.ball_3d_sweep(4), prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
 def test_gyroid_128_k4_sampled(gplib, cuda, prec):
     _sampled(gplib, cuda, W.gyroid_3d(), prec)
