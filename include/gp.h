@@ -104,7 +104,7 @@ typedef struct {
 } gp_opts;
 
 /* Classify cells, collect the ghost faces, number the active DoFs, build the
- * 1D matrices in FP64 and upload the face tables (Sec. 2 / Sec. 2.4 / Sec. 2.6).
+ * 1D matrices in FP64 and upload the face tables (Sec. 2, Sec. 2.4, Sec. 2.7).
  * mesh, ls and opts are read during the call only.  *out receives a new
  * context owned by the caller (release with gp_destroy). */
 gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,

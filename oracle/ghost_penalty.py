@@ -104,7 +104,7 @@ class Oracle:
 
     def A(self, axis: int) -> np.ndarray:
         """One explicit face matrix per axis: on a uniform Cartesian mesh every
-        face of a given normal direction has the same matrix (Sec. 2.3)."""
+        face of a given normal direction has the same matrix (Sec. 2.2)."""
         if axis not in self._A:
             pr = self.pr
             self._A[axis] = face_matrix(pr.dim, pr.degree, pr.h, axis, pr.cweights())

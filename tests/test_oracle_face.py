@@ -110,7 +110,7 @@ def test_face_matrix_spsd_rank_translation(dim, k):
     assert ev.min() > -1e-12 * ev.max()
     # rank k (k+1)^(d-1): one jump per order j and tangential basis function
     assert int((ev > 1e-9 * ev.max()).sum()) == k * (k + 1) ** (dim - 1)
-    # the local matrix is the same on every face of a Cartesian mesh (Sec. 2.3)
+    # the local matrix is the same on every face of a Cartesian mesh (Sec. 2.2)
     B = face_matrix(dim, k, 1.0, 0, c, origin=np.array([3.0, -2.0, 5.0])[:dim])
     np.testing.assert_allclose(A, B, rtol=1e-9, atol=1e-9 * np.abs(A).max())
 
