@@ -142,6 +142,25 @@ gp_status gp_apply(gp_ctx* ctx, const void* x, void* y, void* stream);
 /* y += G x (only DoFs touched by a ghost face are read and written). */
 gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream);
 
+/* Allocation-free y = G x (no counterpart in the paper).  For callers that
+ * cannot allocate device memory when they apply the operator: code whose device
+ * memory is owned by another allocator (a framework pool that reserves the GPU
+ * up front), or latency-critical loops where a cudaMalloc/cudaFree pair would
+ * synchronise the device.  Same result as gp_apply, but the face outputs go to a
+ * fixed scratch array of GP_NOALLOC_SCRATCH_BYTES compiled into the library (every
+ * GPU that loads the library holds it until the process exits) instead of the
+ * context's buffer.  The call allocates nothing and records no trace events.
+ *   - The scratch must hold n_faces * (2k+1) * (k+1)^(d-1) values (4 bytes for
+ *     GP_FP32, 8 otherwise); larger problems get GP_EINVAL and a message.
+ *   - The first call on a device looks the array's device address up with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (every
+ *     value the operator reads is rewritten first, so nothing needs clearing);
+ *     calls whose kernels overlap on the GPU race on it.
+ * x, y, stream and errors as for gp_apply. */
+#define GP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream);
+
 /* End-to-end form with HOST buffers: copies x (n_active elements of the
  * context's precision) to the device, applies G, copies y back and waits
  * for completion.  Uses device buffers owned by the context. */

@@ -8,6 +8,11 @@
 #include "gp_launch.h"
 #include "gp_plan.h"
 
+namespace gp {
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(int device, void** out);
+}  // namespace gp
+
 struct gp_ctx {
   gp::Plan plan;
   int device = -1;
@@ -80,14 +85,17 @@ void free_device(gp_ctx* c) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                \
   } while (0)
 
-gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st) {
+// Scratch for the face outputs: the context's buffer unless `scratch` is given;
+// `trace` = false never creates events (used by the allocation-free entry point).
+gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
+                 bool trace = true) {
   const gp::Plan& p = c->plan;
   gp::ApplyArgs a;
   a.dim = p.dim;
   a.k = p.k;
   a.x = x;
   a.y = y;
-  a.tp = c->d_tp;
+  a.tp = scratch ? scratch : c->d_tp;
   a.add = add;
   a.frows = c->d_frows;
   for (int i = 0; i < 4; ++i) a.rbase[i] = p.rbase[i];
@@ -102,7 +110,7 @@ gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st) {
   a.m = p.mass.data();
   a.s = p.scale.data();
   cudaEvent_t* ev = nullptr;
-  if (c->prof) {
+  if (c->prof && trace) {
     const size_t need = 3 * (size_t)(c->nprof + 1);
     while (c->ev.size() < need) {
       cudaEvent_t e;
@@ -290,6 +298,27 @@ gp_status gp_apply(gp_ctx* ctx, const void* x, void* y, void* stream) {
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
   return launch(ctx, x, y, 0, (cudaStream_t)stream);
+}
+
+gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream) {
+  gp_status s = check_apply(ctx, x, y);
+  if (s != GP_OK) return s;
+  const gp::Plan& p = ctx->plan;
+  const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
+  const size_t need = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
+  if (need > gp::noalloc_scratch_bytes())
+    return fail(ctx, GP_EINVAL,
+                "gp_apply_noalloc: the face outputs need " + std::to_string(need) +
+                    " bytes, more than the fixed scratch of " + std::to_string(gp::noalloc_scratch_bytes()) +
+                    " bytes; use gp_apply");
+  if (p.n_active == 0) return GP_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
+  void* scratch = nullptr;
+  const cudaError_t e = gp::noalloc_scratch(ctx->device, &scratch);
+  if (e != cudaSuccess)
+    return fail(ctx, GP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  return launch(ctx, x, y, 0, (cudaStream_t)stream, scratch, false);
 }
 
 gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream) {

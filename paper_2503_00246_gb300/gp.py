@@ -70,6 +70,7 @@ def _load():
         "gp_reference_1d": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
         "gp_apply": ([P, P, P, P], C.c_int),
         "gp_apply_add": ([P, P, P, P], C.c_int),
+        "gp_apply_noalloc": ([P, P, P, P], C.c_int),
         "gp_apply_host": ([P, P, P, P], C.c_int),
         "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_profile_enable": ([P, C.c_int], C.c_int),
@@ -91,7 +92,8 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_num_touched_dofs", "gp_cell_counts", "gp_active_dof_coords", "gp_ghost_faces",
                "gp_cell_classes", "gp_reference_1d", "gp_apply", "gp_apply_add", "gp_apply_host",
                "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
-               "gp_version")
+               "gp_version", "gp_apply_noalloc")
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def _check(status, ctx=None):
@@ -171,6 +173,15 @@ def gp_apply(ctx: Context, x, y, stream=None):
     _check_vec(ctx, x)
     _check_vec(ctx, y)
     _check(lib.gp_apply(ctx.handle, _ptr(x), _ptr(y), _stream(stream)), ctx)
+
+
+def gp_apply_noalloc(ctx: Context, x, y, stream=None):
+    """y = G x without any device allocation: the face outputs use the library's fixed
+    32 MiB scratch (see gp.h).  For callers whose device memory is owned by another
+    allocator, or whose loop must not pay for cudaMalloc/cudaFree."""
+    _check_vec(ctx, x)
+    _check_vec(ctx, y)
+    _check(lib.gp_apply_noalloc(ctx.handle, _ptr(x), _ptr(y), _stream(stream)), ctx)
 
 
 def gp_apply_add(ctx: Context, x, y, stream=None):
