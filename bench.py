@@ -49,6 +49,30 @@ def _dist():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ["paper_2503_00246_gb300/csrc/gp_kernels.cuh", "paper_2503_00246_gb300/csrc/gp_arith.cuh",
+                  "paper_2503_00246_gb300/csrc/gp_launch.h", "paper_2503_00246_gb300/csrc/gp_plan.cpp"]
+
+
+def _traffic(tag):
+    """DRAM bytes per face-kernel launch from the committed ncu summary, or None when the
+    kernel sources changed since those counters were taken."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "face_kernel_ball64_k3.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_sources_sha256_16 = (\w+)", txt)
+    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(tag) + r"\] = (\d+)", txt)
+    if not m or not t or m.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(t.group(1))
+
+
 def _peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -247,7 +271,7 @@ def run_gpu(args):
                                 gp.GP_FP32: "derived: 152 SM x 128 FP32 FMA/clk x 2070 MHz x 2 flop",
                                 gp.GP_FP64_FF: "derived: FP32 peak / 15 FP32 ops per float-float FMA"}[prec]}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
+        roof["traffic"] = _traffic({gp.GP_FP64: "f64", gp.GP_FP32: "f32", gp.GP_FP64_FF: "ff64"}[prec])
         alg_bytes = w * (ctx.n_touched + ctx.n_active)
         results[prec] = {
             "value": ws * ctx.n_active / (t_max * 1e-3) / 1e9,
