@@ -175,6 +175,43 @@ def run_profile(args):
                       "n_faces": ctx.n_faces, "n_touched": ctx.n_touched, "applies": args.reps}))
 
 
+def run_batched(gp, W, torch, dev, prec, steps, warmup):
+    """The batched workload: 64 independent 3D ball problems, n ~ U{16..96}, k ~ U{2..6},
+    4 right-hand sides each, replayed as one CUDA graph per apply.  Inputs (> 7 GB) exceed L2."""
+    probs = W.batched_3d()
+    nrhs = 4
+    ctxs = [gp.setup_problem(p, precision=prec, device=dev.index or 0) for p in probs]
+    batch = gp.gp_batch_create(ctxs, nrhs)
+    tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.BASE_SEED + 5000)
+    xs = [torch.rand(nrhs * c.n_active, generator=gen, dtype=tdt, device=dev) * 2 - 1 for c in ctxs]
+    ys = [torch.empty_like(x) for x in xs]
+    for _ in range(warmup):
+        gp.gp_batch_apply(batch, xs, ys)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gp.gp_batch_apply(batch, xs, ys)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / steps
+    units = nrhs * sum(c.n_active for c in ctxs)
+    ngroups, scratch = gp.gp_batch_info(batch)
+    out = {"value": units / (t * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_apply": t,
+           "problems": len(probs), "rhs": nrhs, "dof_vectors_per_apply": units,
+           "ghost_faces": sum(c.n_faces for c in ctxs), "kernel_groups": ngroups,
+           "graph_launches_per_apply": 1, "kernels_per_apply": 2 * ngroups,
+           "scratch_bytes": scratch}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del xs, ys
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -328,6 +365,11 @@ def run_gpu(args):
         f = results[p]
         line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
                                               "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value")}
+    if not args.no_batched:
+        line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2)
+                           for p in (gp.GP_FP64_FF, gp.GP_FP32)}
+        line["batched"]["workload"] = ("64 independent 3D balls on [-1,1]^3, n ~ U{16..96}, k ~ U{2..6}, "
+                                       "r ~ U[0.4,0.8], 4 right-hand sides, one CUDA graph per apply")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -431,6 +473,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--workload", default="ball64_k3", choices=sorted(WORKLOADS))
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()

@@ -182,6 +182,23 @@ gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs,
 gp_status gp_profile_enable(gp_ctx* ctx, int enable);
 gp_status gp_profile_read(gp_ctx* ctx, double ms[2], int64_t* calls);
 
+/* Batched form: several independent problems, nrhs right-hand sides each, replayed
+ * as one CUDA graph (the batched workload of many meshes of uneven n, k and
+ * geometry).  gp_batch_create groups the problems by (dimension, degree,
+ * arithmetic); every (problem, right-hand side) pair gets its own face-output
+ * buffer, and one face launch plus one lift launch per group cover all pairs.  The
+ * graph also holds the host-to-device copy of the table of x / y pointers, so each
+ * gp_batch_apply writes that table (pinned host memory) and launches the graph.
+ *   ctxs: contexts on one device; they must outlive the batch.
+ *   x[p], y[p]: device arrays of nrhs * n_active(p) elements, layout [nrhs][n_active];
+ *   y[p] is overwritten.  An apply waits for the apply issued two calls earlier
+ *   (the pointer tables are double-buffered). */
+typedef struct gp_batch gp_batch;
+gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** out);
+gp_status gp_batch_apply(gp_batch* batch, const void* const* x, void* const* y, void* stream);
+gp_status gp_batch_info(const gp_batch* batch, int64_t* ngroups, int64_t* scratch_bytes);
+void gp_batch_destroy(gp_batch* batch);
+
 /* Last error message of ctx (or of the calling thread when ctx is NULL). */
 const char* gp_last_error(const gp_ctx* ctx);
 

@@ -1,7 +1,9 @@
 // C ABI of the ghost-penalty operator (declarations and contracts in gp.h).
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gp.h"
@@ -377,6 +379,221 @@ gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs, const void*
     }
   }
   return GP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches --
+struct gp_batch {
+  int device = -1, nprob = 0, nrhs = 0;
+  std::vector<gp_ctx*> ctxs;
+  struct Group {
+    int dim = 0, k = 0, prec = 0;
+    std::vector<int> prob, rhs;        // segment -> problem, right-hand side
+    void* d_fsegs = nullptr;
+    void* d_lsegs = nullptr;
+    void* d_ptrs[2] = {nullptr, nullptr};
+    void* h_ptrs[2] = {nullptr, nullptr};  // pinned: read by the graph's copy node at replay
+    int face_blocks = 0, lift_blocks = 0;
+    gp::BatchOps ops{};
+  };
+  std::vector<Group> groups;
+  void* d_w = nullptr;
+  size_t w_bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool pending[2] = {false, false};
+  int slot = 0;
+  std::string err;
+};
+
+namespace {
+
+gp::BatchOps ops_for(int prec, int dim) {
+  if (prec == GP_FP64) return dim == 2 ? gp::batch_ops_f64_d2() : gp::batch_ops_f64_d3();
+  if (prec == GP_FP64_FF) return dim == 2 ? gp::batch_ops_ff_d2() : gp::batch_ops_ff_d3();
+  return dim == 2 ? gp::batch_ops_f32_d2() : gp::batch_ops_f32_d3();
+}
+
+void batch_free(gp_batch* b) {
+  for (int i = 0; i < 2; ++i) {
+    if (b->pending[i] && b->done[i]) cudaEventSynchronize(b->done[i]);
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+    if (b->done[i]) cudaEventDestroy(b->done[i]);
+  }
+  for (auto& g : b->groups) {
+    if (g.d_fsegs) cudaFree(g.d_fsegs);
+    if (g.d_lsegs) cudaFree(g.d_lsegs);
+    for (int i = 0; i < 2; ++i) {
+      if (g.d_ptrs[i]) cudaFree(g.d_ptrs[i]);
+      if (g.h_ptrs[i]) cudaFreeHost(g.h_ptrs[i]);
+    }
+  }
+  if (b->d_w) cudaFree(b->d_w);
+  if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** out) {
+  if (!out) return fail(nullptr, GP_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (nprob < 1 || nrhs < 1 || !ctxs) return fail(nullptr, GP_EINVAL, "bad batch arguments");
+  for (int p = 0; p < nprob; ++p) {
+    if (!ctxs[p] || !ctxs[p]->on_device) return fail(nullptr, GP_EINVAL, "every context must be on a device");
+    if (ctxs[p]->device != ctxs[0]->device) return fail(nullptr, GP_EINVAL, "all contexts must share a device");
+  }
+  gp_batch* b = new (std::nothrow) gp_batch();
+  if (!b) return fail(nullptr, GP_ENOMEM, "host allocation failed");
+  b->device = ctxs[0]->device;
+  b->nprob = nprob;
+  b->nrhs = nrhs;
+  b->ctxs.assign(ctxs, ctxs + nprob);
+  DeviceGuard dg(b->device);
+  // group problems by (dimension, degree, arithmetic)
+  std::map<std::tuple<int, int, int>, int> key;
+  for (int p = 0; p < nprob; ++p) {
+    const gp::Plan& pl = ctxs[p]->plan;
+    auto kk = std::make_tuple(pl.dim, pl.k, pl.precision);
+    auto it = key.find(kk);
+    int gi;
+    if (it == key.end()) {
+      gi = (int)b->groups.size();
+      key[kk] = gi;
+      b->groups.emplace_back();
+      b->groups[gi].dim = pl.dim;
+      b->groups[gi].k = pl.k;
+      b->groups[gi].prec = pl.precision;
+      b->groups[gi].ops = ops_for(pl.precision, pl.dim);
+    } else {
+      gi = it->second;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      b->groups[gi].prob.push_back(p);
+      b->groups[gi].rhs.push_back(r);
+    }
+  }
+  // face-output buffers, one per segment, 256-byte aligned in one allocation
+  std::vector<std::vector<size_t>> woff(b->groups.size());
+  size_t total = 0;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    for (int p : b->groups[gi].prob) {
+      const gp::Plan& pl = ctxs[p]->plan;
+      const size_t vb = pl.precision == GP_FP32 ? 4 : 8;
+      woff[gi].push_back(total);
+      total += ((size_t)pl.num_faces() * pl.L * (2 * pl.k + 1) * vb + 255) / 256 * 256;
+    }
+  cudaError_t e = cudaSuccess;
+  if (total > 0) e = cudaMalloc(&b->d_w, total);
+  b->w_bytes = total;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    auto& g = b->groups[gi];
+    std::vector<gp::SegSpec> specs(g.prob.size());
+    for (size_t i = 0; i < g.prob.size(); ++i) {
+      const gp_ctx* c = ctxs[g.prob[i]];
+      const gp::Plan& pl = c->plan;
+      gp::SegSpec& sp = specs[i];
+      sp.fa.frows = c->d_frows;
+      for (int a = 0; a < 4; ++a) {
+        sp.fa.rbase[a] = pl.rbase[a];
+        sp.fa.fstart[a] = pl.fstart[a];
+      }
+      sp.fa.zruns = c->d_zruns;
+      sp.fa.nzruns = (int32_t)pl.num_zero_runs();
+      sp.la.lwin = c->d_lwin;
+      sp.la.lrow = c->d_lrow;
+      sp.la.nlift = (int32_t)pl.num_lift_cells();
+      sp.la.n_active = (int32_t)pl.n_active;
+      sp.wp = (char*)b->d_w + woff[gi][i];
+      for (int j = 0; j < pl.k; ++j) sp.s[j] = pl.scale[j];
+    }
+    std::vector<unsigned char> fs, ls;
+    g.ops.pack(g.k, specs, fs, ls, g.face_blocks, g.lift_blocks);
+    e = cudaMalloc(&g.d_fsegs, fs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_fsegs, fs.data(), fs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_lsegs, ls.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_lsegs, ls.data(), ls.size(), cudaMemcpyHostToDevice);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaMalloc(&g.d_ptrs[i], g.prob.size() * 2 * sizeof(void*));
+      if (e == cudaSuccess) e = cudaMallocHost(&g.h_ptrs[i], g.prob.size() * 2 * sizeof(void*));
+      if (e == cudaSuccess) std::memset(g.h_ptrs[i], 0, g.prob.size() * 2 * sizeof(void*));
+    }
+  }
+  // one graph per slot: copy the pointer table, then each group's face and lift launches
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    for (auto& g : b->groups) {
+      if (e != cudaSuccess) break;
+      const gp::Plan& pl0 = ctxs[g.prob[0]]->plan;
+      e = cudaMemcpyAsync(g.d_ptrs[i], g.h_ptrs[i], g.prob.size() * 2 * sizeof(void*), cudaMemcpyHostToDevice,
+                          b->cap);
+      if (e == cudaSuccess)
+        e = g.ops.run(g.k, g.d_fsegs, g.d_lsegs, g.d_ptrs[i], (int)g.prob.size(), g.face_blocks, g.lift_blocks,
+                      pl0.jumps.data(), pl0.mass.data(), b->cap);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e == cudaSuccess) e = e2;
+    b->graph[i] = graph;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[i], graph, 0);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
+    batch_free(b);
+    delete b;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
+  }
+  *out = b;
+  return GP_OK;
+}
+
+gp_status gp_batch_apply(gp_batch* b, const void* const* x, void* const* y, void* stream) {
+  if (!b || !x || !y) return fail(nullptr, GP_EINVAL, "null argument");
+  for (int p = 0; p < b->nprob; ++p)
+    if ((!x[p] || !y[p]) && b->ctxs[p]->plan.n_active > 0) return fail(nullptr, GP_EINVAL, "null x or y");
+  DeviceGuard dg(b->device);
+  const int s = b->slot;
+  b->slot ^= 1;
+  // the slot's pinned table is read by the graph launched two applies ago
+  if (b->pending[s]) {
+    const cudaError_t e = cudaEventSynchronize(b->done[s]);
+    if (e != cudaSuccess) return fail(nullptr, GP_ECUDA, std::string("batch: ") + cudaGetErrorString(e));
+  }
+  for (auto& g : b->groups) {
+    void** tab = (void**)g.h_ptrs[s];
+    for (size_t i = 0; i < g.prob.size(); ++i) {
+      const gp_ctx* c = b->ctxs[g.prob[i]];
+      const size_t off = (size_t)g.rhs[i] * c->plan.n_active * c->elem;
+      tab[2 * i] = (void*)((const char*)x[g.prob[i]] + off);
+      tab[2 * i + 1] = (void*)((char*)y[g.prob[i]] + off);
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec[s], (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done[s], (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, GP_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  b->pending[s] = true;
+  return GP_OK;
+}
+
+gp_status gp_batch_info(const gp_batch* b, int64_t* ngroups, int64_t* scratch_bytes) {
+  if (!b || !ngroups || !scratch_bytes) return fail(nullptr, GP_EINVAL, "null argument");
+  *ngroups = (int64_t)b->groups.size();
+  *scratch_bytes = (int64_t)b->w_bytes;
+  return GP_OK;
+}
+
+void gp_batch_destroy(gp_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  batch_free(b);
+  delete b;
 }
 
 }  // extern "C"

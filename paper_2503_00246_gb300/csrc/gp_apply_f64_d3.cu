@@ -3,4 +3,5 @@
 
 namespace gp {
 cudaError_t apply_f64_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArF64, a, st) }
+BatchOps batch_ops_f64_d3() { GP_BATCH_OPS(3, ArF64) }
 }  // namespace gp

@@ -3,4 +3,5 @@
 
 namespace gp {
 cudaError_t apply_ff_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArFF, a, st) }
+BatchOps batch_ops_ff_d3() { GP_BATCH_OPS(3, ArFF) }
 }  // namespace gp

@@ -63,12 +63,13 @@ struct LiftArgs {
 };
 
 // ----------------------------------------------------------------- face --
-// One thread per (face, normal line tau); FB faces per CTA.
+// One thread per (face, normal line tau); FB faces per CTA.  `blk` is the CTA's
+// index within its problem; `sc` points to the k scale factors s_j.
 template <int D, int K, class A>
-__global__ void __launch_bounds__(Shape<D, K>::NT)
-face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
-            typename A::IO* __restrict__ y, const FaceArgs fa,
-            const __grid_constant__ Consts<typename A::V, K> c) {
+__device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
+                                          typename A::IO* __restrict__ y, const FaceArgs& fa,
+                                          const Consts<typename A::V, K>& c, const typename A::V* sc,
+                                          const int blk) {
   using S = Shape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
@@ -77,7 +78,6 @@ face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp
   __shared__ V sb2[(D == 3) ? FB : 1][K][L];
   __shared__ V sm[K1][K1];
 
-  const int blk = blockIdx.x;
   if (blk < fa.nzblocks) {
     // zero fill of the active DoFs outside every face patch (overwrite form only):
     // ZGROUP runs of <= 256 elements, descriptors fetched in parallel
@@ -179,7 +179,7 @@ face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp
   if (valid) {
     V sj[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) sj[j] = vfma(c.s[j], out[j], vzero<V>());
+    for (int j = 0; j < K; ++j) sj[j] = vfma(sc[j], out[j], vzero<V>());
     V* dst = wp + (size_t)f * S::P;
     int pos0, pstride;
     if (axis == 0) {            // patch index b + NN * tau
@@ -203,6 +203,65 @@ face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp
       dst[pos0 + pstride * b] = wv;
     }
   }
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(Shape<D, K>::NT)
+face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
+            typename A::IO* __restrict__ y, const FaceArgs fa,
+            const __grid_constant__ Consts<typename A::V, K> c) {
+  face_body<D, K, A>(x, wp, y, fa, c, c.s, blockIdx.x);
+}
+
+// --------------------------------------------------------------- batches --
+// A batch segment is one (problem, right-hand side) pair of a group of problems
+// with the same dimension, degree and arithmetic.  Its x and y pointers live in
+// a separate table the host rewrites for every apply.
+template <typename V, int K>
+struct FaceSeg {
+  FaceArgs fa;
+  V* wp;           // this segment's face outputs
+  V s[K];          // c_j h^{d-2} of the segment's problem
+  int32_t block0;  // first CTA of the segment in the group's face launch
+};
+
+struct LiftSeg {
+  LiftArgs la;
+  int32_t block0;  // first CTA of the segment in the group's lift launch
+};
+
+template <typename IO>
+struct SegPtrs {
+  const IO* x;
+  IO* y;
+};
+
+// index of the segment holding CTA `blk`: the last segment whose block0 <= blk
+template <typename Seg>
+__device__ __forceinline__ int find_segment(const Seg* segs, const int nseg, const int blk) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&segs[mid].block0) <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(Shape<D, K>::NT)
+face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const int nseg,
+                    const SegPtrs<typename A::IO>* __restrict__ ptrs,
+                    const __grid_constant__ Consts<typename A::V, K> c) {
+  __shared__ FaceSeg<typename A::V, K> seg;
+  __shared__ SegPtrs<typename A::IO> sp;
+  if (threadIdx.x == 0) {
+    const int s = find_segment(segs, nseg, (int)blockIdx.x);
+    seg = segs[s];
+    sp = ptrs[s];
+  }
+  __syncthreads();
+  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, seg.s, (int)blockIdx.x - seg.block0);
 }
 
 // ----------------------------------------------------------------- lift --
@@ -303,15 +362,14 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
 }
 
 template <int D, int K, class A>
-__global__ void __launch_bounds__(256)
-lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
-            const LiftArgs la) {
+__device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y,
+                                          const int add, const LiftArgs& la, const int blk) {
   using S = LiftShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
   constexpr int NW = S::NW, CB = S::CB;
   __shared__ int win[CB][NW + 1];
-  const int cell0 = blockIdx.x * CB;
+  const int cell0 = blk * CB;
   const int t = threadIdx.x;
   for (int idx = t; idx < NW * CB; idx += S::NT) {
     const int ln = idx / NW, w = idx - ln * NW;
@@ -361,6 +419,30 @@ lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y
       y[idx] = to_io(outv, (IO*)nullptr);
     }
   }
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(256)
+lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
+            const LiftArgs la) {
+  lift_body<D, K, A>(wp, y, add, la, blockIdx.x);
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(256)
+lift_kernel_batched(const LiftSeg* __restrict__ segs, const FaceSeg<typename A::V, K>* __restrict__ fsegs,
+                    const int nseg, const SegPtrs<typename A::IO>* __restrict__ ptrs) {
+  __shared__ LiftSeg seg;
+  __shared__ typename A::V* wp;
+  __shared__ typename A::IO* y;
+  if (threadIdx.x == 0) {
+    const int s = find_segment(segs, nseg, (int)blockIdx.x);
+    seg = segs[s];
+    wp = fsegs[s].wp;
+    y = ptrs[s].y;
+  }
+  __syncthreads();
+  lift_body<D, K, A>(wp, y, 0, seg.la, (int)blockIdx.x - seg.block0);
 }
 
 }  // namespace gp

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "gp_kernels.cuh"
@@ -70,6 +72,117 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   if (Ar.ev) cudaEventRecord(Ar.ev[2], st);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------- batches --
+// Host description of one batch segment (one problem, one right-hand side).
+struct SegSpec {
+  FaceArgs fa;          // frows, rbase, fstart, zruns, nzruns of the segment's problem
+  LiftArgs la;
+  void* wp = nullptr;   // the segment's face-output buffer
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// Packs the segments of one (d, k, arithmetic) group into the device layouts of
+// FaceSeg<V, K> and LiftSeg, with the CTA offsets of both launches.
+template <int D, int K, class A>
+void pack_batch(const std::vector<SegSpec>& in, std::vector<unsigned char>& fsegs,
+                std::vector<unsigned char>& lsegs, int& face_blocks, int& lift_blocks) {
+  using V = typename A::V;
+  using S = Shape<D, K>;
+  using LS = LiftShape<D, K>;
+  fsegs.assign(in.size() * sizeof(FaceSeg<V, K>), 0);
+  lsegs.assign(in.size() * sizeof(LiftSeg), 0);
+  int fb = 0, lb = 0;
+  for (size_t i = 0; i < in.size(); ++i) {
+    FaceSeg<V, K> fs;
+    fs.fa = in[i].fa;
+    fs.fa.nzblocks = (fs.fa.nzruns + ZGROUP - 1) / ZGROUP;
+    int32_t nb = fs.fa.nzblocks;
+    for (int a = 0; a < D; ++a) {
+      fs.fa.bstart[a] = nb;
+      nb += (fs.fa.fstart[a + 1] - fs.fa.fstart[a] + S::FB - 1) / S::FB;
+    }
+    for (int a = D; a < 4; ++a) fs.fa.bstart[a] = nb;
+    fs.wp = (V*)in[i].wp;
+    for (int j = 0; j < K; ++j) fs.s[j] = from_host<V>(in[i].s[j]);
+    fs.block0 = fb;
+    fb += nb;
+    LiftSeg ls;
+    ls.la = in[i].la;
+    ls.block0 = lb;
+    if (fs.fa.fstart[D] > 0) lb += (ls.la.nlift + LS::CB - 1) / LS::CB;
+    std::memcpy(&fsegs[i * sizeof(FaceSeg<V, K>)], &fs, sizeof(fs));
+    std::memcpy(&lsegs[i * sizeof(LiftSeg)], &ls, sizeof(ls));
+  }
+  face_blocks = fb;
+  lift_blocks = lb;
+}
+
+template <int D, int K, class A>
+cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, int nseg, int face_blocks,
+                      int lift_blocks, const double* g, const double* m, cudaStream_t st) {
+  using V = typename A::V;
+  using IO = typename A::IO;
+  using S = Shape<D, K>;
+  Consts<V, K> c;
+  for (int j = 0; j < K; ++j)
+    for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
+  for (int p = 0; p < K + 1; ++p)
+    for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
+  for (int j = 0; j < K; ++j) c.s[j] = vzero<V>();   // per segment, in FaceSeg
+  if (face_blocks > 0)
+    face_kernel_batched<D, K, A><<<face_blocks, S::NT, 0, st>>>((const FaceSeg<V, K>*)fsegs, nseg,
+                                                               (const SegPtrs<IO>*)ptrs, c);
+  if (lift_blocks > 0)
+    lift_kernel_batched<D, K, A><<<lift_blocks, LiftShape<D, K>::NT, 0, st>>>(
+        (const LiftSeg*)lsegs, (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs);
+  return cudaGetLastError();
+}
+
+// Per translation unit: batch packing and launch for one (arithmetic, dimension).
+struct BatchOps {
+  void (*pack)(int k, const std::vector<SegSpec>&, std::vector<unsigned char>&, std::vector<unsigned char>&,
+               int&, int&);
+  cudaError_t (*run)(int k, const void*, const void*, const void*, int, int, int, const double*, const double*,
+                     cudaStream_t);
+};
+BatchOps batch_ops_f64_d2();
+BatchOps batch_ops_f64_d3();
+BatchOps batch_ops_f32_d2();
+BatchOps batch_ops_f32_d3();
+BatchOps batch_ops_ff_d2();
+BatchOps batch_ops_ff_d3();
+
+#define GP_BATCH_OPS(D, A)                                                                              \
+  BatchOps ops;                                                                                         \
+  ops.pack = [](int k, const std::vector<SegSpec>& in, std::vector<unsigned char>& fs,                  \
+                std::vector<unsigned char>& ls, int& fb, int& lb) {                                     \
+    switch (k) {                                                                                        \
+      case 1: pack_batch<D, 1, A>(in, fs, ls, fb, lb); break;                                           \
+      case 2: pack_batch<D, 2, A>(in, fs, ls, fb, lb); break;                                           \
+      case 3: pack_batch<D, 3, A>(in, fs, ls, fb, lb); break;                                           \
+      case 4: pack_batch<D, 4, A>(in, fs, ls, fb, lb); break;                                           \
+      case 5: pack_batch<D, 5, A>(in, fs, ls, fb, lb); break;                                           \
+      case 6: pack_batch<D, 6, A>(in, fs, ls, fb, lb); break;                                           \
+      case 7: pack_batch<D, 7, A>(in, fs, ls, fb, lb); break;                                           \
+      default: pack_batch<D, 8, A>(in, fs, ls, fb, lb); break;                                          \
+    }                                                                                                   \
+  };                                                                                                    \
+  ops.run = [](int k, const void* fs, const void* ls, const void* pt, int ns, int fb, int lb,          \
+               const double* g, const double* m, cudaStream_t st) -> cudaError_t {                      \
+    switch (k) {                                                                                        \
+      case 1: return run_batch<D, 1, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 2: return run_batch<D, 2, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 3: return run_batch<D, 3, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 4: return run_batch<D, 4, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 5: return run_batch<D, 5, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 6: return run_batch<D, 6, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 7: return run_batch<D, 7, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 8: return run_batch<D, 8, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      default: return cudaErrorInvalidValue;                                                            \
+    }                                                                                                   \
+  };                                                                                                    \
+  return ops;
 
 #define GP_DISPATCH_K(D, A, Ar, st)                    \
   switch ((Ar).k) {                                    \

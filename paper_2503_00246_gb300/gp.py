@@ -73,6 +73,10 @@ def _load():
         "gp_apply_noalloc": ([P, P, P, P], C.c_int),
         "gp_apply_host": ([P, P, P, P], C.c_int),
         "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
+        "gp_batch_create": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P)], C.c_int),
+        "gp_batch_apply": ([P, C.POINTER(P), C.POINTER(P), P], C.c_int),
+        "gp_batch_info": ([P, i64p, i64p], C.c_int),
+        "gp_batch_destroy": ([P], None),
         "gp_profile_enable": ([P, C.c_int], C.c_int),
         "gp_profile_read": ([P, C.POINTER(C.c_double), i64p], C.c_int),
         "gp_last_error": ([P], C.c_char_p),
@@ -92,7 +96,8 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_num_touched_dofs", "gp_cell_counts", "gp_active_dof_coords", "gp_ghost_faces",
                "gp_cell_classes", "gp_reference_1d", "gp_apply", "gp_apply_add", "gp_apply_host",
                "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
-               "gp_version", "gp_apply_noalloc")
+               "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
+               "gp_batch_destroy")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -213,6 +218,54 @@ def gp_apply_batched(ctxs, nrhs, xs, ys, stream=None):
     X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
     Y = (C.c_void_p * n)(*[_ptr(y) for y in ys])
     _check(lib.gp_apply_batched(H, n, nrhs, X, Y, _stream(stream)))
+
+
+class Batch:
+    """Owns a gp_batch handle; keeps its contexts alive."""
+
+    def __init__(self, handle, ctxs, nrhs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+        self.nrhs = nrhs
+
+    def close(self):
+        if self.handle:
+            lib.gp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gp_batch_create(ctxs, nrhs) -> Batch:
+    n = len(ctxs)
+    H = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    h = C.c_void_p()
+    _check(lib.gp_batch_create(H, n, nrhs, C.byref(h)))
+    return Batch(h.value, ctxs, nrhs)
+
+
+def gp_batch_apply(batch: Batch, xs, ys, stream=None):
+    for c, x, y in zip(batch.ctxs, xs, ys):
+        _check_vec(c, x, batch.nrhs)
+        _check_vec(c, y, batch.nrhs)
+    n = len(batch.ctxs)
+    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    Y = (C.c_void_p * n)(*[_ptr(y) for y in ys])
+    _check(lib.gp_batch_apply(batch.handle, X, Y, _stream(stream)))
+
+
+def gp_batch_info(batch: Batch):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib.gp_batch_info(batch.handle, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def gp_batch_destroy(batch: Batch):
+    batch.close()
 
 
 def gp_num_active_dofs(ctx: Context) -> int:

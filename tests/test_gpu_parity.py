@@ -216,3 +216,32 @@ def test_ball_96_k4_sampled(gplib, cuda, prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_gyroid_128_k4_sampled(gplib, cuda, prec):
     _sampled(gplib, cuda, W.gyroid_3d(), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_graph_replays(gplib, cuda, prec):
+    """gp_batch_*: problems of mixed k and dimension, 3 right-hand sides, three graph replays
+    with fresh inputs; every vector equals gp_apply's bitwise and the oracle within tolerance."""
+    probs = [W.small_ball(3, 10, 2, seed=31), W.small_ball(3, 12, 3, seed=32), W.small_ball(3, 8, 5, seed=33),
+             W.small_ball(2, 16, 4, seed=34), W.small_ball(3, 11, 3, seed=35), W.small_ball(3, 9, 2, seed=36)]
+    nrhs = 3
+    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    batch = gplib.gp_batch_create(ctxs, nrhs)
+    ngroups, scratch = gplib.gp_batch_info(batch)
+    assert ngroups == 4 and scratch > 0     # (3D,k2) x2, (3D,k3) x2, (3D,k5), (2D,k4)
+    oracles = [Oracle(p) for p in probs]
+    rng = np.random.default_rng(17)
+    for call in range(3):
+        xs = [rng.uniform(-1, 1, (nrhs, c.n_active)) for c in ctxs]
+        xd = [_dev(cuda, x.ravel(), prec) for x in xs]
+        yd = [cuda.full_like(a, float("nan")) for a in xd]
+        gplib.gp_batch_apply(batch, xd, yd)
+        cuda.cuda.synchronize()
+        for p, c, x, y in zip(range(len(probs)), ctxs, xs, yd):
+            yy = y.double().cpu().numpy().reshape(nrhs, -1)
+            for r in range(nrhs):
+                single = _apply(gplib, cuda, c, x[r], prec)
+                assert np.array_equal(yy[r], single), (p, r)
+                if call == 0:
+                    _close(yy[r], oracles[p].apply(_ref_input(x[r], prec)), prec)
+    batch.close()
