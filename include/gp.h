@@ -199,6 +199,47 @@ gp_status gp_batch_apply(gp_batch* batch, const void* const* x, void* const* y, 
 gp_status gp_batch_info(const gp_batch* batch, int64_t* ngroups, int64_t* scratch_bytes);
 void gp_batch_destroy(gp_batch* batch);
 
+/* Model SPD system (M_active + K_active + G) u = b: the mass and Laplace
+ * stiffness of every active cell integrated over the whole cell (the interior-cell
+ * evaluation of Sec. 2.5.2 applied to all active cells; no cut quadrature) plus the
+ * ghost penalty.  hi: a GP_FP64 or GP_FP64_FF context; lo: a GP_FP32 context of the
+ * same mesh, degree and level set, or NULL.  Both must outlive the system. */
+typedef struct gp_system gp_system;
+gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out);
+
+/* y = A x with the hi (which = 0; x, y double) or lo (which = 1; float) operator.
+ * Deterministic: G first, then the cells of each parity colour in a fixed order. */
+gp_status gp_system_apply(gp_system* sys, int which, const void* x, void* y, void* stream);
+
+/* Solvers (the paper leaves the solver open, Sec. 1).  mode 0, defect correction:
+ * r = b - A_hi u and all updates in FP64; each correction A_lo d = r solved by CG
+ * with the FP32 operator and FP64 inner products to relative residual inner_rtol
+ * (at most max_inner iterations); at most max_outer corrections; stops when
+ * ||b - A_hi u|| <= rtol ||b||.  mode 1: the same outer loop with FP64 CG on the hi
+ * operator as the inner solver (tolerance chosen to reach rtol), i.e. plain FP64 CG
+ * with a true-residual check.  precond 1: Jacobi (diag(A) computed in FP64 on the
+ * host), 0: none.  b, u: device arrays of n_active doubles; u is overwritten (the
+ * solve starts from u = 0).  The call synchronises. */
+typedef struct {
+  double rtol;
+  double inner_rtol;
+  int max_outer;
+  int max_inner;
+  int mode;
+  int precond;
+} gp_solve_opts;
+typedef struct {
+  int outer;            /* outer corrections */
+  int inner;            /* CG iterations in total */
+  int hi_applies;
+  int lo_applies;
+  double rel_residual;  /* ||b - A_hi u|| / ||b|| at return */
+  double seconds;
+} gp_solve_stats;
+gp_status gp_system_solve(gp_system* sys, const double* b, double* u, const gp_solve_opts* opts,
+                          gp_solve_stats* stats);
+void gp_system_destroy(gp_system* sys);
+
 /* Last error message of ctx (or of the calling thread when ctx is NULL). */
 const char* gp_last_error(const gp_ctx* ctx);
 

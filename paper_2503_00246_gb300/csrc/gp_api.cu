@@ -6,37 +6,20 @@
 #include <tuple>
 #include <vector>
 
-#include "gp.h"
-#include "gp_launch.h"
-#include "gp_plan.h"
+#include "gp_internal.h"
 
 namespace gp {
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(int device, void** out);
 }  // namespace gp
 
-struct gp_ctx {
-  gp::Plan plan;
-  int device = -1;
-  bool on_device = false;
-  size_t elem = 8;
-  int32_t* d_frows = nullptr;
-  int32_t* d_lwin = nullptr;
-  int32_t* d_lrow = nullptr;
-  int2* d_zruns = nullptr;
-  void* d_tp = nullptr;          // per-face outputs W_F (scratch)
-  void* d_xh = nullptr;          // gp_apply_host staging
-  void* d_yh = nullptr;
-  std::string err;
-  // tracing: one event triple per traced apply
-  bool prof = false;
-  std::vector<cudaEvent_t> ev;
-  int64_t nprof = 0;
-};
+
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace gpi {
 
 gp_status fail(const gp_ctx* c, gp_status s, const std::string& m) {
   if (c) const_cast<gp_ctx*>(c)->err = m;
@@ -44,19 +27,14 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m) {
   return s;
 }
 
-// Makes `dev` current for the lifetime of the guard and restores the caller's device.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+}  // namespace gpi
+
+using gpi::DeviceGuard;
+using gpi::fail;
+
+namespace {
+
+
 
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src) {
@@ -87,10 +65,9 @@ void free_device(gp_ctx* c) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                \
   } while (0)
 
-// Scratch for the face outputs: the context's buffer unless `scratch` is given;
-// `trace` = false never creates events (used by the allocation-free entry point).
-gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
-                 bool trace = true) {
+}  // namespace
+
+gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace) {
   const gp::Plan& p = c->plan;
   gp::ApplyArgs a;
   a.dim = p.dim;
@@ -133,6 +110,9 @@ gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, vo
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return GP_OK;
 }
+
+namespace {
+using gpi::launch;
 
 gp_status check_apply(const gp_ctx* c, const void* x, const void* y) {
   if (!c) return fail(nullptr, GP_EINVAL, "null context");

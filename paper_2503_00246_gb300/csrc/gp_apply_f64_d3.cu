@@ -1,7 +1,8 @@
-// Instantiations of the face kernels: FP64, dimension 3, degrees 1..8.
+// Instantiations of the face and cell kernels: FP64, dimension 3, degrees 1..8.
 #include "gp_launch.h"
 
 namespace gp {
 cudaError_t apply_f64_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArF64, a, st) }
 BatchOps batch_ops_f64_d3() { GP_BATCH_OPS(3, ArF64) }
+CellsFn cells_f64_d3() { GP_CELLS_FN(3, ArF64) }
 }  // namespace gp

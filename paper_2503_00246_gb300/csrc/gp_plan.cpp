@@ -148,6 +148,105 @@ void reference_1d(int k, const std::vector<double>& /*gl*/, std::vector<double>&
     }
 }
 
+// S^[a][b] = int_0^1 l_a' l_b' with k+1 Gauss points (exact for degree 2k-2); the
+// derivative of l_m is evaluated as sum_i 1/(x_m - x_i) prod_{l != m, i} (x - x_l)/(x_m - x_l),
+// which stays finite when a Gauss point coincides with a node.
+void reference_stiffness(int k, std::vector<double>& stiff) {
+  const int N = k + 1;
+  std::vector<R> gl, xq, wq;
+  gauss_lobatto_01_r(k, gl);
+  gauss_legendre_01(N, xq, wq);
+  std::vector<R> Dv(N * N);  // Dv[q][m] = l_m'(x_q)
+  for (int q = 0; q < N; ++q)
+    for (int m = 0; m < N; ++m) {
+      R sum = 0;
+      for (int i = 0; i < N; ++i) {
+        if (i == m) continue;
+        R prod = 1 / (gl[m] - gl[i]);
+        for (int l = 0; l < N; ++l)
+          if (l != m && l != i) prod *= (xq[q] - gl[l]) / (gl[m] - gl[l]);
+        sum += prod;
+      }
+      Dv[q * N + m] = sum;
+    }
+  stiff.assign(N * N, 0.0);
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      R s = 0;
+      for (int q = 0; q < N; ++q) s += wq[q] * Dv[q * N + a] * Dv[q * N + b];
+      stiff[a * N + b] = (double)s;
+    }
+}
+
+void build_cell_table(Plan& p) {
+  const int d = p.dim, n = p.n, k = p.k;
+  const int R1 = d == 3 ? (k + 1) * (k + 1) : k + 1;
+  std::vector<int64_t> byc[8];
+  for (int64_t c = 0; c < p.ncell; ++c) {
+    if (p.cls[c] == OUTSIDE) continue;
+    int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+    byc[(ci & 1) + 2 * (cj & 1) + 4 * (cl & 1)].push_back(c);
+  }
+  p.ncact = 0;
+  for (int col = 0; col < 8; ++col) p.ncact += (int64_t)byc[col].size();
+  p.crow.assign((size_t)p.ncact * R1, 0);
+  int64_t pos = 0;
+  for (int col = 0; col < 8; ++col) {
+    p.cstart[col] = (int32_t)pos;
+    for (int64_t c : byc[col]) {
+      int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+      for (int t = 0; t < R1; ++t) {
+        int q = t % (k + 1), r = t / (k + 1);
+        int64_t row = (int64_t)(cj * k + q) + (d == 3 ? (int64_t)p.nl * (cl * k + r) : 0);
+        p.crow[(size_t)pos * R1 + t] = (int32_t)p.compact(ci * k, row);
+      }
+      ++pos;
+    }
+  }
+  p.cstart[8] = (int32_t)pos;
+}
+
+// Diagonal of the model system: per active cell h^d M_ii M_jj M_kk + h^(d-2) (S_ii M_jj M_kk +
+// M_ii S_jj M_kk + M_ii M_jj S_kk) at local node (i, j, k); per ghost face
+// sum_j s_j g_j[b]^2 times the tangential M^ diagonals at patch node (b, tau).
+void build_diagonal(const Plan& p, std::vector<double>& diag) {
+  const int d = p.dim, k = p.k, K1 = k + 1, NN = 2 * k + 1;
+  const int R1 = d == 3 ? K1 * K1 : K1;
+  diag.assign(p.n_active, 0.0);
+  const double hm = d == 3 ? p.h * p.h * p.h : p.h * p.h, hs = d == 3 ? p.h : 1.0;
+  auto M = [&](int a) { return p.mass[a * K1 + a]; };
+  auto S = [&](int a) { return p.stiff[a * K1 + a]; };
+  for (int64_t c = 0; c < p.ncact; ++c)
+    for (int t = 0; t < R1; ++t) {
+      const int j = t % K1, l = d == 3 ? t / K1 : 0;
+      const int64_t base = p.crow[(size_t)c * R1 + t];
+      for (int i = 0; i < K1; ++i) {
+        double v;
+        if (d == 3)
+          v = hm * M(i) * M(j) * M(l) + hs * (S(i) * M(j) * M(l) + M(i) * S(j) * M(l) + M(i) * M(j) * S(l));
+        else
+          v = hm * M(i) * M(j) + hs * (S(i) * M(j) + M(i) * S(j));
+        diag[base + i] += v;
+      }
+    }
+  std::vector<double> gb(NN, 0.0);  // sum_j s_j g_j[b]^2
+  for (int b = 0; b < NN; ++b)
+    for (int j = 0; j < k; ++j) gb[b] += p.scale[j] * p.jumps[j * NN + b] * p.jumps[j * NN + b];
+  const int L = p.L, R = d == 3 ? NN * K1 : NN;
+  for (int a = 0; a < d; ++a)
+    for (int64_t f = p.fstart[a]; f < p.fstart[a + 1]; ++f)
+      for (int tau = 0; tau < L; ++tau) {
+        const int t1 = d == 3 ? tau % K1 : tau, t2 = d == 3 ? tau / K1 : 0;
+        const double mt = M(t1) * (d == 3 ? M(t2) : 1.0);
+        for (int b = 0; b < NN; ++b) {
+          int64_t idx;
+          if (a == 0) idx = p.frows[p.rbase[0] + (f - p.fstart[0]) * L + tau] + b;
+          else idx = p.frows[p.rbase[a] + (f - p.fstart[a]) * R + b + NN * t2] + t1;
+          diag[idx] += gb[b] * mt;
+        }
+      }
+}
+
 // -------------------------------------------------------- classification --
 
 static int64_t ipow(int64_t b, int e) {
@@ -621,6 +720,7 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
   // ---- 1D reference data and the per-order scale c_j h^(d-2)
   gauss_lobatto_01(k, p.gl);
   reference_1d(k, p.gl, p.mass, p.jumps);
+  reference_stiffness(k, p.stiff);
   p.scale.resize(k);
   const double hd = d == 3 ? h : 1.0;
   for (int j = 0; j < k; ++j) {

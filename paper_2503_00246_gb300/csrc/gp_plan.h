@@ -58,8 +58,16 @@ struct Plan {
   int64_t num_lift_cells() const { return (int64_t)lcell.size() / 4; }
   int64_t num_zero_runs() const { return (int64_t)zruns.size() / 2; }
 
+  // active cells for the mass + stiffness operator, grouped by the parity colour
+  // (ci&1) + 2 (cj&1) + 4 (cl&1): cells of one colour share no node
+  std::vector<int32_t> crow;      // ncact x (k+1)^(d-1): compact index of (ci k, cj k + q, cl k + r)
+  int32_t cstart[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t num_active_cells() const { return ncact; }
+  int64_t ncact = 0;
+
   // FP64 1D reference data
   std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
+  std::vector<double> stiff;      // (k+1)^2: int_0^1 l_a' l_b' 
   std::vector<double> mass;       // (k+1)^2
   std::vector<double> jumps;      // k x (2k+1)
   std::vector<double> scale;      // k: c_j h^(dim-2)
@@ -76,5 +84,10 @@ void active_coords(const Plan& p, double* xyz);
 void gauss_lobatto_01(int k, std::vector<double>& x);
 void reference_1d(int k, const std::vector<double>& gl, std::vector<double>& mass,
                   std::vector<double>& jumps);
+void reference_stiffness(int k, std::vector<double>& stiff);
+// Builds crow / cstart (the active-cell table of the mass + stiffness operator).
+void build_cell_table(Plan& p);
+// diag(M_active + K_active + G) in FP64 (needs the cell table).
+void build_diagonal(const Plan& p, std::vector<double>& diag);
 
 }  // namespace gp

@@ -1,0 +1,340 @@
+// Model SPD system (M_active + K_active + G) u = b and its solvers.
+//
+// The system couples the ghost penalty G with the mass and Laplace stiffness of
+// every active cell integrated as a full cell (Sec. 2.5.2 for the interior-cell
+// evaluation).  The paper leaves the solver to future work (Sec. 1); this file
+// provides the defect-correction scheme of mixed-precision solvers: residuals,
+// updates and inner products in FP64, the inner correction solved by CG with the
+// FP32 operator, next to plain CG with the FP64 operator for comparison.
+//
+// Every reduction has a fixed order (fixed grid, fixed tree), so a solve is
+// bitwise reproducible.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "gp_internal.h"
+
+struct gp_system {
+  gp_ctx* hi = nullptr;   // FP64 or float-float operator
+  gp_ctx* lo = nullptr;   // FP32 operator (optional)
+  int device = -1;
+  int64_t n = 0;
+  int32_t* d_crow = nullptr;
+  int32_t cstart[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  gp::CellsFn cells_hi = nullptr, cells_lo = nullptr;
+  // solver vectors
+  double *r = nullptr, *p = nullptr, *q = nullptr, *dd = nullptr, *z = nullptr, *ri = nullptr;
+  float *r32 = nullptr, *d32 = nullptr, *ri32 = nullptr, *p32 = nullptr, *q32 = nullptr, *z32 = nullptr;
+  double* dinv = nullptr;   // 1 / diag(A) (Jacobi)
+  float* dinv32 = nullptr;
+  double* part = nullptr;   // dot partials + result
+  double* h_res = nullptr;  // pinned copy of the dot result
+  cudaStream_t st = nullptr;
+  std::string err;
+};
+
+namespace {
+
+using gpi::DeviceGuard;
+using gpi::fail;
+
+constexpr int kDotBlocks = 1024;
+constexpr int kThreads = 256;
+constexpr int kVecBlocks = 2048;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dot_partial(const T* __restrict__ a, const T* __restrict__ b,
+                                                        int64_t n, double* __restrict__ part) {
+  __shared__ double sh[kThreads];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads)
+    s = fma((double)a[i], (double)b[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kThreads) dot_final(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
+
+// vector updates in the vectors' own precision (FP32 vectors: FP32 arithmetic)
+template <typename T>
+__global__ void axpy_k(T* __restrict__ y, const T* __restrict__ x, double a, int64_t n) {
+  const T at = (T)a;
+  GRID_STRIDE(i, n) y[i] = fma(at, x[i], y[i]);
+}
+template <typename T>
+__global__ void xpay_k(T* __restrict__ p, const T* __restrict__ r, double beta, int64_t n) {
+  const T bt = (T)beta;
+  GRID_STRIDE(i, n) p[i] = fma(bt, p[i], r[i]);
+}
+__global__ void resid_k(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q,
+                        int64_t n) {
+  GRID_STRIDE(i, n) r[i] = b[i] - q[i];
+}
+__global__ void to32_k(float* __restrict__ o, const double* __restrict__ v, int64_t n) {
+  GRID_STRIDE(i, n) o[i] = (float)v[i];
+}
+__global__ void add32_k(double* __restrict__ u, const float* __restrict__ d, int64_t n) {
+  GRID_STRIDE(i, n) u[i] += (double)d[i];
+}
+template <typename T>
+__global__ void scale_k(T* __restrict__ z, const T* __restrict__ dinv, const T* __restrict__ r, int64_t n) {
+  GRID_STRIDE(i, n) z[i] = dinv[i] * r[i];
+}
+__global__ void add64_k(double* __restrict__ u, const double* __restrict__ d, int64_t n) {
+  GRID_STRIDE(i, n) u[i] += d[i];
+}
+
+template <typename T>
+cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
+  dot_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(a, b, s->n, s->part);
+  dot_final<<<1, kThreads, 0, s->st>>>(s->part, s->part + kDotBlocks);
+  cudaError_t e = cudaMemcpyAsync(s->h_res, s->part + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  *out = *s->h_res;
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// y = A x with the operator of context c (G, then the cell colours adding on top)
+gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st) {
+  gp_status g = gpi::launch(c, x, y, 0, st);
+  if (g != GP_OK) return g;
+  const gp::Plan& p = c->plan;
+  const cudaError_t e = cells(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(), p.h, st);
+  if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
+  return GP_OK;
+}
+
+gp::CellsFn cells_for(const gp::Plan& p) {
+  if (p.precision == GP_FP64) return p.dim == 2 ? gp::cells_f64_d2() : gp::cells_f64_d3();
+  if (p.precision == GP_FP64_FF) return p.dim == 2 ? gp::cells_ff_d2() : gp::cells_ff_d3();
+  return p.dim == 2 ? gp::cells_f32_d2() : gp::cells_f32_d3();
+}
+
+void sys_free(gp_system* s) {
+  void* ptrs[] = {s->d_crow, s->r, s->p, s->q, s->dd, s->z, s->ri, s->r32, s->d32, s->ri32, s->p32, s->q32,
+                  s->z32, s->dinv, s->dinv32, s->part};
+  for (void* v : ptrs)
+    if (v) cudaFree(v);
+  if (s->h_res) cudaFreeHost(s->h_res);
+  if (s->st) cudaStreamDestroy(s->st);
+}
+
+#define SYS_CUDA(call)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                               \
+      return fail(nullptr, e_ == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, s->err);      \
+    }                                                                                            \
+  } while (0)
+
+// Preconditioned CG (Jacobi when dinv is given) on A d = rhs from d = 0, until
+// ||r|| <= tol * ||rhs|| or maxit iterations.
+template <typename T>
+gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* r, T* p, T* q, T* z,
+             const T* dinv, double tol, int maxit, int* iters, int* applies) {
+  const int64_t n = s->n;
+  SYS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(T), s->st));
+  SYS_CUDA(cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
+  const T* zz = r;
+  if (dinv) {
+    scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
+    zz = z;
+  }
+  SYS_CUDA(cudaMemcpyAsync(p, zz, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
+  double rr0 = 0.0, rz = 0.0;
+  SYS_CUDA(dot<T>(s, r, r, &rr0));
+  SYS_CUDA(dot<T>(s, r, zz, &rz));
+  const double stop = tol * tol * rr0;
+  double rr = rr0;
+  int it = 0;
+  while (it < maxit && rr > stop && rr > 0.0) {
+    gp_status g = sys_apply(s, c, cells, p, q, s->st);
+    if (g != GP_OK) return g;
+    ++*applies;
+    double pq = 0.0;
+    SYS_CUDA(dot<T>(s, p, q, &pq));
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    axpy_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(d, p, alpha, n);
+    axpy_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(r, q, -alpha, n);
+    if (dinv) scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
+    double rz1 = 0.0;
+    SYS_CUDA(dot<T>(s, r, r, &rr));
+    if (dinv) SYS_CUDA(dot<T>(s, r, zz, &rz1));
+    else rz1 = rr;
+    xpay_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(p, zz, rz1 / rz, n);
+    rz = rz1;
+    ++it;
+  }
+  *iters = it;
+  return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
+  if (!out) return fail(nullptr, GP_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!hi || !hi->on_device) return fail(nullptr, GP_EINVAL, "the high-precision context must be on a device");
+  if (hi->plan.precision == GP_FP32) return fail(nullptr, GP_EINVAL, "hi must be GP_FP64 or GP_FP64_FF");
+  if (lo) {
+    if (!lo->on_device || lo->device != hi->device) return fail(nullptr, GP_EINVAL, "lo must be on hi's device");
+    if (lo->plan.precision != GP_FP32) return fail(nullptr, GP_EINVAL, "lo must be GP_FP32");
+    const gp::Plan &a = hi->plan, &b = lo->plan;
+    if (a.dim != b.dim || a.n != b.n || a.k != b.k || a.n_active != b.n_active || a.num_faces() != b.num_faces() ||
+        a.h != b.h)
+      return fail(nullptr, GP_EINVAL, "hi and lo must describe the same mesh, degree and level set");
+  }
+  gp_system* s = new (std::nothrow) gp_system();
+  if (!s) return fail(nullptr, GP_ENOMEM, "host allocation failed");
+  s->hi = hi;
+  s->lo = lo;
+  s->device = hi->device;
+  s->n = hi->plan.n_active;
+  DeviceGuard dg(s->device);
+  gp::Plan& p = hi->plan;
+  if (p.crow.empty() && p.n_active > 0) gp::build_cell_table(p);
+  std::memcpy(s->cstart, p.cstart, sizeof(s->cstart));
+  s->cells_hi = cells_for(p);
+  if (lo) s->cells_lo = cells_for(lo->plan);
+  auto cleanup = [&](cudaError_t e) {
+    std::string m = std::string("system setup: ") + cudaGetErrorString(e);
+    sys_free(s);
+    delete s;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !p.crow.empty()) e = cudaMalloc(&s->d_crow, p.crow.size() * sizeof(int32_t));
+  if (e == cudaSuccess && !p.crow.empty())
+    e = cudaMemcpy(s->d_crow, p.crow.data(), p.crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  const size_t n8 = (size_t)std::max<int64_t>(s->n, 1) * 8, n4 = (size_t)std::max<int64_t>(s->n, 1) * 4;
+  if (e == cudaSuccess) e = cudaMalloc(&s->r, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->p, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->q, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dd, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->z, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ri, n8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dinv, n8);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->z32, n4);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->dinv32, n4);
+  if (e == cudaSuccess && s->n > 0) {
+    // Jacobi: inverse diagonal of the model system, computed on the host in FP64
+    std::vector<double> diag;
+    gp::build_diagonal(p, diag);
+    std::vector<double> inv(diag.size());
+    std::vector<float> inv32(diag.size());
+    for (size_t i = 0; i < diag.size(); ++i) {
+      inv[i] = diag[i] > 0 ? 1.0 / diag[i] : 1.0;
+      inv32[i] = (float)inv[i];
+    }
+    e = cudaMemcpy(s->dinv, inv.data(), n8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && lo) e = cudaMemcpy(s->dinv32, inv32.data(), n4, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->r32, n4);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->d32, n4);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->ri32, n4);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->p32, n4);
+  if (e == cudaSuccess && lo) e = cudaMalloc(&s->q32, n4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, (kDotBlocks + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, sizeof(double));
+  if (e != cudaSuccess) return cleanup(e);
+  *out = s;
+  return GP_OK;
+}
+
+gp_status gp_system_apply(gp_system* s, int which, const void* x, void* y, void* stream) {
+  if (!s) return fail(nullptr, GP_EINVAL, "null system");
+  gp_ctx* c = which == 0 ? s->hi : s->lo;
+  if (!c) return fail(nullptr, GP_EINVAL, "this system has no FP32 operator");
+  if (s->n > 0 && (!x || !y || x == y)) return fail(nullptr, GP_EINVAL, "bad x or y");
+  if (s->n == 0) return GP_OK;
+  DeviceGuard dg(s->device);
+  return sys_apply(s, c, which == 0 ? s->cells_hi : s->cells_lo, x, y, (cudaStream_t)stream);
+}
+
+gp_status gp_system_solve(gp_system* s, const double* b, double* u, const gp_solve_opts* o, gp_solve_stats* stats) {
+  if (!s || !b || !u || !o || !stats) return fail(nullptr, GP_EINVAL, "null argument");
+  if (o->mode == 0 && !s->lo) return fail(nullptr, GP_EINVAL, "defect correction needs the FP32 operator");
+  std::memset(stats, 0, sizeof(*stats));
+  DeviceGuard dg(s->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = s->n;
+  const bool jac = o->precond == 1;
+  gp_status g = GP_OK;
+  // outer loop on the true FP64 residual r = b - A_hi u; the correction A d = r is
+  // solved by FP32 PCG (mode 0, to inner_rtol) or FP64 PCG (mode 1, to what rtol needs)
+  SYS_CUDA(cudaMemsetAsync(u, 0, n * sizeof(double), s->st));
+  SYS_CUDA(cudaMemcpyAsync(s->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+  double bb = 0.0;
+  SYS_CUDA(dot<double>(s, b, b, &bb));
+  const double nb = std::sqrt(bb);
+  int outer = 0;
+  double rn = nb;
+  while (outer < o->max_outer) {
+    double rr = 0.0;
+    SYS_CUDA(dot<double>(s, s->r, s->r, &rr));
+    rn = std::sqrt(rr);
+    if (rn <= o->rtol * nb || rr == 0.0) break;
+    int it = 0, applies = 0;
+    if (o->mode == 0) {
+      to32_k<<<kVecBlocks, kThreads, 0, s->st>>>(s->r32, s->r, n);
+      g = cg<float>(s, s->lo, s->cells_lo, s->r32, s->d32, s->ri32, s->p32, s->q32, s->z32,
+                    jac ? s->dinv32 : nullptr, o->inner_rtol, o->max_inner, &it, &applies);
+      if (g != GP_OK) return g;
+      stats->lo_applies += applies;
+      add32_k<<<kVecBlocks, kThreads, 0, s->st>>>(u, s->d32, n);
+    } else {
+      const double tol = std::max(0.5 * o->rtol * nb / rn, 1e-15);
+      g = cg<double>(s, s->hi, s->cells_hi, s->r, s->dd, s->ri, s->p, s->q, s->z, jac ? s->dinv : nullptr, tol,
+                     o->max_inner, &it, &applies);
+      if (g != GP_OK) return g;
+      stats->hi_applies += applies;
+      add64_k<<<kVecBlocks, kThreads, 0, s->st>>>(u, s->dd, n);
+    }
+    stats->inner += it;
+    g = sys_apply(s, s->hi, s->cells_hi, u, s->q, s->st);
+    if (g != GP_OK) return g;
+    stats->hi_applies++;
+    resid_k<<<kVecBlocks, kThreads, 0, s->st>>>(s->r, b, s->q, n);
+    ++outer;
+  }
+  double rr = 0.0;
+  SYS_CUDA(dot<double>(s, s->r, s->r, &rr));
+  stats->outer = outer;
+  stats->rel_residual = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return GP_OK;
+}
+
+void gp_system_destroy(gp_system* s) {
+  if (!s) return;
+  DeviceGuard dg(s->device);
+  if (s->st) cudaStreamSynchronize(s->st);
+  sys_free(s);
+  delete s;
+}
+
+}  // extern "C"

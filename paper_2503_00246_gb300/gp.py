@@ -44,6 +44,16 @@ class gp_levelset(C.Structure):
                 ("samples", C.c_int)]
 
 
+class gp_solve_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
+                ("max_inner", C.c_int), ("mode", C.c_int), ("precond", C.c_int)]
+
+
+class gp_solve_stats(C.Structure):
+    _fields_ = [("outer", C.c_int), ("inner", C.c_int), ("hi_applies", C.c_int), ("lo_applies", C.c_int),
+                ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+
 class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
@@ -77,6 +87,10 @@ def _load():
         "gp_batch_apply": ([P, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_batch_info": ([P, i64p, i64p], C.c_int),
         "gp_batch_destroy": ([P], None),
+        "gp_system_create": ([P, P, C.POINTER(P)], C.c_int),
+        "gp_system_apply": ([P, C.c_int, P, P, P], C.c_int),
+        "gp_system_solve": ([P, P, P, C.POINTER(gp_solve_opts), C.POINTER(gp_solve_stats)], C.c_int),
+        "gp_system_destroy": ([P], None),
         "gp_profile_enable": ([P, C.c_int], C.c_int),
         "gp_profile_read": ([P, C.POINTER(C.c_double), i64p], C.c_int),
         "gp_last_error": ([P], C.c_char_p),
@@ -97,7 +111,8 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_cell_classes", "gp_reference_1d", "gp_apply", "gp_apply_add", "gp_apply_host",
                "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
                "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
-               "gp_batch_destroy")
+               "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
+               "gp_system_destroy")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -266,6 +281,52 @@ def gp_batch_info(batch: Batch):
 
 def gp_batch_destroy(batch: Batch):
     batch.close()
+
+
+class System:
+    """Owns a gp_system handle; keeps its contexts alive."""
+
+    def __init__(self, handle, hi, lo):
+        self.handle, self.hi, self.lo = handle, hi, lo
+
+    def close(self):
+        if self.handle:
+            lib.gp_system_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gp_system_create(hi: Context, lo: Context | None = None) -> System:
+    h = C.c_void_p()
+    _check(lib.gp_system_create(hi.handle, lo.handle if lo is not None else None, C.byref(h)))
+    return System(h.value, hi, lo)
+
+
+def gp_system_apply(sys: System, which: int, x, y, stream=None):
+    ctx = sys.hi if which == 0 else sys.lo
+    _check_vec(ctx, x)
+    _check_vec(ctx, y)
+    _check(lib.gp_system_apply(sys.handle, which, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def gp_system_solve(sys: System, b, u, rtol=1e-10, inner_rtol=1e-4, max_outer=50, max_inner=20000, mode=0,
+                    precond=1):
+    """Solve (M+K+G) u = b; returns the gp_solve_stats as a dict."""
+    _check_vec(sys.hi, b)
+    _check_vec(sys.hi, u)
+    o = gp_solve_opts(rtol, inner_rtol, max_outer, max_inner, mode, precond)
+    st = gp_solve_stats()
+    _check(lib.gp_system_solve(sys.handle, _ptr(b), _ptr(u), C.byref(o), C.byref(st)))
+    return {f: getattr(st, f) for f, _ in gp_solve_stats._fields_}
+
+
+def gp_system_destroy(sys: System):
+    sys.close()
 
 
 def gp_num_active_dofs(ctx: Context) -> int:

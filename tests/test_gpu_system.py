@@ -1,0 +1,75 @@
+"""GPU: the model system (M_active + K_active + G) against the oracle, and its solvers.
+
+The system's operator is checked element by element against the oracle's
+cell operator plus ghost penalty (FP64 / float-float: 1e-12, FP32: 1e-5).  The
+solvers are checked through the oracle: the solution must satisfy
+||b - A_oracle u|| <= 1e-9 ||b|| (the solvers stop at 1e-10 with the GPU operator),
+defect correction and plain FP64 CG must agree, and a solve is bitwise
+reproducible.
+"""
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+from oracle.cell_operator import CellOperator
+from oracle.ghost_penalty import Oracle
+from paper_2503_00246_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_system(pr):
+    o = Oracle(pr)
+    cop = CellOperator(pr, o.num, o.cls)
+    return o, (lambda x: o.apply(x) + cop.apply(x))
+
+
+@pytest.mark.parametrize("hi", [0, 2])
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 14), (2, 5, 8), (3, 1, 10), (3, 3, 8), (3, 4, 7)])
+def test_system_apply_matches_oracle(gplib, cuda, dim, k, n, hi):
+    pr = W.small_ball(dim, n, k, radius=0.6, seed=80 + k)
+    o, A = _oracle_system(pr)
+    chi = gplib.setup_problem(pr, precision=hi)
+    clo = gplib.setup_problem(pr, precision=1)
+    sysm = gplib.gp_system_create(chi, clo)
+    x = W.x_vectors(pr, chi.n_active)[0]
+    ref = A(x)
+    for which, dt, tol, xin in ((0, cuda.float64, 1e-12, x), (1, cuda.float32, 1e-5, x.astype(np.float32))):
+        xd = cuda.tensor(xin, dtype=dt, device="cuda")
+        yd = cuda.full_like(xd, float("nan"))
+        gplib.gp_system_apply(sysm, which, xd, yd)
+        cuda.cuda.synchronize()
+        y = yd.double().cpu().numpy()
+        r = ref if which == 0 else A(xin.astype(np.float64))
+        assert np.abs(y - r).max() <= tol * np.abs(r).max(), (which, np.abs(y - r).max() / np.abs(r).max())
+    sysm.close()
+
+
+@pytest.mark.parametrize("hi", [0, 2])
+def test_defect_correction_and_cg(gplib, cuda, hi):
+    pr = W.small_ball(3, 12, 3, radius=0.62, seed=91)
+    o, A = _oracle_system(pr)
+    chi = gplib.setup_problem(pr, precision=hi)
+    clo = gplib.setup_problem(pr, precision=1)
+    sysm = gplib.gp_system_create(chi, clo)
+    b = W.rhs_vector(pr, chi.n_active)
+    bd = cuda.tensor(b, dtype=cuda.float64, device="cuda")
+    u_dc = cuda.zeros_like(bd)
+    u_cg = cuda.zeros_like(bd)
+    st_dc = gplib.gp_system_solve(sysm, bd, u_dc, rtol=1e-10, inner_rtol=1e-4, mode=0)
+    st_cg = gplib.gp_system_solve(sysm, bd, u_cg, rtol=1e-10, mode=1)
+    u_np = cuda.zeros_like(bd)   # without the preconditioner: more iterations, same answer
+    st_np = gplib.gp_system_solve(sysm, bd, u_np, rtol=1e-10, mode=1, precond=0, max_inner=50000)
+    assert st_np["rel_residual"] <= 1e-10 and st_np["inner"] > st_cg["inner"]
+    for st in (st_dc, st_cg):
+        assert st["rel_residual"] <= 1e-10, st
+    assert st_dc["outer"] >= 2 and st_dc["lo_applies"] > 0
+    for u in (u_dc, u_cg):
+        un = u.cpu().numpy()
+        assert np.linalg.norm(b - A(un)) <= 1e-9 * np.linalg.norm(b)
+    a, c = u_dc.cpu().numpy(), u_cg.cpu().numpy()
+    assert np.linalg.norm(a - c) <= 1e-7 * np.linalg.norm(c)
+    u2 = cuda.zeros_like(bd)
+    gplib.gp_system_solve(sysm, bd, u2, rtol=1e-10, inner_rtol=1e-4, mode=0)
+    assert cuda.equal(u2, u_dc)            # fixed reduction order: bitwise reproducible
+    sysm.close()
