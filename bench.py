@@ -212,6 +212,35 @@ def run_batched(gp, W, torch, dev, prec, steps, warmup):
     return out
 
 
+def run_cg(args):
+    """The solver study: gyroid (iso 0.3) on [-pi,pi]^3, n^3 cells, k = 4, model system
+    (M_active + K_active + G) u = b, b ~ U[-1,1], per-order weights gamma / (j!)^2: FP32-inner
+    defect correction and FP64 PCG, both to relative residual 1e-10 (Jacobi), float-float as
+    the FP64-accuracy operator.  The full 128^3 mesh needs ~1e5 iterations; --cg-n picks n."""
+    import torch
+
+    from paper_2503_00246_gb300 import build as B
+    B.build()
+    from paper_2503_00246_gb300 import gp, workloads as W
+    t0 = time.perf_counter()
+    pr = W.gyroid_3d(k=4, n=args.cg_n)
+    pr.weights = W.paper_weights(0.5, 4)
+    hi = gp.setup_problem(pr, precision=gp.GP_FP64_FF, device=0)
+    lo = gp.setup_problem(pr, precision=gp.GP_FP32, device=0)
+    sysm = gp.gp_system_create(hi, lo)
+    b = torch.tensor(W.rhs_vector(pr, hi.n_active), dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(b)
+    setup = time.perf_counter() - t0
+    out = {"workload": f"{args.cg_n}^3 gyroid sin x cos y + sin y cos z + sin z cos x = 0.3 on [-pi,pi]^3, "
+                       "k=4, c_j = 0.5/(j!)^2, (M_active + K_active + G) u = b, b ~ U[-1,1]",
+           "n_active_dofs": hi.n_active, "ghost_faces": hi.n_faces, "setup_s": setup}
+    for name, mode in (("defect_correction_fp32_inner", 0), ("pcg_fp64", 1)):
+        st = gp.gp_system_solve(sysm, b, u, rtol=1e-10, inner_rtol=args.inner_rtol, mode=mode,
+                                max_inner=args.max_inner)
+        out[name] = st
+    print(json.dumps(out), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -472,7 +501,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg"])
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--max-inner", type=int, default=200000)
+    ap.add_argument("--cg-n", type=int, default=32)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--workload", default="ball64_k3", choices=sorted(WORKLOADS))
@@ -480,6 +512,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "profile":
         run_profile(args)
+    elif args.mode == "cg":
+        run_cg(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -73,3 +73,22 @@ def test_defect_correction_and_cg(gplib, cuda, hi):
     gplib.gp_system_solve(sysm, bd, u2, rtol=1e-10, inner_rtol=1e-4, mode=0)
     assert cuda.equal(u2, u_dc)            # fixed reduction order: bitwise reproducible
     sysm.close()
+
+
+def test_gyroid_k4_defect_correction_vs_fp64_pcg(gplib, cuda):
+    """The solver study on a 16^3 gyroid (iso 0.3), k = 4, with the paper's weights
+    c_j = gamma / (j!)^2: both solvers reach 1e-10, defect correction with a handful of
+    FP64 applies, and the solutions agree."""
+    pr = W.gyroid_3d(k=4, n=16)
+    pr.weights = W.paper_weights(0.5, 4)
+    hi = gplib.setup_problem(pr, precision=2)
+    lo = gplib.setup_problem(pr, precision=1)
+    sysm = gplib.gp_system_create(hi, lo)
+    b = cuda.tensor(W.rhs_vector(pr, hi.n_active), dtype=cuda.float64, device="cuda")
+    u_dc, u_cg = cuda.zeros_like(b), cuda.zeros_like(b)
+    st_dc = gplib.gp_system_solve(sysm, b, u_dc, rtol=1e-10, inner_rtol=1e-4, mode=0, max_inner=100000)
+    st_cg = gplib.gp_system_solve(sysm, b, u_cg, rtol=1e-10, mode=1, max_inner=100000)
+    assert st_dc["rel_residual"] <= 1e-10 and st_cg["rel_residual"] <= 1e-10
+    assert st_dc["hi_applies"] < 20 < st_cg["hi_applies"]
+    assert cuda.linalg.norm(u_dc - u_cg) <= 1e-6 * cuda.linalg.norm(u_cg)
+    sysm.close()
