@@ -101,6 +101,9 @@ typedef struct {
   int precision;            /* GP_FP64, GP_FP32 or GP_FP64_FF */
   int all_faces;            /* 1: penalise every interior face of the active mesh */
   int device;               /* CUDA device ordinal; -1 = build the host plan only */
+  int part_lo, part_hi;     /* 0, 0: the whole mesh.  Otherwise this context is the slab
+                               partition of cell layers [part_lo, part_hi) along the last
+                               axis (y in 2D, z in 3D); see gp_partition_info */
 } gp_opts;
 
 /* Classify cells, collect the ghost faces, number the active DoFs, build the
@@ -128,6 +131,47 @@ gp_status gp_cell_counts(const gp_ctx* ctx, int64_t counts[3]);
 gp_status gp_active_dof_coords(const gp_ctx* ctx, double* xyz);
 gp_status gp_ghost_faces(const gp_ctx* ctx, int32_t* axis, int64_t* cell);
 gp_status gp_cell_classes(const gp_ctx* ctx, int8_t* cls);
+
+/* ---- Slab partitions (Sec. 2.7 and Algorithm 1: distributed evaluation) ----
+ *
+ * The paper distributes the cells over MPI ranks with a weighted load balance,
+ * gives a face shared by two ranks to the lower rank, imports the ghost values
+ * of u before the face loop and adds the ghost contributions of w afterwards.
+ * Here a partition is a slab of whole cell layers [part_lo, part_hi) along the
+ * last axis (y in 2D, z in 3D), so that every exchange is one contiguous block:
+ *   - its faces are the ghost faces whose lower cell lies in the slab (the face
+ *     between two slabs belongs to the lower one);
+ *   - its vector holds, in global order, the active DoFs on the lattice planes
+ *     [part_lo k, min(part_hi + 1, n) k] of the last axis (one cell of halo above);
+ *   - entries [0, n_owned) are owned; [n_owned, n_local) is the halo, equal to the
+ *     first n_lower entries of the partition above; the first n_lower entries are
+ *     the halo of the partition below (n_lower = 0 for the first slab).
+ * One application: copy x[0, n_lower) of every partition to the halo of the one
+ * below, apply (gp_apply), then add y[n_owned, n_local) of every partition into
+ * y[0, n_lower) of the one above.  y[0, n_owned) is then the global result.  A slab
+ * with a neighbour on both sides needs at least two layers (GP_EINVAL otherwise).
+ * The model system (gp_system_create) takes whole meshes only. */
+typedef struct {
+  int32_t layer_lo, layer_hi;  /* cell layers of the slab */
+  int64_t offset;              /* global index of local entry 0 */
+  int64_t n_local;             /* local vector length (== gp_num_active_dofs) */
+  int64_t n_owned;             /* owned entries [0, n_owned) */
+  int64_t n_lower;             /* entries shared with the partition below */
+  int64_t n_global;            /* active DoFs of the whole mesh */
+} gp_partition;
+
+/* Partition layout of a context (a whole-mesh context reports one slab with
+ * offset 0 and n_owned == n_local == n_global). */
+gp_status gp_partition_info(const gp_ctx* ctx, gp_partition* out);
+
+/* Weighted slab partition for nparts processes: cell weight 0 outside, 1 inside,
+ * k^(d-1) cut (Sec. 2.7).  bounds (host, nparts + 1 entries, caller-owned)
+ * receives layer boundaries 0 = b_0 < ... < b_nparts = n: b_p is the first layer
+ * boundary where the prefix weight reaches p / nparts of the total, clamped so
+ * that every slab has at least two layers.  Needs n >= 2 nparts (GP_EINVAL
+ * otherwise).  opts->part_lo / part_hi and opts->device are ignored. */
+gp_status gp_partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
+                             int nparts, int32_t* bounds);
 
 /* The FP64 1D reference matrices of this context (Sec. 2.4, M^1 and G^1_k):
  *   mass  (k+1)^2 doubles, M^[a][b] = integral_0^1 phi_a phi_b;

@@ -21,6 +21,7 @@ Modules
   mesh          level-set cell classification, ghost-face set, active-DoF
                 numbering (lattice-lexicographic, x fastest, compacted)
   ghost_penalty explicit face matrices, y = G x, energy x^T G x, sampled rows
+  partition     weighted slab partitions, face owners and DoF windows (Sec. 2.7)
 
 Every function is pinned by the tests in ``tests/test_oracle_*.py`` against
 closed forms, brute force and invariants that do not reuse its formulas.

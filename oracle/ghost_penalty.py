@@ -115,12 +115,18 @@ class Oracle:
             self._pidx[axis] = self.num.patch_index(axis, self.faces[axis])
         return self._pidx[axis]
 
-    def apply(self, x: np.ndarray) -> np.ndarray:
-        """y = G x: loop over faces, y[patch] += A_F x[patch] (Algorithm 1, face loop)."""
+    def apply(self, x: np.ndarray, face_mask=None) -> np.ndarray:
+        """y = G x: loop over faces, y[patch] += A_F x[patch] (Algorithm 1, face loop).
+
+        ``face_mask`` (one bool array per axis) restricts the loop to a subset of
+        the faces, e.g. those one rank evaluates (Sec. 2.7).
+        """
         x = np.asarray(x, dtype=np.float64)
         y = np.zeros(self.n_active)
         for a in range(self.pr.dim):
             idx = self.patch_index(a)
+            if face_mask is not None:
+                idx = idx[face_mask[a]]
             if idx.shape[0] == 0:
                 continue
             yf = x[idx] @ self.A(a).T

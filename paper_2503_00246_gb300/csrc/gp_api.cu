@@ -239,6 +239,31 @@ gp_status gp_cell_classes(const gp_ctx* ctx, int8_t* cls) {
   return GP_OK;
 }
 
+gp_status gp_partition_info(const gp_ctx* ctx, gp_partition* out) {
+  if (!ctx || !out) return fail(ctx, GP_EINVAL, "null argument");
+  const gp::Plan& p = ctx->plan;
+  out->layer_lo = p.part_lo;
+  out->layer_hi = p.part_hi;
+  out->offset = p.g_offset;
+  out->n_local = p.n_active;
+  out->n_owned = p.n_owned;
+  out->n_lower = p.n_lower;
+  out->n_global = p.n_global;
+  return GP_OK;
+}
+
+gp_status gp_partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, int nparts,
+                             int32_t* bounds) {
+  try {
+    std::string err;
+    gp_status s = gp::partition_slabs(mesh, ls, opts, nparts, bounds, err);
+    if (s != GP_OK) return fail(nullptr, s, err);
+    return GP_OK;
+  } catch (const std::exception& e) {
+    return fail(nullptr, GP_ENOMEM, e.what());
+  }
+}
+
 gp_status gp_reference_1d(const gp_ctx* ctx, double* mass, double* jumps, double* scale) {
   if (!ctx || !mass || !jumps || !scale) return fail(ctx, GP_EINVAL, "null argument");
   const gp::Plan& p = ctx->plan;

@@ -413,8 +413,9 @@ void active_coords(const Plan& p, double* xyz) {
 
 // ---------------------------------------------------------------- plan --
 
-gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, Plan& p,
-                     std::string& err) {
+// Checks the arguments and classifies the cells (fills the mesh fields and cls).
+static gp_status classify_mesh(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, Plan& p,
+                               std::string& err) {
   if (!mesh || !ls || !opts) { err = "null argument"; return GP_EINVAL; }
   const int d = mesh->dim;
   if (d != 2 && d != 3) { err = "dim must be 2 or 3"; return GP_EINVAL; }
@@ -475,8 +476,67 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
   }
   for (int c = 0; c < 3; ++c) p.cell_counts[c] = 0;
   for (int64_t c = 0; c < p.ncell; ++c) p.cell_counts[(int)p.cls[c]]++;
+  return GP_OK;
+}
 
-  // ---- ghost faces, sorted by axis then lower cell
+// Cell weights for the load balance of Sec. 2.7: 0 outside, 1 inside, k^(d-1) cut.
+// Layer l (cells with last coordinate l) weighs C_{l+1} - C_l.  Boundary b_p is the
+// first layer boundary with C_b * nparts >= p * C_n, clamped to [2p, n - 2(nparts - p)]
+// and pushed up to b_{p-1} + 2: every partition holds at least two layers, so the halo
+// of a partition never reaches beyond its neighbour.
+gp_status partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, int nparts,
+                          int32_t* bounds, std::string& err) {
+  if (!bounds) { err = "null argument"; return GP_EINVAL; }
+  if (nparts < 1) { err = "nparts must be >= 1"; return GP_EINVAL; }
+  Plan p;
+  gp_status st = classify_mesh(mesh, ls, opts, p, err);
+  if (st != GP_OK) return st;
+  const int n = p.n;
+  if (nparts > 1 && n < 2 * nparts) { err = "fewer than two cell layers per partition"; return GP_EINVAL; }
+  const int64_t layer = p.ncell / n;
+  const int64_t wcut = ipow(p.k, p.dim - 1);
+  std::vector<int64_t> C(n + 1, 0);
+  for (int l = 0; l < n; ++l) {
+    int64_t w = 0;
+    for (int64_t c = (int64_t)l * layer; c < (int64_t)(l + 1) * layer; ++c)
+      w += p.cls[c] == INSIDE ? 1 : (p.cls[c] == CUT ? wcut : 0);
+    C[l + 1] = C[l] + w;
+  }
+  bounds[0] = 0;
+  bounds[nparts] = n;
+  for (int q = 1; q < nparts; ++q) {
+    int b = 0;
+    while (b < n && C[b] * nparts < q * C[n]) ++b;
+    b = std::max(b, 2 * q);
+    b = std::min(b, n - 2 * (nparts - q));
+    b = std::max(b, bounds[q - 1] + 2);
+    bounds[q] = b;
+  }
+  return GP_OK;
+}
+
+gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, Plan& p,
+                     std::string& err) {
+  gp_status st = classify_mesh(mesh, ls, opts, p, err);
+  if (st != GP_OK) return st;
+  const int d = p.dim, n = p.n, k = p.k;
+  const double h = p.h;
+
+  // ---- partition (Sec. 2.7): layers [part_lo, part_hi) of the last axis
+  p.partitioned = opts->part_lo != 0 || opts->part_hi != 0;
+  p.part_lo = p.partitioned ? opts->part_lo : 0;
+  p.part_hi = p.partitioned ? opts->part_hi : n;
+  if (p.partitioned) {
+    if (p.part_lo < 0 || p.part_hi > n || p.part_hi <= p.part_lo) { err = "bad partition layers"; return GP_EINVAL; }
+    if (p.part_lo > 0 && p.part_hi < n && p.part_hi - p.part_lo < 2) {
+      err = "a partition between two others needs at least two cell layers";
+      return GP_EINVAL;
+    }
+  }
+  const int64_t layer_cells = p.ncell / n;
+
+  // ---- ghost faces, sorted by axis then lower cell.  A face belongs to the partition of
+  // its lower cell: the lower rank of the two for a face across a partition boundary.
   p.face_cell.clear();
   const int64_t stride[3] = {1, n, (int64_t)n * n};
   for (int a = 0; a < d; ++a) {
@@ -484,6 +544,8 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
     for (int64_t c = 0; c < p.ncell; ++c) {
       int ia = (int)((c / stride[a]) % n);
       if (ia + 1 >= n) continue;
+      const int64_t lay = c / layer_cells;
+      if (lay < p.part_lo || lay >= p.part_hi) continue;
       int8_t c0 = p.cls[c], c1 = p.cls[c + stride[a]];
       if (c0 == OUTSIDE || c1 == OUTSIDE) continue;
       if (opts->all_faces || c0 == CUT || c1 == CUT) p.face_cell.push_back(c);
@@ -536,8 +598,38 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
     }
     p.run_off[row + 1] = (int32_t)(p.runs.size() / 2);
   }
-  p.n_active = total;
   if (total >= ((int64_t)1 << 31) - 1) { err = "too many active DoFs for 32-bit indices"; return GP_EUNSUPPORTED; }
+  p.n_global = total;
+  p.n_active = total;
+  p.g_offset = 0;
+  p.n_owned = total;
+  p.n_lower = 0;
+  if (p.partitioned) {
+    // keep the lattice planes [W0, W1] of the last axis, renumbered from 0
+    const int64_t rpp = d == 3 ? p.nl : 1;                 // lattice rows per plane
+    auto plane_start = [&](int64_t Z) { return Z * rpp < p.nrows ? p.row_start[Z * rpp] : total; };
+    const int64_t W0 = (int64_t)p.part_lo * k, W1 = (int64_t)std::min(p.part_hi + 1, n) * k;
+    p.g_offset = plane_start(W0);
+    p.n_active = plane_start(W1 + 1) - p.g_offset;
+    p.n_owned = (p.part_hi < n ? plane_start((int64_t)p.part_hi * k) : total) - p.g_offset;
+    p.n_lower = p.part_lo > 0 ? plane_start((int64_t)(p.part_lo + 1) * k + 1) - p.g_offset : 0;
+    std::vector<int32_t> runs2, off2(p.nrows + 1, 0);
+    for (int64_t row = 0; row < p.nrows; ++row) {
+      const int64_t Z = row / rpp;
+      if (Z >= W0 && Z <= W1) {
+        for (int r = p.run_off[row]; r < p.run_off[row + 1]; ++r) {
+          runs2.push_back(p.runs[2 * r]);
+          runs2.push_back(p.runs[2 * r + 1]);
+        }
+        p.row_start[row] -= p.g_offset;
+      } else {
+        p.row_start[row] = 0;
+      }
+      off2[row + 1] = (int32_t)(runs2.size() / 2);
+    }
+    p.runs.swap(runs2);
+    p.run_off.swap(off2);
+  }
 
   // ---- row table of the involved cells
   const int L = p.L;

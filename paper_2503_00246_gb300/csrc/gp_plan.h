@@ -65,6 +65,14 @@ struct Plan {
   int64_t num_active_cells() const { return ncact; }
   int64_t ncact = 0;
 
+  // slab partition (Sec. 2.7): cell layers [part_lo, part_hi) along the last axis.  The
+  // vector is the global numbering restricted to the lattice planes [part_lo k,
+  // min(part_hi + 1, n) k] of that axis: entries [0, n_owned) are owned, the rest is the
+  // one-cell halo above; the first n_lower entries are the halo of the partition below.
+  bool partitioned = false;
+  int part_lo = 0, part_hi = 0;
+  int64_t n_global = 0, g_offset = 0, n_owned = 0, n_lower = 0;
+
   // FP64 1D reference data
   std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
   std::vector<double> stiff;      // (k+1)^2: int_0^1 l_a' l_b' 
@@ -79,6 +87,10 @@ struct Plan {
 gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
                      Plan& p, std::string& err);
 void active_coords(const Plan& p, double* xyz);
+// Weighted slab partition of the cell layers along the last axis into nparts pieces;
+// bounds receives nparts + 1 layer indices.
+gp_status partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts, int nparts,
+                          int32_t* bounds, std::string& err);
 
 // 1D precompute (exposed for the unit tests through gp_reference_1d)
 void gauss_lobatto_01(int k, std::vector<double>& x);

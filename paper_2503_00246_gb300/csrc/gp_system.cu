@@ -200,6 +200,8 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   *out = nullptr;
   if (!hi || !hi->on_device) return fail(nullptr, GP_EINVAL, "the high-precision context must be on a device");
   if (hi->plan.precision == GP_FP32) return fail(nullptr, GP_EINVAL, "hi must be GP_FP64 or GP_FP64_FF");
+  if (hi->plan.partitioned || (lo && lo->plan.partitioned))
+    return fail(nullptr, GP_EUNSUPPORTED, "the model system is built for whole meshes only");
   if (lo) {
     if (!lo->on_device || lo->device != hi->device) return fail(nullptr, GP_EINVAL, "lo must be on hi's device");
     if (lo->plan.precision != GP_FP32) return fail(nullptr, GP_EINVAL, "lo must be GP_FP32");

@@ -57,7 +57,13 @@ class gp_solve_stats(C.Structure):
 class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int)]
+
+
+class gp_partition(C.Structure):
+    _fields_ = [("layer_lo", C.c_int32), ("layer_hi", C.c_int32), ("offset", C.c_int64),
+                ("n_local", C.c_int64), ("n_owned", C.c_int64), ("n_lower", C.c_int64),
+                ("n_global", C.c_int64)]
 
 
 def _load():
@@ -77,6 +83,9 @@ def _load():
         "gp_active_dof_coords": ([P, C.POINTER(C.c_double)], C.c_int),
         "gp_ghost_faces": ([P, C.POINTER(C.c_int32), i64p], C.c_int),
         "gp_cell_classes": ([P, C.POINTER(C.c_int8)], C.c_int),
+        "gp_partition_info": ([P, C.POINTER(gp_partition)], C.c_int),
+        "gp_partition_slabs": ([C.POINTER(gp_mesh), C.POINTER(gp_levelset), C.POINTER(gp_opts), C.c_int,
+                                C.POINTER(C.c_int32)], C.c_int),
         "gp_reference_1d": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
         "gp_apply": ([P, P, P, P], C.c_int),
         "gp_apply_add": ([P, P, P, P], C.c_int),
@@ -112,7 +121,7 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
                "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
-               "gp_system_destroy")
+               "gp_system_destroy", "gp_partition_info", "gp_partition_slabs")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -367,6 +376,21 @@ def gp_cell_classes(ctx: Context, n_cells: int) -> np.ndarray:
     return out
 
 
+def gp_partition_info(ctx: Context) -> dict:
+    """Layout of a slab partition: layer_lo, layer_hi, offset, n_local, n_owned, n_lower, n_global."""
+    out = gp_partition()
+    _check(lib.gp_partition_info(ctx.handle, C.byref(out)), ctx)
+    return {f: getattr(out, f) for f, _ in gp_partition._fields_}
+
+
+def gp_partition_slabs(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts, nparts: int) -> np.ndarray:
+    """Layer boundaries (nparts + 1 int32) of the weighted slab partition."""
+    b = np.zeros(nparts + 1, dtype=np.int32)
+    _check(lib.gp_partition_slabs(C.byref(mesh), C.byref(levelset), C.byref(opts), int(nparts),
+                                  b.ctypes.data_as(C.POINTER(C.c_int32))))
+    return b
+
+
 def gp_reference_1d(ctx: Context):
     k = ctx.degree
     m = np.zeros((k + 1) * (k + 1))
@@ -400,7 +424,7 @@ def gp_version() -> str:
 
 # ------------------------------------------------------------ marshalling --
 
-def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0):
+def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None):
     """gp_mesh / gp_levelset / gp_opts for a workloads.Problem (kept alive in the tuple)."""
     mesh = gp_mesh()
     mesh.dim = pr.dim
@@ -432,9 +456,18 @@ def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0):
     opts.precision = precision
     opts.all_faces = 1 if pr.all_faces else 0
     opts.device = device
+    if part is not None:
+        opts.part_lo, opts.part_hi = int(part[0]), int(part[1])
     return mesh, ls, opts, keep
 
 
-def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0) -> Context:
-    mesh, ls, opts, keep = structs_for(pr, precision, device)
+def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None) -> Context:
+    """Context for a workloads.Problem; part = (layer_lo, layer_hi) selects a slab partition."""
+    mesh, ls, opts, keep = structs_for(pr, precision, device, part)
     return gp_setup(mesh, ls, opts)
+
+
+def partition_problem(pr: W.Problem, nparts: int) -> np.ndarray:
+    """Layer boundaries of the weighted slab partition of a workloads.Problem."""
+    mesh, ls, opts, keep = structs_for(pr, GP_FP64, -1)
+    return gp_partition_slabs(mesh, ls, opts, nparts)
