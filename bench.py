@@ -168,19 +168,37 @@ def run_profile(args):
     tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     x = torch.tensor(W.x_vectors(pr, ctx.n_active)[0], dtype=tdt, device="cuda")
     y = torch.empty_like(x)
+    tiles = gp.gp_autotune(ctx, args.tune_reps)[0] if args.tune_reps > 0 else gp.gp_get_tiles(ctx)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")     # ncu --nvtx --nvtx-include "timed/" skips the tuning
     for _ in range(args.reps):
         gp.gp_apply(ctx, x, y)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     print(json.dumps({"workload": args.workload, "precision": args.precision, "n_active": ctx.n_active,
-                      "n_faces": ctx.n_faces, "n_touched": ctx.n_touched, "applies": args.reps}))
+                      "n_faces": ctx.n_faces, "n_touched": ctx.n_touched, "applies": args.reps,
+                      "tiles": tiles}))
 
 
-def run_batched(gp, W, torch, dev, prec, steps, warmup):
+def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):
     """The batched workload: 64 independent 3D ball problems, n ~ U{16..96}, k ~ U{2..6},
-    4 right-hand sides each, replayed as one CUDA graph per apply.  Inputs (> 7 GB) exceed L2."""
+    4 right-hand sides each, replayed as one CUDA graph per apply.  Inputs (> 7 GB) exceed L2.
+    With tune_reps > 0 the tile shape of every degree is tuned on that degree's largest
+    problem and used by the whole group."""
     probs = W.batched_3d()
     nrhs = 4
     ctxs = [gp.setup_problem(p, precision=prec, device=dev.index or 0) for p in probs]
+    tuned = {}
+    if tune_reps > 0:
+        by_k = {}
+        for p, c in zip(probs, ctxs):
+            by_k.setdefault(p.degree, []).append(c)
+        for k in sorted(by_k):
+            big = max(by_k[k], key=lambda c: c.n_faces)
+            t, _ = gp.gp_autotune(big, tune_reps)
+            for c in by_k[k]:
+                gp.gp_set_tiles(c, t)
+            tuned[str(k)] = t
     batch = gp.gp_batch_create(ctxs, nrhs)
     tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     gen = torch.Generator(device=dev)
@@ -203,7 +221,7 @@ def run_batched(gp, W, torch, dev, prec, steps, warmup):
            "problems": len(probs), "rhs": nrhs, "dof_vectors_per_apply": units,
            "ghost_faces": sum(c.n_faces for c in ctxs), "kernel_groups": ngroups,
            "graph_launches_per_apply": 1, "kernels_per_apply": 2 * ngroups,
-           "scratch_bytes": scratch}
+           "scratch_bytes": scratch, "tiles_per_degree": tuned or None}
     batch.close()
     for c in ctxs:
         c.close()
@@ -270,6 +288,11 @@ def run_gpu(args):
     precs = ([gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32] if args.precision == "both" else [names[args.precision]])
     for prec in precs:
         ctx = gp.setup_problem(pr, precision=prec, device=local)
+        tiles = None
+        if args.tune_reps > 0:          # tile shape picked on this GPU, before any timing
+            default = gp.gp_get_tiles(ctx)
+            chosen, (tf, tl) = gp.gp_autotune(ctx, args.tune_reps)
+            tiles = {"default": default, "chosen": chosen, "face_ms": tf, "lift_ms": tl}
         w = 4 if prec == gp.GP_FP32 else 8
         tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
         x_np = W.x_vectors(pr, ctx.n_active)[0]
@@ -286,6 +309,7 @@ def run_gpu(args):
         if prec == precs[0]:
             clocks.start()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         t0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(float(i))                 # evict x, y and the tables from L2
@@ -294,6 +318,7 @@ def run_gpu(args):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         if ws > 1:
             dist.barrier()
         ck = clocks.stop() if prec == precs[0] else None
@@ -355,6 +380,7 @@ def run_gpu(args):
             "clocks": ck,
             "n_active": ctx.n_active, "n_faces": nf, "n_touched": ctx.n_touched,
             "paper_flops_per_step": _flops_paper(d, k, nf),
+            "tiles": tiles,
         }
         ctx.close()
 
@@ -387,15 +413,16 @@ def run_gpu(args):
         "apply_hbm": {"achieved": r["apply_hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": r["apply_hbm_frac"],
                       "peak_source": peak_src},
         "kernel_ms": r["kernel_ms"],
+        "tiles": r["tiles"],
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
     }
     tags = {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff64"}
     for p in order[1:]:
         f = results[p]
         line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
-                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value")}
+                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value", "tiles")}
     if not args.no_batched:
-        line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2)
+        line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2, args.tune_reps)
                            for p in (gp.GP_FP64_FF, gp.GP_FP32)}
         line["batched"]["workload"] = ("64 independent 3D balls on [-1,1]^3, n ~ U{16..96}, k ~ U{2..6}, "
                                        "r ~ U[0.4,0.8], 4 right-hand sides, one CUDA graph per apply")
@@ -509,6 +536,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--workload", default="ball64_k3", choices=sorted(WORKLOADS))
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune-reps", type=int, default=5,
+                    help="timed launches per candidate tile shape before the run (0: default shapes)")
     args = ap.parse_args()
     if args.mode == "profile":
         run_profile(args)

@@ -173,6 +173,42 @@ gp_status gp_partition_info(const gp_ctx* ctx, gp_partition* out);
 gp_status gp_partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
                              int nparts, int32_t* bounds);
 
+/* ---- Tile shapes and the autotuner (no counterpart in the paper) ----
+ *
+ * The face kernel runs faces_per_cta faces per CTA (faces_per_cta * (k+1)^(d-1)
+ * threads, one per normal line); the lift kernel runs lift_threads threads per CTA
+ * over the rows of lift_cells_per_cta owner cells.  A field 0 means the default
+ * (about 256 threads, one row per thread).  Limits: at most 512 threads per CTA,
+ * lift_threads a multiple of 32, and at most 46 KB of dynamic shared memory per CTA
+ * (GP_EINVAL otherwise).  The shape changes the speed, never the result: every
+ * DoF is summed in the same fixed order. */
+typedef struct {
+  int faces_per_cta;
+  int lift_cells_per_cta;
+  int lift_threads;
+} gp_tiles;
+
+/* The context's current shape (defaults resolved). */
+gp_status gp_get_tiles(const gp_ctx* ctx, gp_tiles* out);
+/* Sets the context's shape (checked against the limits above). */
+gp_status gp_set_tiles(gp_ctx* ctx, const gp_tiles* tiles);
+
+/* Times every candidate shape of the face kernel (about 64 to 512 threads per
+ * CTA) and of the lift kernel (64 to 512 threads, one or two rows per thread)
+ * on this context's own tables: reps launches each, L2 flushed before every
+ * timed launch, CUDA events on a private stream.  Keeps the fastest face shape
+ * and the fastest lift shape in the context and records them in a
+ * process-wide table keyed by (device, d, k, precision), which gp_setup reads
+ * for every new context.  best (may be NULL) receives the shape, ms (may be
+ * NULL, 2 doubles) the mean face and lift kernel times in milliseconds.
+ * Allocates and frees two vectors and a 256 MB flush buffer; synchronises. */
+gp_status gp_autotune(gp_ctx* ctx, int reps, gp_tiles* best, double* ms);
+
+/* The process-wide table: record a shape (e.g. one read back from a cache
+ * file) or look one up (GP_EINVAL if absent). */
+gp_status gp_tiles_record(int device, int dim, int degree, int precision, const gp_tiles* tiles);
+gp_status gp_tiles_lookup(int device, int dim, int degree, int precision, gp_tiles* out);
+
 /* The FP64 1D reference matrices of this context (Sec. 2.4, M^1 and G^1_k):
  *   mass  (k+1)^2 doubles, M^[a][b] = integral_0^1 phi_a phi_b;
  *   jumps k*(2k+1) doubles, g_j[b] = jump of the j-th derivative of patch

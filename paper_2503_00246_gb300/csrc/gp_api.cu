@@ -67,7 +67,8 @@ void free_device(gp_ctx* c) {
 
 }  // namespace
 
-gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace) {
+gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace,
+                      const gp::Tiles* tiles, int which) {
   const gp::Plan& p = c->plan;
   gp::ApplyArgs a;
   a.dim = p.dim;
@@ -100,6 +101,8 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
     c->nprof++;
   }
   a.ev = ev;
+  a.tiles = tiles ? *tiles : c->tiles;
+  a.which = which;
   cudaError_t e;
   if (p.precision == GP_FP64)
     e = p.dim == 2 ? gp::apply_f64_d2(a, st) : gp::apply_f64_d3(a, st);
@@ -178,6 +181,7 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
       return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
     }
     c->on_device = true;
+    gpi::tiles_lookup(c->device, c->plan.dim, c->plan.k, c->plan.precision, &c->tiles);
   }
   *out = c;
   return GP_OK;
@@ -401,6 +405,7 @@ struct gp_batch {
     void* h_ptrs[2] = {nullptr, nullptr};  // pinned: read by the graph's copy node at replay
     int face_blocks = 0, lift_blocks = 0;
     gp::BatchOps ops{};
+    gp::Tiles tiles{};                 // the tile shape of the group's first context
   };
   std::vector<Group> groups;
   void* d_w = nullptr;
@@ -475,6 +480,7 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       b->groups[gi].k = pl.k;
       b->groups[gi].prec = pl.precision;
       b->groups[gi].ops = ops_for(pl.precision, pl.dim);
+      b->groups[gi].tiles = ctxs[p]->tiles;
     } else {
       gi = it->second;
     }
@@ -519,7 +525,10 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       for (int j = 0; j < pl.k; ++j) sp.s[j] = pl.scale[j];
     }
     std::vector<unsigned char> fs, ls;
-    g.ops.pack(g.k, specs, fs, ls, g.face_blocks, g.lift_blocks);
+    if (!g.ops.pack(g.k, specs, g.tiles, fs, ls, g.face_blocks, g.lift_blocks)) {
+      e = cudaErrorInvalidConfiguration;
+      break;
+    }
     e = cudaMalloc(&g.d_fsegs, fs.size());
     if (e == cudaSuccess) e = cudaMemcpy(g.d_fsegs, fs.data(), fs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g.d_lsegs, ls.size());
@@ -540,7 +549,7 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
                           b->cap);
       if (e == cudaSuccess)
         e = g.ops.run(g.k, g.d_fsegs, g.d_lsegs, g.d_ptrs[i], (int)g.prob.size(), g.face_blocks, g.lift_blocks,
-                      pl0.jumps.data(), pl0.mass.data(), b->cap);
+                      pl0.jumps.data(), pl0.mass.data(), g.tiles, b->cap);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);

@@ -5,4 +5,5 @@ namespace gp {
 cudaError_t apply_f64_d2(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(2, ArF64, a, st) }
 BatchOps batch_ops_f64_d2() { GP_BATCH_OPS(2, ArF64) }
 CellsFn cells_f64_d2() { GP_CELLS_FN(2, ArF64) }
+TileOps tile_ops_f64_d2() { GP_TILE_OPS(2, ArF64) }
 }  // namespace gp

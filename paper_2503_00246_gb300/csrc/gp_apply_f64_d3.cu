@@ -5,4 +5,5 @@ namespace gp {
 cudaError_t apply_f64_d3(const ApplyArgs& a, cudaStream_t st) { GP_DISPATCH_K(3, ArF64, a, st) }
 BatchOps batch_ops_f64_d3() { GP_BATCH_OPS(3, ArF64) }
 CellsFn cells_f64_d3() { GP_CELLS_FN(3, ArF64) }
+TileOps tile_ops_f64_d3() { GP_TILE_OPS(3, ArF64) }
 }  // namespace gp

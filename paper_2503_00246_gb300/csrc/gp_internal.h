@@ -20,6 +20,7 @@ struct gp_ctx {
   void* d_tp = nullptr;          // per-face outputs W_F (scratch)
   void* d_xh = nullptr;          // gp_apply_host staging
   void* d_yh = nullptr;
+  gp::Tiles tiles{};             // tile shape of the face and lift launches (0: defaults)
   std::string err;
   // tracing: one event triple per traced apply
   bool prof = false;
@@ -48,7 +49,17 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m);
 
 // Enqueues y = G x (add = 0) or y += G x (add = 1) for context c; `scratch` replaces the
 // context's face-output buffer when given; `trace` = false never records events.
+// `tiles` overrides the context's tile shape; `which` (bit 0 face, bit 1 lift) drops a
+// kernel (the autotuner times them apart).
 gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
-                 bool trace = true);
+                 bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3);
+
+// Tile-shape helpers for the context's (dimension, arithmetic).
+gp::TileOps tile_ops(int dim, int precision);
+
+// Process-wide table of tuned tile shapes, keyed by (device, dimension, degree, precision);
+// gp_setup starts every context from the entry of its key, if there is one.
+bool tiles_lookup(int device, int dim, int k, int precision, gp::Tiles* out);
+void tiles_record(int device, int dim, int k, int precision, const gp::Tiles& t);
 
 }  // namespace gpi

@@ -31,9 +31,26 @@ struct Shape {
   static constexpr int L = (D == 2) ? (K + 1) : (K + 1) * (K + 1);  // tangential nodes per face
   static constexpr int NN = 2 * K + 1;                               // nodes on a normal line
   static constexpr int P = NN * L;                                   // patch nodes per face
-  static constexpr int FB = (256 / L) > 0 ? (256 / L) : 1;           // faces per CTA
-  static constexpr int NT = FB * L;                                  // threads per CTA
+  static constexpr int FB = (256 / L) > 0 ? (256 / L) : 1;           // default faces per CTA
 };
+
+// Tile shape of one (d, k, arithmetic) apply, picked per GPU by the autotuner:
+// faces per face CTA (fb * L threads), owner cells per lift CTA and lift threads.
+struct Tiles {
+  int32_t fb = 0;
+  int32_t lcb = 0;
+  int32_t lnt = 0;
+};
+
+constexpr int MAX_CTA_THREADS = 512;
+constexpr size_t MAX_DYN_SMEM = 46 * 1024;   // plus < 2 KB of static shared memory: under the 48 KB default
+
+// dynamic shared memory of the face kernel: the k jump planes (and the first
+// tangential pass in 3D) of fb faces
+template <int D, int K, typename V>
+__host__ __device__ constexpr size_t face_smem(int fb) {
+  return (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
+}
 
 // Kernel constants (passed by value; they sit in the constant bank).
 template <typename V, int K>
@@ -63,20 +80,23 @@ struct LiftArgs {
 };
 
 // ----------------------------------------------------------------- face --
-// One thread per (face, normal line tau); FB faces per CTA.  `blk` is the CTA's
-// index within its problem; `sc` points to the k scale factors s_j.
+// One thread per (face, normal line tau); fb faces per CTA (blockDim.x = fb L).
+// `blk` is the CTA's index within its problem; `sc` points to the k scale
+// factors s_j; `dsm` is the face_smem<D, K, V>(fb) bytes of dynamic shared memory.
 template <int D, int K, class A>
 __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
                                           typename A::IO* __restrict__ y, const FaceArgs& fa,
                                           const Consts<typename A::V, K>& c, const typename A::V* sc,
-                                          const int blk) {
+                                          const int blk, const int fb, unsigned char* dsm) {
   using S = Shape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
-  constexpr int L = S::L, FB = S::FB, NN = S::NN, K1 = K + 1;
-  __shared__ V buf[FB][K][L];
-  __shared__ V sb2[(D == 3) ? FB : 1][K][L];
+  constexpr int L = S::L, NN = S::NN, K1 = K + 1;
+  typedef V Plane[K][L];
+  Plane* buf = reinterpret_cast<Plane*>(dsm);            // [fb][K][L]
+  Plane* sb2 = buf + fb;                                  // [fb][K][L], 3D only
   __shared__ V sm[K1][K1];
+  const int nt = (int)blockDim.x;
 
   if (blk < fa.nzblocks) {
     // zero fill of the active DoFs outside every face patch (overwrite form only):
@@ -84,11 +104,11 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     __shared__ int2 zr[ZGROUP];
     const int r0 = blk * ZGROUP;
     const int nr = min(ZGROUP, fa.nzruns - r0);
-    if ((int)threadIdx.x < nr) zr[threadIdx.x] = __ldg(fa.zruns + r0 + threadIdx.x);
+    for (int i = threadIdx.x; i < nr; i += nt) zr[i] = __ldg(fa.zruns + r0 + i);   // nt may be < ZGROUP
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
       const int2 run = zr[r];
-      for (int i = threadIdx.x; i < run.y; i += S::NT) y[run.x + i] = IO(0);
+      for (int i = threadIdx.x; i < run.y; i += nt) y[run.x + i] = IO(0);
     }
     return;
   }
@@ -101,12 +121,12 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   if (D >= 3 && blk >= fa.bstart[2]) {
     axis = 2; fbase = fa.fstart[2]; fend = fa.fstart[3]; bbase = fa.bstart[2]; rbase = fa.rbase[2];
   }
-  const int f0 = fbase + (blk - bbase) * FB;
+  const int f0 = fbase + (blk - bbase) * fb;
   const int t = threadIdx.x;
   const int fl = t / L, tau = t - fl * L;
   const int f = f0 + fl;
   const bool valid = f < fend;
-  for (int i = t; i < K1 * K1; i += S::NT) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
+  for (int i = t; i < K1 * K1; i += nt) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
 
   // ---- gather this thread's normal line (2k+1 values)
   V v[NN];
@@ -128,13 +148,26 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
 #pragma unroll
     for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
   }
-  // ---- contract with the k jump vectors
+  // ---- contract with the k jump vectors.  Mirroring the patch about the face maps
+  // basis b to 2k - b, K- to K+ and d/dn to -d/dn, so g_j[2k - b] = (-1)^(j+1) g_j[b]
+  // (j = 1..k; row j - 1 of c.g): odd orders see v[b] + v[2k-b], even orders
+  // v[b] - v[2k-b], and only odd orders see the shared node b = k.
+  {
+    V vp[K], vm[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    V acc = vzero<V>();
+    for (int b = 0; b < K; ++b) {
+      vp[b] = vadd(v[b], v[NN - 1 - b]);
+      vm[b] = vsub(v[b], v[NN - 1 - b]);
+    }
 #pragma unroll
-    for (int b = 0; b < NN; ++b) acc = vfma(c.g[j][b], v[b], acc);
-    buf[fl][j][tau] = acc;
+    for (int j = 0; j < K; ++j) {
+      const bool odd = (j % 2) == 0;   // order j + 1
+      Dot<V> acc = dot_first(c.g[j][0], odd ? vp[0] : vm[0]);
+#pragma unroll
+      for (int b = 1; b < K; ++b) dot_fma(acc, c.g[j][b], odd ? vp[b] : vm[b]);
+      if (odd) dot_fma(acc, c.g[j][K], v[K]);
+      buf[fl][j][tau] = dot_value(acc);
+    }
   }
   __syncthreads();
 
@@ -147,20 +180,20 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      V acc = vzero<V>();
+      Dot<V> acc = dot_first(m1[0], buf[fl][j][K1 * t2]);
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], buf[fl][j][q + K1 * t2], acc);
-      sb2[fl][j][tau] = acc;
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], buf[fl][j][q + K1 * t2]);
+      sb2[fl][j][tau] = dot_value(acc);
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      V acc = vzero<V>();
+      Dot<V> acc = dot_first(m1[0], sb2[fl][j][t1]);
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], sb2[fl][j][t1 + K1 * q], acc);
-      out[j] = acc;
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], sb2[fl][j][t1 + K1 * q]);
+      out[j] = dot_value(acc);
     }
   } else {
     V m1[K1];
@@ -168,10 +201,10 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      V acc = vzero<V>();
+      Dot<V> acc = dot_first(m1[0], buf[fl][j][0]);
 #pragma unroll
-      for (int q = 0; q < K1; ++q) acc = vfma(m1[q], buf[fl][j][q], acc);
-      out[j] = acc;
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], buf[fl][j][q]);
+      out[j] = dot_value(acc);
     }
   }
 
@@ -179,7 +212,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   if (valid) {
     V sj[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) sj[j] = vfma(sc[j], out[j], vzero<V>());
+    for (int j = 0; j < K; ++j) sj[j] = vmul(sc[j], out[j]);
     V* dst = wp + (size_t)f * S::P;
     int pos0, pstride;
     if (axis == 0) {            // patch index b + NN * tau
@@ -195,22 +228,39 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
       pos0 = tau;
       pstride = K1 * K1;
     }
+    // W[b] = E_b + O_b and W[2k-b] = E_b - O_b, with E_b (O_b) the sum over odd
+    // (even) orders of g_j[b] s_j out_j; W[k] = E_k
 #pragma unroll
-    for (int b = 0; b < NN; ++b) {
-      V wv = vzero<V>();
+    for (int b = 0; b <= K; ++b) {
+      Dot<V> ev = dot_first(c.g[0][b], sj[0]);
 #pragma unroll
-      for (int j = 0; j < K; ++j) wv = vfma(c.g[j][b], sj[j], wv);
-      dst[pos0 + pstride * b] = wv;
+      for (int j = 2; j < K; j += 2) dot_fma(ev, c.g[j][b], sj[j]);
+      const V e = dot_value(ev);
+      if (b == K) {
+        dst[pos0 + pstride * b] = e;
+      } else if constexpr (K == 1) {
+        dst[pos0 + pstride * b] = e;
+        dst[pos0 + pstride * (NN - 1 - b)] = e;
+      } else {
+        Dot<V> ov = dot_first(c.g[1][b], sj[1]);
+#pragma unroll
+        for (int j = 3; j < K; j += 2) dot_fma(ov, c.g[j][b], sj[j]);
+        const V o = dot_value(ov);
+        dst[pos0 + pstride * b] = vadd(e, o);
+        dst[pos0 + pstride * (NN - 1 - b)] = vsub(e, o);
+      }
     }
   }
 }
 
+extern __shared__ __align__(16) unsigned char gp_dyn_smem[];
+
 template <int D, int K, class A>
-__global__ void __launch_bounds__(Shape<D, K>::NT)
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
 face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
-            typename A::IO* __restrict__ y, const FaceArgs fa,
+            typename A::IO* __restrict__ y, const FaceArgs fa, const int fb,
             const __grid_constant__ Consts<typename A::V, K> c) {
-  face_body<D, K, A>(x, wp, y, fa, c, c.s, blockIdx.x);
+  face_body<D, K, A>(x, wp, y, fa, c, c.s, blockIdx.x, fb, gp_dyn_smem);
 }
 
 // --------------------------------------------------------------- batches --
@@ -249,9 +299,9 @@ __device__ __forceinline__ int find_segment(const Seg* segs, const int nseg, con
 }
 
 template <int D, int K, class A>
-__global__ void __launch_bounds__(Shape<D, K>::NT)
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
 face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const int nseg,
-                    const SegPtrs<typename A::IO>* __restrict__ ptrs,
+                    const SegPtrs<typename A::IO>* __restrict__ ptrs, const int fb,
                     const __grid_constant__ Consts<typename A::V, K> c) {
   __shared__ FaceSeg<typename A::V, K> seg;
   __shared__ SegPtrs<typename A::IO> sp;
@@ -261,7 +311,7 @@ face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const in
     sp = ptrs[s];
   }
   __syncthreads();
-  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, seg.s, (int)blockIdx.x - seg.block0);
+  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, seg.s, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
 }
 
 // ----------------------------------------------------------------- lift --
@@ -280,8 +330,8 @@ template <int D, int K>
 struct LiftShape {
   static constexpr int KR = (D == 3) ? K * K : K;   // x-rows per owner cell
   static constexpr int CB0 = 256 / KR;
-  static constexpr int CB = CB0 < 1 ? 1 : CB0;      // owner cells per CTA
-  static constexpr int NT = 256;
+  static constexpr int CB = CB0 < 1 ? 1 : CB0;      // default owner cells per CTA
+  static constexpr int NT = 256;                    // default threads per CTA
   static constexpr int NW = (D == 3) ? 36 : 12;     // candidate faces per cell
   static constexpr int NTYPE = (D == 3) ? 4 : 2;
   // rows of type m (bit 0: q == 0, bit 1: r == 0)
@@ -296,11 +346,12 @@ struct LiftShape {
 // Native FP64: the adds of a missing face are skipped (FP64 issue is the scarce
 // resource on GB300; the host groups owner cells with the same candidate-face
 // pattern so that the skips are warp-uniform).  FP32 and float-float: branch-free
-// (a missing face reads face 0 and adds zeros), so all loads of the row are in
-// flight at once.
+// (a missing face reads face 0 and adds zeros), with the loads of each (axis, s_a)
+// group of up to four faces issued before their adds, so they are in flight together.
+// Either way each node adds its contributions in the order (axis, s_a, s_1, s_2).
 template <int D, int K, class A, int M>
 __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, const int* win, const int q,
-                                         const int r, typename A::V (&acc)[K], unsigned& found) {
+                                         const int r, Sum<typename A::V> (&acc)[K], unsigned& found) {
   using V = typename A::V;
   constexpr int K1 = K + 1, NN = 2 * K + 1;
   constexpr int P = Shape<D, K>::P;
@@ -308,6 +359,25 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
   constexpr bool QZ = (M & 1) != 0;   // q == 0
   constexpr bool RZ = (M & 2) != 0;   // r == 0 (3D)
   constexpr unsigned ALL = (1u << K) - 1u;
+  // patch position of node p = 0 of this row in the face (a, s_a, s_1, s_2), and how
+  // many of the row's k nodes that face reaches
+  auto where = [&](const int a, const int sa, const int s1, const int s2, int& cnt) -> int {
+    if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face
+      cnt = (sa == 0) ? 1 : K;
+      const int tq = q + (1 - s1) * K;
+      const int tr = (D == 3) ? r + (1 - s2) * K : 0;
+      return (2 - sa) * K + NN * (tq + K1 * tr);
+    }
+    cnt = (s1 == 0) ? 1 : K;
+    if (a == 1) {             // x index p + (1 - s1) k, normal b = q + (2 - s_a) k
+      const int bb = q + (2 - sa) * K;
+      const int tz = (D == 3) ? r + (1 - s2) * K : 0;
+      return (1 - s1) * K + K1 * (bb + NN * tz);
+    }
+    const int ty = q + (1 - s2) * K;   // normal z: x index p + (1 - s1) k, y index q + (1 - s2) k
+    const int bb = r + (2 - sa) * K;
+    return (1 - s1) * K + K1 * (ty + K1 * bb);
+  };
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     // zero-ness of the normal coordinate and of the two tangential coordinates
@@ -317,71 +387,99 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
 #pragma unroll
     for (int sa = 0; sa < 3; ++sa) {
       if (a != 0 && sa == 0 && !nz) continue;
+      if constexpr (SKIP) {
+        // native FP64: skip the adds of a missing face (warp-uniform by the host's cell order)
 #pragma unroll
-      for (int s1 = 0; s1 < 2; ++s1) {
-        if (s1 == 0 && !xz) continue;
+        for (int s1 = 0; s1 < 2; ++s1) {
+          if (s1 == 0 && !xz) continue;
 #pragma unroll
-        for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
-          if (D == 3 && s2 == 0 && !yz) continue;
-          const int w = (D == 3) ? a * 12 + sa * 4 + s1 * 2 + s2 : a * 6 + sa * 2 + s1;
-          const int f = win[w];
-          const bool ok = f >= 0;
-          if (SKIP && !ok) continue;
-          const V* src = wp + (size_t)(ok ? f : 0) * P;
-          // patch position of node p and how many of the row's nodes the face reaches
-          int pos, cnt;
-          if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face
-            const int tq = q + (1 - s1) * K;
-            const int tr = (D == 3) ? r + (1 - s2) * K : 0;
-            pos = (2 - sa) * K + NN * (tq + K1 * tr);
-            cnt = (sa == 0) ? 1 : K;
-          } else if (a == 1) {      // x index p + (1 - s1) k, normal b = q + (2 - s_a) k
-            const int bb = q + (2 - sa) * K;
-            const int tz = (D == 3) ? r + (1 - s2) * K : 0;
-            pos = (1 - s1) * K + K1 * (bb + NN * tz);
-            cnt = (s1 == 0) ? 1 : K;
-          } else {                  // normal z: x index p + (1 - s1) k, y index q + (1 - s2) k
-            const int ty = q + (1 - s2) * K;
-            const int bb = r + (2 - sa) * K;
-            pos = (1 - s1) * K + K1 * (ty + K1 * bb);
-            cnt = (s1 == 0) ? 1 : K;
+          for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
+            if (D == 3 && s2 == 0 && !yz) continue;
+            const int f = win[(D == 3) ? a * 12 + sa * 4 + s1 * 2 + s2 : a * 6 + sa * 2 + s1];
+            if (f < 0) continue;
+            int cnt;
+            const int pos = where(a, sa, s1, s2, cnt);
+            const V* src = wp + (size_t)f * P + pos;
+#pragma unroll
+            for (int p = 0; p < K; ++p)
+              if (p < cnt) sum_add(acc[p], src[p]);
+            found |= (cnt == 1) ? 1u : ALL;
           }
-          if (!ok) pos = 0;
+        }
+      } else {
+        // FP32 and float-float: branch-free.  All loads of the (up to 4) faces of this
+        // (a, s_a) are issued before their adds; a missing face reads face 0 and adds 0.
+        V ld[4 * K];
+        int n = 0;
 #pragma unroll
-          for (int p = 0; p < K; ++p) {
-            if (p < cnt) {
-              const V v = src[pos + p];
-              acc[p] = vadd(acc[p], (SKIP || ok) ? v : vzero<V>());
-            }
+        for (int s1 = 0; s1 < 2; ++s1) {
+          if (s1 == 0 && !xz) continue;
+#pragma unroll
+          for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
+            if (D == 3 && s2 == 0 && !yz) continue;
+            const int f = win[(D == 3) ? a * 12 + sa * 4 + s1 * 2 + s2 : a * 6 + sa * 2 + s1];
+            const bool ok = f >= 0;
+            int cnt;
+            const int pos = where(a, sa, s1, s2, cnt);
+            const V* src = wp + (size_t)(ok ? f : 0) * P + (ok ? pos : 0);
+#pragma unroll
+            for (int p = 0; p < K; ++p)
+              if (p < cnt) {
+                const V v = src[p];
+                ld[n++] = ok ? v : vzero<V>();
+              }
+            if (ok) found |= (cnt == 1) ? 1u : ALL;
           }
-          if (ok) found |= (cnt == 1) ? 1u : ALL;
+        }
+        n = 0;
+#pragma unroll
+        for (int s1 = 0; s1 < 2; ++s1) {
+          if (s1 == 0 && !xz) continue;
+#pragma unroll
+          for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
+            if (D == 3 && s2 == 0 && !yz) continue;
+            const int cnt = (a == 0) ? ((sa == 0) ? 1 : K) : ((s1 == 0) ? 1 : K);
+#pragma unroll
+            for (int p = 0; p < K; ++p)
+              if (p < cnt) sum_add(acc[p], ld[n++]);
+          }
         }
       }
     }
   }
 }
 
+// dynamic shared memory of the lift kernel: the candidate windows of cb cells
+template <int D, int K>
+__host__ __device__ constexpr size_t lift_smem(int cb) {
+  return (size_t)cb * (LiftShape<D, K>::NW + 1) * sizeof(int);
+}
+
+// cb owner cells per CTA; each of the blockDim.x threads takes the items g, g + nt, ...
+// of the cb * KR rows.
 template <int D, int K, class A>
 __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y,
-                                          const int add, const LiftArgs& la, const int blk) {
+                                          const int add, const LiftArgs& la, const int blk, const int cb,
+                                          unsigned char* dsm) {
   using S = LiftShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
-  constexpr int NW = S::NW, CB = S::CB;
-  __shared__ int win[CB][NW + 1];
-  const int cell0 = blk * CB;
-  const int t = threadIdx.x;
-  for (int idx = t; idx < NW * CB; idx += S::NT) {
+  constexpr int NW = S::NW;
+  typedef int Win[NW + 1];
+  Win* win = reinterpret_cast<Win*>(dsm);                // [cb][NW + 1]
+  const int cell0 = blk * cb;
+  const int t = threadIdx.x, nt = (int)blockDim.x;
+  for (int idx = t; idx < NW * cb; idx += nt) {
     const int ln = idx / NW, w = idx - ln * NW;
     win[ln][w] = (cell0 + ln < la.nlift) ? __ldg(la.lwin + (size_t)cell0 * NW + idx) : -1;
   }
   __syncthreads();
   // one pass: item -> (row type m, cell, row of that type); items sorted by type
-  constexpr int E1 = CB * S::count(0);
-  constexpr int E2 = E1 + CB * S::count(1);
-  constexpr int E3 = E2 + CB * S::count(2);
-  constexpr int ITEMS = CB * S::KR;
-  for (int g = t; g < ITEMS; g += S::NT) {
+  const int E1 = cb * S::count(0);
+  const int E2 = E1 + cb * S::count(1);
+  const int E3 = E2 + cb * S::count(2);
+  const int ITEMS = cb * S::KR;
+  for (int g = t; g < ITEMS; g += nt) {
     int m, local;
     if (g < E1) { m = 0; local = g; }
     else if (g < E2 || S::NTYPE == 2) { m = 1; local = g - E1; }
@@ -399,9 +497,9 @@ __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, 
     }
     const int row = q + (D == 3 ? K * r : 0);
     const int base = __ldg(la.lrow + (size_t)row * la.nlift + cell);
-    V acc[K];
+    Sum<V> acc[K];
 #pragma unroll
-    for (int p = 0; p < K; ++p) acc[p] = vzero<V>();
+    for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();
     unsigned found = 0;
     switch (m) {
       case 0: lift_row<D, K, A, 0>(wp, win[ci], q, r, acc, found); break;
@@ -415,23 +513,24 @@ __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, 
       if (!((found >> p) & 1u)) continue;
       const int idx = base + p;
       if (idx >= la.n_active) continue;
-      const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), acc[p]) : acc[p];
+      const V sv = dot_value(acc[p]);
+      const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), sv) : sv;
       y[idx] = to_io(outv, (IO*)nullptr);
     }
   }
 }
 
 template <int D, int K, class A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
 lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
-            const LiftArgs la) {
-  lift_body<D, K, A>(wp, y, add, la, blockIdx.x);
+            const LiftArgs la, const int cb) {
+  lift_body<D, K, A>(wp, y, add, la, blockIdx.x, cb, gp_dyn_smem);
 }
 
 template <int D, int K, class A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
 lift_kernel_batched(const LiftSeg* __restrict__ segs, const FaceSeg<typename A::V, K>* __restrict__ fsegs,
-                    const int nseg, const SegPtrs<typename A::IO>* __restrict__ ptrs) {
+                    const int nseg, const SegPtrs<typename A::IO>* __restrict__ ptrs, const int cb) {
   __shared__ LiftSeg seg;
   __shared__ typename A::V* wp;
   __shared__ typename A::IO* y;
@@ -442,7 +541,7 @@ lift_kernel_batched(const LiftSeg* __restrict__ segs, const FaceSeg<typename A::
     y = ptrs[s].y;
   }
   __syncthreads();
-  lift_body<D, K, A>(wp, y, 0, seg.la, (int)blockIdx.x - seg.block0);
+  lift_body<D, K, A>(wp, y, 0, seg.la, (int)blockIdx.x - seg.block0, cb, gp_dyn_smem);
 }
 
 }  // namespace gp

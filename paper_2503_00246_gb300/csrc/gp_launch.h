@@ -27,7 +27,71 @@ struct ApplyArgs {
   const double* m = nullptr; // host FP64: (k+1)^2
   const double* s = nullptr; // host FP64: k
   cudaEvent_t* ev = nullptr;  // optional: 3 events recorded around the two kernels
+  Tiles tiles{};              // 0 fields: the defaults of default_tiles
+  int which = 3;              // bit 0: face kernel, bit 1: lift kernel (the autotuner times them apart)
 };
+
+// Default tile shape: about 256 threads per CTA, one item per thread.
+template <int D, int K>
+Tiles default_tiles_t() {
+  Tiles t;
+  t.fb = Shape<D, K>::FB;
+  t.lcb = LiftShape<D, K>::CB;
+  t.lnt = LiftShape<D, K>::NT;
+  return t;
+}
+
+// Fills zero fields of t with the defaults and checks the limits of the kernels
+// (threads per CTA <= MAX_CTA_THREADS, lift threads a multiple of 32, dynamic
+// shared memory <= MAX_DYN_SMEM).  Returns false if t is out of range.
+template <int D, int K, typename V>
+bool resolve_tiles(Tiles& t) {
+  const Tiles d = default_tiles_t<D, K>();
+  if (t.fb == 0) t.fb = d.fb;
+  if (t.lcb == 0) t.lcb = d.lcb;
+  if (t.lnt == 0) t.lnt = d.lnt;
+  if (t.fb < 1 || t.fb * Shape<D, K>::L > MAX_CTA_THREADS || face_smem<D, K, V>(t.fb) > MAX_DYN_SMEM) return false;
+  if (t.lnt < 32 || t.lnt > MAX_CTA_THREADS || t.lnt % 32 != 0) return false;
+  if (t.lcb < 1 || lift_smem<D, K>(t.lcb) > MAX_DYN_SMEM) return false;
+  return true;
+}
+
+// Per (arithmetic, dimension): default tiles and range check for degree k.
+struct TileOps {
+  Tiles (*defaults)(int k);
+  bool (*resolve)(int k, Tiles& t);
+};
+TileOps tile_ops_f64_d2();
+TileOps tile_ops_f64_d3();
+TileOps tile_ops_f32_d2();
+TileOps tile_ops_f32_d3();
+TileOps tile_ops_ff_d2();
+TileOps tile_ops_ff_d3();
+
+#define GP_TILE_CASE(D, A, K) \
+  case K: return resolve_tiles<D, K, typename A::V>(t);
+#define GP_TILE_OPS(D, A)                                                                     \
+  TileOps ops;                                                                                \
+  ops.defaults = [](int k) -> Tiles {                                                         \
+    switch (k) {                                                                              \
+      case 1: return default_tiles_t<D, 1>();                                                 \
+      case 2: return default_tiles_t<D, 2>();                                                 \
+      case 3: return default_tiles_t<D, 3>();                                                 \
+      case 4: return default_tiles_t<D, 4>();                                                 \
+      case 5: return default_tiles_t<D, 5>();                                                 \
+      case 6: return default_tiles_t<D, 6>();                                                 \
+      case 7: return default_tiles_t<D, 7>();                                                 \
+      default: return default_tiles_t<D, 8>();                                                \
+    }                                                                                         \
+  };                                                                                          \
+  ops.resolve = [](int k, Tiles& t) -> bool {                                                 \
+    switch (k) {                                                                              \
+      GP_TILE_CASE(D, A, 1) GP_TILE_CASE(D, A, 2) GP_TILE_CASE(D, A, 3) GP_TILE_CASE(D, A, 4) \
+      GP_TILE_CASE(D, A, 5) GP_TILE_CASE(D, A, 6) GP_TILE_CASE(D, A, 7) GP_TILE_CASE(D, A, 8) \
+      default: return false;                                                                  \
+    }                                                                                         \
+  };                                                                                          \
+  return ops;
 
 // One entry point per (arithmetic, dimension); each dispatches on k = 1..8.
 cudaError_t apply_f64_d2(const ApplyArgs& a, cudaStream_t st);
@@ -48,6 +112,8 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   for (int p = 0; p < K + 1; ++p)
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(Ar.m[p * (K + 1) + q]);
   for (int j = 0; j < K; ++j) c.s[j] = from_host<V>(Ar.s[j]);
+  Tiles t = Ar.tiles;
+  if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
   FaceArgs fa;
   fa.frows = Ar.frows;
   for (int a = 0; a < 4; ++a) fa.rbase[a] = Ar.rbase[a];
@@ -58,18 +124,19 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   for (int a = 0; a < 4; ++a) fa.fstart[a] = Ar.fstart[a];
   for (int a = 0; a < D; ++a) {
     fa.bstart[a] = nb;
-    nb += (Ar.fstart[a + 1] - Ar.fstart[a] + S::FB - 1) / S::FB;
+    nb += (Ar.fstart[a + 1] - Ar.fstart[a] + t.fb - 1) / t.fb;
   }
   for (int a = D; a < 4; ++a) fa.bstart[a] = nb;
   const bool faces = Ar.fstart[D] > 0;
-  using LS = LiftShape<D, K>;
-  const int32_t nlb = (Ar.la.nlift + LS::CB - 1) / LS::CB;
+  const int32_t nlb = (Ar.la.nlift + t.lcb - 1) / t.lcb;
   if (Ar.ev) cudaEventRecord(Ar.ev[0], st);
-  if (nb > 0)
-    face_kernel<D, K, A><<<nb, S::NT, 0, st>>>((const IO*)Ar.x, (V*)Ar.tp, (IO*)Ar.y, fa, c);
+  if (nb > 0 && (Ar.which & 1))
+    face_kernel<D, K, A><<<nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>((const IO*)Ar.x, (V*)Ar.tp,
+                                                                          (IO*)Ar.y, fa, t.fb, c);
   if (Ar.ev) cudaEventRecord(Ar.ev[1], st);
-  if (nlb > 0 && faces)
-    lift_kernel<D, K, A><<<nlb, LS::NT, 0, st>>>((const V*)Ar.tp, (IO*)Ar.y, Ar.add, Ar.la);
+  if (nlb > 0 && faces && (Ar.which & 2))
+    lift_kernel<D, K, A><<<nlb, t.lnt, lift_smem<D, K>(t.lcb), st>>>((const V*)Ar.tp, (IO*)Ar.y, Ar.add, Ar.la,
+                                                                     t.lcb);
   if (Ar.ev) cudaEventRecord(Ar.ev[2], st);
   return cudaGetLastError();
 }
@@ -86,11 +153,10 @@ struct SegSpec {
 // Packs the segments of one (d, k, arithmetic) group into the device layouts of
 // FaceSeg<V, K> and LiftSeg, with the CTA offsets of both launches.
 template <int D, int K, class A>
-void pack_batch(const std::vector<SegSpec>& in, std::vector<unsigned char>& fsegs,
+bool pack_batch(const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned char>& fsegs,
                 std::vector<unsigned char>& lsegs, int& face_blocks, int& lift_blocks) {
   using V = typename A::V;
-  using S = Shape<D, K>;
-  using LS = LiftShape<D, K>;
+  if (!resolve_tiles<D, K, V>(t)) return false;
   fsegs.assign(in.size() * sizeof(FaceSeg<V, K>), 0);
   lsegs.assign(in.size() * sizeof(LiftSeg), 0);
   int fb = 0, lb = 0;
@@ -101,7 +167,7 @@ void pack_batch(const std::vector<SegSpec>& in, std::vector<unsigned char>& fseg
     int32_t nb = fs.fa.nzblocks;
     for (int a = 0; a < D; ++a) {
       fs.fa.bstart[a] = nb;
-      nb += (fs.fa.fstart[a + 1] - fs.fa.fstart[a] + S::FB - 1) / S::FB;
+      nb += (fs.fa.fstart[a + 1] - fs.fa.fstart[a] + t.fb - 1) / t.fb;
     }
     for (int a = D; a < 4; ++a) fs.fa.bstart[a] = nb;
     fs.wp = (V*)in[i].wp;
@@ -111,20 +177,22 @@ void pack_batch(const std::vector<SegSpec>& in, std::vector<unsigned char>& fseg
     LiftSeg ls;
     ls.la = in[i].la;
     ls.block0 = lb;
-    if (fs.fa.fstart[D] > 0) lb += (ls.la.nlift + LS::CB - 1) / LS::CB;
+    if (fs.fa.fstart[D] > 0) lb += (ls.la.nlift + t.lcb - 1) / t.lcb;
     std::memcpy(&fsegs[i * sizeof(FaceSeg<V, K>)], &fs, sizeof(fs));
     std::memcpy(&lsegs[i * sizeof(LiftSeg)], &ls, sizeof(ls));
   }
   face_blocks = fb;
   lift_blocks = lb;
+  return true;
 }
 
 template <int D, int K, class A>
 cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, int nseg, int face_blocks,
-                      int lift_blocks, const double* g, const double* m, cudaStream_t st) {
+                      int lift_blocks, const double* g, const double* m, Tiles t, cudaStream_t st) {
   using V = typename A::V;
   using IO = typename A::IO;
   using S = Shape<D, K>;
+  if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
   Consts<V, K> c;
   for (int j = 0; j < K; ++j)
     for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
@@ -132,20 +200,20 @@ cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, in
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
   for (int j = 0; j < K; ++j) c.s[j] = vzero<V>();   // per segment, in FaceSeg
   if (face_blocks > 0)
-    face_kernel_batched<D, K, A><<<face_blocks, S::NT, 0, st>>>((const FaceSeg<V, K>*)fsegs, nseg,
-                                                               (const SegPtrs<IO>*)ptrs, c);
+    face_kernel_batched<D, K, A><<<face_blocks, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>(
+        (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs, t.fb, c);
   if (lift_blocks > 0)
-    lift_kernel_batched<D, K, A><<<lift_blocks, LiftShape<D, K>::NT, 0, st>>>(
-        (const LiftSeg*)lsegs, (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs);
+    lift_kernel_batched<D, K, A><<<lift_blocks, t.lnt, lift_smem<D, K>(t.lcb), st>>>(
+        (const LiftSeg*)lsegs, (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs, t.lcb);
   return cudaGetLastError();
 }
 
 // Per translation unit: batch packing and launch for one (arithmetic, dimension).
 struct BatchOps {
-  void (*pack)(int k, const std::vector<SegSpec>&, std::vector<unsigned char>&, std::vector<unsigned char>&,
-               int&, int&);
+  bool (*pack)(int k, const std::vector<SegSpec>&, Tiles&, std::vector<unsigned char>&,
+               std::vector<unsigned char>&, int&, int&);
   cudaError_t (*run)(int k, const void*, const void*, const void*, int, int, int, const double*, const double*,
-                     cudaStream_t);
+                     Tiles, cudaStream_t);
 };
 BatchOps batch_ops_f64_d2();
 BatchOps batch_ops_f64_d3();
@@ -156,30 +224,31 @@ BatchOps batch_ops_ff_d3();
 
 #define GP_BATCH_OPS(D, A)                                                                              \
   BatchOps ops;                                                                                         \
-  ops.pack = [](int k, const std::vector<SegSpec>& in, std::vector<unsigned char>& fs,                  \
-                std::vector<unsigned char>& ls, int& fb, int& lb) {                                     \
+  ops.pack = [](int k, const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned char>& fs,       \
+                std::vector<unsigned char>& ls, int& fb, int& lb) -> bool {                             \
     switch (k) {                                                                                        \
-      case 1: pack_batch<D, 1, A>(in, fs, ls, fb, lb); break;                                           \
-      case 2: pack_batch<D, 2, A>(in, fs, ls, fb, lb); break;                                           \
-      case 3: pack_batch<D, 3, A>(in, fs, ls, fb, lb); break;                                           \
-      case 4: pack_batch<D, 4, A>(in, fs, ls, fb, lb); break;                                           \
-      case 5: pack_batch<D, 5, A>(in, fs, ls, fb, lb); break;                                           \
-      case 6: pack_batch<D, 6, A>(in, fs, ls, fb, lb); break;                                           \
-      case 7: pack_batch<D, 7, A>(in, fs, ls, fb, lb); break;                                           \
-      default: pack_batch<D, 8, A>(in, fs, ls, fb, lb); break;                                          \
+      case 1: return pack_batch<D, 1, A>(in, t, fs, ls, fb, lb);                                        \
+      case 2: return pack_batch<D, 2, A>(in, t, fs, ls, fb, lb);                                        \
+      case 3: return pack_batch<D, 3, A>(in, t, fs, ls, fb, lb);                                        \
+      case 4: return pack_batch<D, 4, A>(in, t, fs, ls, fb, lb);                                        \
+      case 5: return pack_batch<D, 5, A>(in, t, fs, ls, fb, lb);                                        \
+      case 6: return pack_batch<D, 6, A>(in, t, fs, ls, fb, lb);                                        \
+      case 7: return pack_batch<D, 7, A>(in, t, fs, ls, fb, lb);                                        \
+      case 8: return pack_batch<D, 8, A>(in, t, fs, ls, fb, lb);                                        \
+      default: return false;                                                                            \
     }                                                                                                   \
   };                                                                                                    \
   ops.run = [](int k, const void* fs, const void* ls, const void* pt, int ns, int fb, int lb,          \
-               const double* g, const double* m, cudaStream_t st) -> cudaError_t {                      \
+               const double* g, const double* m, Tiles t, cudaStream_t st) -> cudaError_t {             \
     switch (k) {                                                                                        \
-      case 1: return run_batch<D, 1, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 2: return run_batch<D, 2, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 3: return run_batch<D, 3, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 4: return run_batch<D, 4, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 5: return run_batch<D, 5, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 6: return run_batch<D, 6, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 7: return run_batch<D, 7, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
-      case 8: return run_batch<D, 8, A>(fs, ls, pt, ns, fb, lb, g, m, st);                              \
+      case 1: return run_batch<D, 1, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 2: return run_batch<D, 2, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 3: return run_batch<D, 3, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 4: return run_batch<D, 4, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 5: return run_batch<D, 5, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 6: return run_batch<D, 6, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 7: return run_batch<D, 7, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 8: return run_batch<D, 8, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
       default: return cudaErrorInvalidValue;                                                            \
     }                                                                                                   \
   };                                                                                                    \

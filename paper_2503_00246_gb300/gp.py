@@ -60,6 +60,10 @@ class gp_opts(C.Structure):
                 ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int)]
 
 
+class gp_tiles(C.Structure):
+    _fields_ = [("faces_per_cta", C.c_int), ("lift_cells_per_cta", C.c_int), ("lift_threads", C.c_int)]
+
+
 class gp_partition(C.Structure):
     _fields_ = [("layer_lo", C.c_int32), ("layer_hi", C.c_int32), ("offset", C.c_int64),
                 ("n_local", C.c_int64), ("n_owned", C.c_int64), ("n_lower", C.c_int64),
@@ -83,6 +87,11 @@ def _load():
         "gp_active_dof_coords": ([P, C.POINTER(C.c_double)], C.c_int),
         "gp_ghost_faces": ([P, C.POINTER(C.c_int32), i64p], C.c_int),
         "gp_cell_classes": ([P, C.POINTER(C.c_int8)], C.c_int),
+        "gp_get_tiles": ([P, C.POINTER(gp_tiles)], C.c_int),
+        "gp_set_tiles": ([P, C.POINTER(gp_tiles)], C.c_int),
+        "gp_autotune": ([P, C.c_int, C.POINTER(gp_tiles), C.POINTER(C.c_double)], C.c_int),
+        "gp_tiles_record": ([C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(gp_tiles)], C.c_int),
+        "gp_tiles_lookup": ([C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(gp_tiles)], C.c_int),
         "gp_partition_info": ([P, C.POINTER(gp_partition)], C.c_int),
         "gp_partition_slabs": ([C.POINTER(gp_mesh), C.POINTER(gp_levelset), C.POINTER(gp_opts), C.c_int,
                                 C.POINTER(C.c_int32)], C.c_int),
@@ -121,7 +130,8 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_apply_batched", "gp_profile_enable", "gp_profile_read", "gp_last_error",
                "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
-               "gp_system_destroy", "gp_partition_info", "gp_partition_slabs")
+               "gp_system_destroy", "gp_partition_info", "gp_partition_slabs", "gp_get_tiles",
+               "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -374,6 +384,48 @@ def gp_cell_classes(ctx: Context, n_cells: int) -> np.ndarray:
     out = np.zeros(n_cells, dtype=np.int8)
     _check(lib.gp_cell_classes(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_int8))), ctx)
     return out
+
+
+def _tiles_dict(t: gp_tiles) -> dict:
+    return {f: getattr(t, f) for f, _ in gp_tiles._fields_}
+
+
+def _tiles_struct(d: dict) -> gp_tiles:
+    t = gp_tiles()
+    for f, _ in gp_tiles._fields_:
+        setattr(t, f, int(d.get(f, 0)))
+    return t
+
+
+def gp_get_tiles(ctx: Context) -> dict:
+    """faces_per_cta, lift_cells_per_cta, lift_threads of the context."""
+    t = gp_tiles()
+    _check(lib.gp_get_tiles(ctx.handle, C.byref(t)), ctx)
+    return _tiles_dict(t)
+
+
+def gp_set_tiles(ctx: Context, tiles: dict):
+    _check(lib.gp_set_tiles(ctx.handle, C.byref(_tiles_struct(tiles))), ctx)
+
+
+def gp_autotune(ctx: Context, reps: int = 10):
+    """Times the candidate tile shapes on the context; returns (tiles, (face_ms, lift_ms))."""
+    t = gp_tiles()
+    ms = (C.c_double * 2)()
+    _check(lib.gp_autotune(ctx.handle, int(reps), C.byref(t), ms), ctx)
+    return _tiles_dict(t), (ms[0], ms[1])
+
+
+def gp_tiles_record(device: int, dim: int, degree: int, precision: int, tiles: dict):
+    _check(lib.gp_tiles_record(device, dim, degree, precision, C.byref(_tiles_struct(tiles))))
+
+
+def gp_tiles_lookup(device: int, dim: int, degree: int, precision: int):
+    """The process-wide entry for the key, or None."""
+    t = gp_tiles()
+    if lib.gp_tiles_lookup(device, dim, degree, precision, C.byref(t)) != GP_OK:
+        return None
+    return _tiles_dict(t)
 
 
 def gp_partition_info(ctx: Context) -> dict:

@@ -161,3 +161,41 @@ def test_reference_1d_high_precision(gplib, k):
                     prod[p + q] += ca * cb
             Mref[a, b] = float(sum(c / (p + 1) for p, c in enumerate(prod)))
     assert np.abs(M - Mref).max() <= 2e-15 * np.abs(Mref).max()
+
+
+def test_tile_shapes_host(gplib):
+    # defaults, range checks and the process-wide table (no kernel runs)
+    ctx = gplib.setup_problem(W.small_ball(3, 8, 3, seed=2), precision=2, device=-1)
+    t = gplib.gp_get_tiles(ctx)
+    assert t["faces_per_cta"] * 16 <= 512 and t["lift_threads"] % 32 == 0
+    good = {"faces_per_cta": 32, "lift_cells_per_cta": 8, "lift_threads": 128}
+    gplib.gp_set_tiles(ctx, good)
+    assert gplib.gp_get_tiles(ctx) == good
+    for bad in [{"faces_per_cta": 33}, {"lift_threads": 100}, {"lift_threads": 1024},
+                {"lift_cells_per_cta": 1000}, {"faces_per_cta": -1}]:
+        with pytest.raises(gplib.GpError):
+            gplib.gp_set_tiles(ctx, bad)
+    assert gplib.gp_get_tiles(ctx) == good
+    with pytest.raises(gplib.GpError):
+        gplib.gp_tiles_record(0, 4, 3, 0, good)
+    with pytest.raises(gplib.GpError):
+        gplib.gp_autotune(ctx)                      # host-only context
+    gplib.gp_tiles_record(-1, 2, 7, 1, {"faces_per_cta": 4})
+    assert gplib.gp_tiles_lookup(-1, 2, 7, 1) == {"faces_per_cta": 4, "lift_cells_per_cta": 0, "lift_threads": 0}
+    assert gplib.gp_tiles_lookup(-1, 2, 6, 1) is None
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_jump_vectors_mirror_symmetry(gplib, k):
+    # Reflecting the patch about the face swaps K- and K+, maps basis b to 2k - b and
+    # flips d/dn: g_j[2k - b] = (-1)^(j+1) g_j[b], so g_j[k] = 0 for even j.  The face
+    # kernel uses only b <= k of each g_j and relies on this.
+    ctx = gplib.setup_problem(W.small_ball(3, 6, k), device=-1)
+    _, g, _ = gplib.gp_reference_1d(ctx)
+    g = np.asarray(g).reshape(k, 2 * k + 1)
+    for j in range(1, k + 1):
+        row = g[j - 1]
+        scale = np.abs(row).max()
+        assert np.abs(row[::-1] * (-1) ** (j + 1) - row).max() <= 1e-14 * scale
+        if j % 2 == 0:
+            assert abs(row[k]) <= 1e-14 * scale

@@ -58,9 +58,14 @@ def test_defect_correction_and_cg(gplib, cuda, hi):
     u_cg = cuda.zeros_like(bd)
     st_dc = gplib.gp_system_solve(sysm, bd, u_dc, rtol=1e-10, inner_rtol=1e-4, mode=0)
     st_cg = gplib.gp_system_solve(sysm, bd, u_cg, rtol=1e-10, mode=1)
-    u_np = cuda.zeros_like(bd)   # without the preconditioner: more iterations, same answer
-    st_np = gplib.gp_system_solve(sysm, bd, u_np, rtol=1e-10, mode=1, precond=0, max_inner=50000)
-    assert st_np["rel_residual"] <= 1e-10 and st_np["inner"] > st_cg["inner"]
+    # without the preconditioner: more iterations to the same residual.  Compared at 1e-9:
+    # the attainable residual of unpreconditioned CG is the operator's rounding (about
+    # 1e-14 relative for float-float) times cond(A), which is near 1e-10 here.
+    u_j9, u_n9 = cuda.zeros_like(bd), cuda.zeros_like(bd)
+    st_j9 = gplib.gp_system_solve(sysm, bd, u_j9, rtol=1e-9, mode=1, precond=1)
+    st_n9 = gplib.gp_system_solve(sysm, bd, u_n9, rtol=1e-9, mode=1, precond=0, max_inner=50000)
+    assert st_j9["rel_residual"] <= 1e-9 and st_n9["rel_residual"] <= 1e-9
+    assert st_n9["inner"] > st_j9["inner"]
     for st in (st_dc, st_cg):
         assert st["rel_residual"] <= 1e-10, st
     assert st_dc["outer"] >= 2 and st_dc["lo_applies"] > 0
