@@ -40,6 +40,9 @@ FP64_FLOP_PER_CLK_SM = 4
 FP32_FLOP_PER_CLK_SM = 256
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# FP32 instructions per float-float multiply-add term of a compensated dot product: the exact
+# product (4) plus the two-sum into the running sum (6) plus the error accumulation (2)
+FF_OPS_PER_FMA = 12.0
 
 
 def _dist():
@@ -135,12 +138,20 @@ class Clocks:
 # ---------------------------------------------------------------- GPU arm --
 
 def _flops_face(d, k, nf):
-    """Flops of the face kernel as written: per normal line k dot products of length 2k+1
-    (jumps), (d-1) tangential passes of k (k+1)-term dot products, k scalings, and the
-    (2k+1) k-term normal expansion."""
+    """Flops the face kernel executes (a multiply-add counts 2, a multiply or add 1; an
+    n-term dot product 2n - 1), per normal line: the even-odd split (2k adds), the k
+    jump dot products (k + 1 terms for odd orders, k for even ones), (d-1) tangential
+    passes of k (k+1)-term dot products, k scalings, and the expansion (per node b <= k
+    one odd-order and, for b < k, one even-order partial sum, plus 2 adds)."""
     L = (k + 1) ** (d - 1)
-    per_line = k * (2 * k + 1) + (d - 1) * k * (k + 1) + k + (2 * k + 1) * k
-    return 2.0 * nf * L * per_line
+    n_odd, n_even = (k + 1) // 2, k // 2            # orders j = 1, 3, ... and j = 2, 4, ...
+    contraction = 2 * k + n_odd * (2 * (k + 1) - 1) + n_even * (2 * k - 1)
+    tangential = (d - 1) * k * (2 * (k + 1) - 1)
+    expansion = (k + 1) * (2 * n_odd - 1)
+    if k > 1:
+        expansion += k * ((2 * n_even - 1) + 2)
+    per_line = contraction + tangential + k + expansion
+    return float(nf) * L * per_line
 
 
 def _flops_paper(d, k, nf):
@@ -230,6 +241,85 @@ def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):
     return out
 
 
+def run_sweep(args):
+    """The degree sweep: 96^3 cells on [-1,1]^3, ball of radius 0.7, k = 1..8, y = G x in the
+    three arithmetic forms (tile shapes tuned first), L2 flushed between timed applies.
+    Reports GDoF/s, ghost faces/s, the face kernel's executed and the paper's flop rates
+    against each form's ALU peak, the apply's algorithmic HBM bytes/s, and the relative error
+    against the FP64 oracle (full oracle apply for k <= --sweep-check-kmax)."""
+    import torch
+
+    from paper_2503_00246_gb300 import build as B
+    B.build()
+    from paper_2503_00246_gb300 import gp, workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: fp32_peak / FF_OPS_PER_FMA}
+    tags = {gp.GP_FP64_FF: "ff64", gp.GP_FP64: "fp64", gp.GP_FP32: "fp32"}
+    ks = [int(v) for v in args.sweep_k.split(",")]
+    out = {"workload": "96^3 cells on [-1,1]^3, ball r = 0.7 (seeded centre offset), gamma = 0.5 for every order",
+           "peaks_tflops": {tags[p]: peak[p] for p in peak}, "hbm_gbs": hbm, "hbm_source": peak_src, "k": {}}
+    stream = torch.cuda.current_stream()
+    for k in ks:
+        pr = W.ball_3d_sweep(k)
+        rec = {}
+        ref = ref32 = None
+        for prec in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32):
+            ctx = gp.setup_problem(pr, precision=prec, device=0)
+            tiles = gp.gp_autotune(ctx, args.tune_reps)[0] if args.tune_reps > 0 else gp.gp_get_tiles(ctx)
+            tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
+            x_np = W.x_vectors(pr, ctx.n_active)[0]
+            x = torch.tensor(x_np, dtype=tdt, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                gp.gp_apply(ctx, x, y)
+            nsteps = args.sweep_steps
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+            gp.gp_profile_enable(ctx, True)
+            torch.cuda.synchronize()
+            for i in range(nsteps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                gp.gp_apply(ctx, x, y)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms_face, ms_lift, calls = gp.gp_profile_read(ctx)
+            gp.gp_profile_enable(ctx, False)
+            t = sum(a.elapsed_time(b) for a, b in ev) / nsteps * 1e-3
+            tf = ms_face / calls * 1e-3
+            nf = ctx.n_faces
+            w = 4 if prec == gp.GP_FP32 else 8
+            fl_exec, fl_paper = _flops_face(3, k, nf), _flops_paper(3, k, nf)
+            r = {"gdofs": ctx.n_active / t / 1e9, "ms": t * 1e3, "face_ms": tf * 1e3, "lift_ms": ms_lift / calls,
+                 "gfaces_per_s": nf / t / 1e9,
+                 "face_tflops_executed": fl_exec / tf / 1e12, "face_frac_of_peak": fl_exec / tf / 1e12 / peak[prec],
+                 "paper_flops_tflops": fl_paper / t / 1e12,
+                 "apply_hbm_gbs": w * (ctx.n_touched + ctx.n_active) / t / 1e9,
+                 "apply_hbm_frac": w * (ctx.n_touched + ctx.n_active) / t / 1e9 / hbm,
+                 "tiles": tiles, "rel_err_vs_oracle": None}
+            if k <= args.sweep_check_kmax:
+                if ref is None:
+                    from oracle.ghost_penalty import Oracle
+                    o = Oracle(pr)
+                    ref = o.apply(x_np)
+                    ref32 = o.apply(x_np.astype(np.float32).astype(np.float64))
+                rr = ref32 if prec == gp.GP_FP32 else ref
+                r["rel_err_vs_oracle"] = float(np.linalg.norm(y.double().cpu().numpy() - rr) / np.linalg.norm(rr))
+            rec[tags[prec]] = r
+            rec["n_active"], rec["n_faces"], rec["n_touched"] = ctx.n_active, nf, ctx.n_touched
+            ctx.close()
+            del x, y
+            torch.cuda.empty_cache()
+        out["k"][str(k)] = rec
+        print(json.dumps({"k": k, **rec}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_cg(args):
     """The solver study: gyroid (iso 0.3) on [-pi,pi]^3, n^3 cells, k = 4, model system
     (M_active + K_active + G) u = b, b ~ U[-1,1], per-order weights gamma / (j!)^2: FP32-inner
@@ -280,7 +370,7 @@ def run_gpu(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
     fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
-    ff_peak = fp32_peak / 15.0
+    ff_peak = fp32_peak / FF_OPS_PER_FMA
     clocks = Clocks(local)
 
     results = {}
@@ -360,12 +450,13 @@ def run_gpu(args):
                 "peak": {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: ff_peak}[prec],
                 "peak_source": {gp.GP_FP64: "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz x 2 flop",
                                 gp.GP_FP32: "derived: 152 SM x 128 FP32 FMA/clk x 2070 MHz x 2 flop",
-                                gp.GP_FP64_FF: "derived: FP32 peak / 15 FP32 ops per float-float FMA"}[prec]}
+                                gp.GP_FP64_FF: "derived: FP32 peak / 12 FP32 ops per compensated float-float multiply-add"}[prec]}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = _traffic({gp.GP_FP64: "f64", gp.GP_FP32: "f32", gp.GP_FP64_FF: "ff64"}[prec])
         alg_bytes = w * (ctx.n_touched + ctx.n_active)
         results[prec] = {
             "value": ws * ctx.n_active / (t_max * 1e-3) / 1e9,
+            "ghost_faces_per_s": ws * ctx.n_faces / (t_max * 1e-3),
             "ms_per_step": t_max,
             "wall_ms_per_step": wall * 1e3 / args.steps,
             "kernel_ms": {"jump": jump_ms, "lift": lift_ms},
@@ -413,6 +504,7 @@ def run_gpu(args):
         "apply_hbm": {"achieved": r["apply_hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": r["apply_hbm_frac"],
                       "peak_source": peak_src},
         "kernel_ms": r["kernel_ms"],
+        "ghost_faces_per_s": r["ghost_faces_per_s"],
         "tiles": r["tiles"],
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
     }
@@ -420,7 +512,8 @@ def run_gpu(args):
     for p in order[1:]:
         f = results[p]
         line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
-                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value", "tiles")}
+                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value", "tiles",
+                                              "ghost_faces_per_s")}
     if not args.no_batched:
         line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2, args.tune_reps)
                            for p in (gp.GP_FP64_FF, gp.GP_FP32)}
@@ -428,6 +521,7 @@ def run_gpu(args):
                                        "r ~ U[0.4,0.8], 4 right-hand sides, one CUDA graph per apply")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_paper_like"] = cpu_kronecker(args.cpu_seconds / 2)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -465,6 +559,30 @@ def cpu_baseline(seconds: float):
     return {"value": o.n_active / t / 1e9, "unit": "GDoF/s", "cores": _cores(), "kind": "oracle",
             "sample": f"{reps} full applies of the 64^3 k=3 workload ({o.n_faces} faces, explicit "
                       f"{(2 * 3 + 1) * 16}x{(2 * 3 + 1) * 16} face matrices, numpy FP64), {el:.1f} s"}
+
+
+def cpu_kronecker(seconds: float):
+    """The paper-like CPU baseline: the factorised (Kronecker) face operator of the paper
+    in C with OpenMP over faces, FP64 (oracle/kron_cpu.c), full applies for about `seconds`."""
+    from oracle.cpu_kronecker import KroneckerOpenMP
+    from oracle.ghost_penalty import Oracle
+    from paper_2503_00246_gb300 import workloads as W
+    pr = W.ball_3d()
+    o = Oracle(pr)
+    kc = KroneckerOpenMP(pr, o)
+    x = W.x_vectors(pr, o.n_active)[0]
+    kc.apply(x)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        kc.apply(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and reps >= 3:
+            break
+    t = el / reps
+    return {"value": o.n_active / t / 1e9, "unit": "GDoF/s", "cores": kc.nthreads,
+            "kind": "paper-like CPU (Kronecker form of the face operator, C + OpenMP over faces, FP64)",
+            "sample": f"{reps} full applies of the 64^3 k=3 workload, {el:.1f} s"}
 
 
 def run_reference(args):
@@ -528,7 +646,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg", "sweep"])
+    ap.add_argument("--sweep-k", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-steps", type=int, default=50)
+    ap.add_argument("--sweep-check-kmax", type=int, default=5)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--max-inner", type=int, default=200000)
     ap.add_argument("--cg-n", type=int, default=32)
@@ -541,6 +662,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "profile":
         run_profile(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     elif args.mode == "cg":
         run_cg(args)
     elif args.impl == "reference":
