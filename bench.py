@@ -261,12 +261,15 @@ def run_sweep(args):
     fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     peak = {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: fp32_peak / FF_OPS_PER_FMA}
     tags = {gp.GP_FP64_FF: "ff64", gp.GP_FP64: "fp64", gp.GP_FP32: "fp32"}
-    ks = [int(v) for v in args.sweep_k.split(",")]
-    out = {"workload": "96^3 cells on [-1,1]^3, ball r = 0.7 (seeded centre offset), gamma = 0.5 for every order",
+    names = args.sweep_workloads.split(",") if args.sweep_workloads else \
+        [f"ball96_k{int(v)}" for v in args.sweep_k.split(",")]
+    out = {"workload": "96^3 cells on [-1,1]^3, ball r = 0.7 (seeded centre offset), gamma = 0.5 for every order"
+                       if not args.sweep_workloads else "see the keys",
            "peaks_tflops": {tags[p]: peak[p] for p in peak}, "hbm_gbs": hbm, "hbm_source": peak_src, "k": {}}
     stream = torch.cuda.current_stream()
-    for k in ks:
-        pr = W.ball_3d_sweep(k)
+    for name in names:
+        pr = WORKLOADS[name](W)
+        k = pr.degree
         rec = {}
         ref = ref32 = None
         for prec in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32):
@@ -294,7 +297,7 @@ def run_sweep(args):
             tf = ms_face / calls * 1e-3
             nf = ctx.n_faces
             w = 4 if prec == gp.GP_FP32 else 8
-            fl_exec, fl_paper = _flops_face(3, k, nf), _flops_paper(3, k, nf)
+            fl_exec, fl_paper = _flops_face(pr.dim, k, nf), _flops_paper(pr.dim, k, nf)
             r = {"gdofs": ctx.n_active / t / 1e9, "ms": t * 1e3, "face_ms": tf * 1e3, "lift_ms": ms_lift / calls,
                  "gfaces_per_s": nf / t / 1e9,
                  "face_tflops_executed": fl_exec / tf / 1e12, "face_frac_of_peak": fl_exec / tf / 1e12 / peak[prec],
@@ -315,8 +318,8 @@ def run_sweep(args):
             ctx.close()
             del x, y
             torch.cuda.empty_cache()
-        out["k"][str(k)] = rec
-        print(json.dumps({"k": k, **rec}), file=sys.stderr, flush=True)
+        out["k"][str(k) if not args.sweep_workloads else name] = rec
+        print(json.dumps({"workload": name, **rec}), file=sys.stderr, flush=True)
     print(json.dumps(out), flush=True)
 
 
@@ -516,7 +519,7 @@ def run_gpu(args):
                                               "ghost_faces_per_s")}
     if not args.no_batched:
         line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2, args.tune_reps)
-                           for p in (gp.GP_FP64_FF, gp.GP_FP32)}
+                           for p in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32)}
         line["batched"]["workload"] = ("64 independent 3D balls on [-1,1]^3, n ~ U{16..96}, k ~ U{2..6}, "
                                        "r ~ U[0.4,0.8], 4 right-hand sides, one CUDA graph per apply")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -648,6 +651,7 @@ def main():
     ap.add_argument("--no-check", dest="check", action="store_false")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg", "sweep"])
     ap.add_argument("--sweep-k", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-workloads", default="", help="comma-separated workload names instead of --sweep-k")
     ap.add_argument("--sweep-steps", type=int, default=50)
     ap.add_argument("--sweep-check-kmax", type=int, default=5)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
