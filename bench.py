@@ -323,6 +323,80 @@ def run_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_micro(args):
+    """Per-face and per-cell cost with the data in cache, the GPU counterpart of the paper's
+    single-cell benchmark (Sec. 3.1: the ghost-penalty evaluation on one face against the
+    sum-factorised interior-cell Laplace, per k, in 2D and 3D).  Every cell of a box is
+    inside and every interior face penalised; the box is sized to about four waves of
+    face-kernel threads (1.2M normal lines), and the applies repeat over the same data
+    without an L2 flush.  Reports ns per face (face kernel alone and whole y = G x),
+    ns per cell of the Laplace cell kernel (mass weight 0, stiffness 1), in each arithmetic."""
+    import torch
+
+    from paper_2503_00246_gb300 import build as B
+    B.build()
+    from paper_2503_00246_gb300 import gp, workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    ks = [int(v) for v in args.sweep_k.split(",")]
+    reps = args.micro_reps
+    out = {"what": "ns per face / per cell, data hot in L2, all cells inside, all interior faces penalised",
+           "d": {}}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    for d in (2, 3):
+        out["d"][str(d)] = {}
+        for k in ks:
+            L = (k + 1) ** (d - 1)      # face-kernel threads per face: about 4 waves of the GPU
+            n = max(4, int(round((1.2e6 / (d * L)) ** (1.0 / d))))
+            pr = W.box_problem(d, n, k, all_faces=True)
+            rec = {"n": n, "cells": n ** d}
+            lo = gp.setup_problem(pr, precision=gp.GP_FP32, device=0)
+            for prec in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32):
+                ctx = lo if prec == gp.GP_FP32 else gp.setup_problem(pr, precision=prec, device=0)
+                if args.tune_reps > 0:
+                    gp.gp_autotune(ctx, args.tune_reps)
+                tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
+                x = torch.rand(ctx.n_active, dtype=tdt, device=dev)
+                y = torch.empty_like(x)
+                gp.gp_profile_enable(ctx, True)
+                t_apply = timed(lambda: gp.gp_apply(ctx, x, y))
+                ms_face, ms_lift, calls = gp.gp_profile_read(ctx)
+                gp.gp_profile_enable(ctx, False)
+                nf = ctx.n_faces
+                r = {"ns_per_face_apply": t_apply / nf * 1e9, "ns_per_face_kernel": ms_face / calls * 1e6 / nf}
+                if prec != gp.GP_FP32:
+                    sysm = gp.gp_system_create(ctx, lo)
+                    r["ns_per_cell_laplace"] = timed(lambda: gp.gp_system_cells(sysm, 0, x, y, 0.0, 1.0)) / n ** d * 1e9
+                    if prec == gp.GP_FP64:
+                        x32 = torch.rand(lo.n_active, dtype=torch.float32, device=dev)
+                        y32 = torch.empty_like(x32)
+                        rec["fp32_ns_per_cell_laplace"] = timed(
+                            lambda: gp.gp_system_cells(sysm, 1, x32, y32, 0.0, 1.0)) / n ** d * 1e9
+                    sysm.close()
+                rec[{gp.GP_FP64_FF: "ff64", gp.GP_FP64: "fp64", gp.GP_FP32: "fp32"}[prec]] = r
+                rec["faces"] = nf
+                if ctx is not lo:
+                    ctx.close()
+            rec["fp32"]["ns_per_cell_laplace"] = rec.pop("fp32_ns_per_cell_laplace")
+            lo.close()
+            out["d"][str(d)][str(k)] = rec
+            print(json.dumps({"d": d, "k": k, **rec}), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def run_cg(args):
     """The solver study: gyroid (iso 0.3) on [-pi,pi]^3, n^3 cells, k = 4, model system
     (M_active + K_active + G) u = b, b ~ U[-1,1], per-order weights gamma / (j!)^2: FP32-inner
@@ -649,7 +723,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg", "sweep"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile", "cg", "sweep", "micro"])
+    ap.add_argument("--micro-reps", type=int, default=200)
     ap.add_argument("--sweep-k", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--sweep-workloads", default="", help="comma-separated workload names instead of --sweep-k")
     ap.add_argument("--sweep-steps", type=int, default=50)
@@ -668,6 +743,8 @@ def main():
         run_profile(args)
     elif args.mode == "sweep":
         run_sweep(args)
+    elif args.mode == "micro":
+        run_micro(args)
     elif args.mode == "cg":
         run_cg(args)
     elif args.impl == "reference":

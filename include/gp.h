@@ -291,6 +291,13 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out);
  * Deterministic: G first, then the cells of each parity colour in a fixed order. */
 gp_status gp_system_apply(gp_system* sys, int which, const void* x, void* y, void* stream);
 
+/* y = (mass_weight M_active + stiff_weight K_active) x with the hi (which = 0) or lo
+ * (which = 1) arithmetic, y overwritten: the interior-cell evaluation of Sec. 2.5.2 on
+ * every active cell (mass 0, stiffness 1 is the Laplace operator of the paper's cell loop,
+ * Algorithm 1).  Same argument rules as gp_system_apply. */
+gp_status gp_system_cells(gp_system* sys, int which, double mass_weight, double stiff_weight, const void* x,
+                          void* y, void* stream);
+
 /* Solvers (the paper leaves the solver open, Sec. 1).  mode 0, defect correction:
  * r = b - A_hi u and all updates in FP64; each correction A_lo d = r solved by CG
  * with the FP32 operator and FP64 inner products to relative residual inner_rtol

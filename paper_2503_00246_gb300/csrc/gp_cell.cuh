@@ -150,10 +150,10 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y
   }
 }
 
-// Launches the parity colours in order.
+// Launches the parity colours in order; y += (wm M_active + ws K_active) x.
 template <int D, int K, class A>
 cudaError_t run_cells(const void* x, void* y, const int32_t* crow, const int32_t* cstart, const double* m,
-                      const double* s, double h, cudaStream_t st) {
+                      const double* s, double h, double wm, double ws, cudaStream_t st) {
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
@@ -163,8 +163,8 @@ cudaError_t run_cells(const void* x, void* y, const int32_t* crow, const int32_t
       c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
       c.s[p][q] = from_host<V>(s[p * (K + 1) + q]);
     }
-  c.hm = from_host<V>(D == 3 ? h * h * h : h * h);
-  c.hs = from_host<V>(D == 3 ? h : 1.0);
+  c.hm = from_host<V>(wm * (D == 3 ? h * h * h : h * h));
+  c.hs = from_host<V>(ws * (D == 3 ? h : 1.0));
   const int ncol = D == 3 ? 8 : 4;
   for (int col = 0; col < ncol; ++col) {
     CellArgs ca;

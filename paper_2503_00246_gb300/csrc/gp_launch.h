@@ -255,8 +255,9 @@ BatchOps batch_ops_ff_d3();
   return ops;
 
 // y += (M_active + K_active) x over the active cells (parity colours in order).
+// wm, ws: weights of the mass and the stiffness (1, 1 for the model system's M + K).
 using CellsFn = cudaError_t (*)(int k, const void* x, void* y, const int32_t* crow, const int32_t* cstart,
-                                const double* m, const double* s, double h, cudaStream_t st);
+                                const double* m, const double* s, double h, double wm, double ws, cudaStream_t st);
 CellsFn cells_f64_d2();
 CellsFn cells_f64_d3();
 CellsFn cells_f32_d2();
@@ -266,16 +267,16 @@ CellsFn cells_ff_d3();
 
 #define GP_CELLS_FN(D, A)                                                                               \
   return [](int k, const void* x, void* y, const int32_t* crow, const int32_t* cstart, const double* m, \
-            const double* s, double h, cudaStream_t st) -> cudaError_t {                                \
+            const double* s, double h, double wm, double ws, cudaStream_t st) -> cudaError_t {          \
     switch (k) {                                                                                        \
-      case 1: return run_cells<D, 1, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 2: return run_cells<D, 2, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 3: return run_cells<D, 3, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 4: return run_cells<D, 4, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 5: return run_cells<D, 5, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 6: return run_cells<D, 6, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 7: return run_cells<D, 7, A>(x, y, crow, cstart, m, s, h, st);                               \
-      case 8: return run_cells<D, 8, A>(x, y, crow, cstart, m, s, h, st);                               \
+      case 1: return run_cells<D, 1, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 2: return run_cells<D, 2, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 3: return run_cells<D, 3, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 4: return run_cells<D, 4, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 5: return run_cells<D, 5, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 6: return run_cells<D, 6, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 7: return run_cells<D, 7, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
+      case 8: return run_cells<D, 8, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
       default: return cudaErrorInvalidValue;                                                            \
     }                                                                                                   \
   };

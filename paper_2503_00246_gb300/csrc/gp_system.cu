@@ -119,7 +119,7 @@ gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, v
   gp_status g = gpi::launch(c, x, y, 0, st);
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
-  const cudaError_t e = cells(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(), p.h, st);
+  const cudaError_t e = cells(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
@@ -275,6 +275,24 @@ gp_status gp_system_apply(gp_system* s, int which, const void* x, void* y, void*
   if (s->n == 0) return GP_OK;
   DeviceGuard dg(s->device);
   return sys_apply(s, c, which == 0 ? s->cells_hi : s->cells_lo, x, y, (cudaStream_t)stream);
+}
+
+gp_status gp_system_cells(gp_system* s, int which, double mass_weight, double stiff_weight, const void* x, void* y,
+                          void* stream) {
+  if (!s) return fail(nullptr, GP_EINVAL, "null system");
+  gp_ctx* c = which == 0 ? s->hi : s->lo;
+  if (!c) return fail(nullptr, GP_EINVAL, "this system has no FP32 operator");
+  if (s->n > 0 && (!x || !y || x == y)) return fail(nullptr, GP_EINVAL, "bad x or y");
+  if (s->n == 0) return GP_OK;
+  DeviceGuard dg(s->device);
+  const gp::Plan& p = c->plan;
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(y, 0, (size_t)s->n * c->elem, st);
+  if (e == cudaSuccess)
+    e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(),
+                                                   p.h, mass_weight, stiff_weight, st);
+  if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
+  return GP_OK;
 }
 
 gp_status gp_system_solve(gp_system* s, const double* b, double* u, const gp_solve_opts* o, gp_solve_stats* stats) {

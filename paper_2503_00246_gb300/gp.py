@@ -107,6 +107,7 @@ def _load():
         "gp_batch_destroy": ([P], None),
         "gp_system_create": ([P, P, C.POINTER(P)], C.c_int),
         "gp_system_apply": ([P, C.c_int, P, P, P], C.c_int),
+        "gp_system_cells": ([P, C.c_int, C.c_double, C.c_double, P, P, P], C.c_int),
         "gp_system_solve": ([P, P, P, C.POINTER(gp_solve_opts), C.POINTER(gp_solve_stats)], C.c_int),
         "gp_system_destroy": ([P], None),
         "gp_profile_enable": ([P, C.c_int], C.c_int),
@@ -131,7 +132,7 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
                "gp_system_destroy", "gp_partition_info", "gp_partition_slabs", "gp_get_tiles",
-               "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup")
+               "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup", "gp_system_cells")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -331,6 +332,14 @@ def gp_system_apply(sys: System, which: int, x, y, stream=None):
     _check_vec(ctx, x)
     _check_vec(ctx, y)
     _check(lib.gp_system_apply(sys.handle, which, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def gp_system_cells(sys: System, which: int, x, y, mass: float = 1.0, stiff: float = 1.0, stream=None):
+    """y = (mass M_active + stiff K_active) x with the hi (0) or lo (1) arithmetic."""
+    ctx = sys.hi if which == 0 else sys.lo
+    _check_vec(ctx, x)
+    _check_vec(ctx, y)
+    _check(lib.gp_system_cells(sys.handle, int(which), float(mass), float(stiff), _ptr(x), _ptr(y), _stream(stream)))
 
 
 def gp_system_solve(sys: System, b, u, rtol=1e-10, inner_rtol=1e-4, max_outer=50, max_inner=20000, mode=0,

@@ -46,6 +46,30 @@ def test_system_apply_matches_oracle(gplib, cuda, dim, k, n, hi):
 
 
 @pytest.mark.parametrize("hi", [0, 2])
+@pytest.mark.parametrize("dim,k,n", [(2, 3, 12), (3, 1, 9), (3, 2, 8), (3, 5, 6)])
+def test_cell_operator_weights(gplib, cuda, dim, k, n, hi):
+    # the interior-cell evaluation alone (Sec. 2.5.2): Laplace (0, 1), mass (1, 0) and a mix
+    from oracle.cell_operator import CellOperator
+    pr = W.small_ball(dim, n, k, radius=0.6, seed=120 + k)
+    o = Oracle(pr)
+    co = CellOperator(pr, o.num, o.cls)
+    chi = gplib.setup_problem(pr, precision=hi)
+    clo = gplib.setup_problem(pr, precision=1)
+    sysm = gplib.gp_system_create(chi, clo)
+    x = W.x_vectors(pr, chi.n_active)[0]
+    for mass, stiff in ((0.0, 1.0), (1.0, 0.0), (2.0, -0.5)):
+        for which, dt, tol, xin in ((0, cuda.float64, 1e-12, x), (1, cuda.float32, 1e-5, x.astype(np.float32))):
+            xd = cuda.tensor(xin, dtype=dt, device="cuda")
+            yd = cuda.full_like(xd, float("nan"))
+            gplib.gp_system_cells(sysm, which, xd, yd, mass=mass, stiff=stiff)
+            cuda.cuda.synchronize()
+            y = yd.double().cpu().numpy()
+            r = co.apply(xin.astype(np.float64), mass=mass, stiff=stiff)
+            assert np.abs(y - r).max() <= tol * np.abs(r).max(), (mass, stiff, which)
+    sysm.close()
+
+
+@pytest.mark.parametrize("hi", [0, 2])
 def test_defect_correction_and_cg(gplib, cuda, hi):
     pr = W.small_ball(3, 12, 3, radius=0.62, seed=91)
     o, A = _oracle_system(pr)
