@@ -30,6 +30,8 @@ struct gp_system {
   float* dinv32 = nullptr;
   double* part = nullptr;   // dot partials + result
   double* h_res = nullptr;  // pinned copy of the dot result
+  void* d_cg = nullptr;     // CgScalars of the running CG (device)
+  void* h_cg = nullptr;     // pinned copy
   cudaStream_t st = nullptr;
   std::string err;
 };
@@ -107,16 +109,18 @@ __global__ void add64_k(double* __restrict__ u, const double* __restrict__ d, in
 template <typename T>
 cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
   dot_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(a, b, s->n, s->part);
-  dot_final<<<1, kThreads, 0, s->st>>>(s->part, s->part + kDotBlocks);
-  cudaError_t e = cudaMemcpyAsync(s->h_res, s->part + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->st);
+  dot_final<<<1, kThreads, 0, s->st>>>(s->part, s->part + 2 * kDotBlocks);
+  cudaError_t e =
+      cudaMemcpyAsync(s->h_res, s->part + 2 * kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   *out = *s->h_res;
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 // y = A x with the operator of context c (G, then the cell colours adding on top)
-gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st) {
-  gp_status g = gpi::launch(c, x, y, 0, st);
+gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st,
+                    bool trace = true) {
+  gp_status g = gpi::launch(c, x, y, 0, st, nullptr, trace);
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
   const cudaError_t e = cells(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, st);
@@ -132,10 +136,11 @@ gp::CellsFn cells_for(const gp::Plan& p) {
 
 void sys_free(gp_system* s) {
   void* ptrs[] = {s->d_crow, s->r, s->p, s->q, s->dd, s->z, s->ri, s->r32, s->d32, s->ri32, s->p32, s->q32,
-                  s->z32, s->dinv, s->dinv32, s->part};
+                  s->z32, s->dinv, s->dinv32, s->part, s->d_cg};
   for (void* v : ptrs)
     if (v) cudaFree(v);
   if (s->h_res) cudaFreeHost(s->h_res);
+  if (s->h_cg) cudaFreeHost(s->h_cg);
   if (s->st) cudaStreamDestroy(s->st);
 }
 
@@ -148,46 +153,228 @@ void sys_free(gp_system* s) {
     }                                                                                            \
   } while (0)
 
+// ---- CG with its scalars on the device --------------------------------------------
+// One iteration is enqueued without a host round trip: q = A p; alpha = rz / (p.q);
+// d += alpha p, r -= alpha q, z = D^-1 r together with the partial sums of r.r and r.z;
+// beta = rz' / rz; p = z + beta p.  A block of kCgBlock iterations is captured once as a
+// CUDA graph and replayed; the host reads the scalars (converged, iterations) after
+// each replay.  Iterations after convergence leave d and r unchanged (alpha = 0).
+// Every reduction has a fixed grid and tree: bitwise reproducible.
+struct CgScalars {
+  double rz, rr, stop, alpha, beta;
+  int done, iters, maxit, breakdown;
+};
+
+constexpr int kCgBlock = 16;
+
+__global__ void __launch_bounds__(kThreads) cg_init_final(const double* __restrict__ part, CgScalars* sc,
+                                                          double tol, int maxit) {
+  __shared__ double sa[kThreads], sb[kThreads];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) {
+    a += part[i];
+    b += part[kDotBlocks + i];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double rr0 = sa[0];
+    sc->rr = rr0;
+    sc->rz = sb[0];
+    sc->stop = tol * tol * rr0;
+    sc->iters = 0;
+    sc->maxit = maxit;
+    sc->breakdown = 0;
+    sc->alpha = sc->beta = 0.0;
+    sc->done = (maxit <= 0 || !(rr0 > sc->stop) || !(rr0 > 0.0)) ? 1 : 0;
+  }
+}
+
+// alpha = rz / (p.q) from the partial sums of p.q
+__global__ void __launch_bounds__(kThreads) cg_alpha(const double* __restrict__ part, CgScalars* sc) {
+  __shared__ double sh[kThreads];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) a += part[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double pq = sh[0];
+    double alpha = 0.0;
+    if (!sc->done) {
+      if (pq > 0.0) alpha = sc->rz / pq;
+      else { sc->done = 1; sc->breakdown = 1; }
+    }
+    sc->alpha = alpha;
+  }
+}
+
+// d += alpha p, r -= alpha q, z = dinv r (when dinv), and the partial sums of r.r, r.z
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cg_update(T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
+                                                      const T* __restrict__ q, T* __restrict__ z,
+                                                      const T* __restrict__ dinv, const CgScalars* __restrict__ sc,
+                                                      int64_t n, double* __restrict__ part) {
+  if (sc->done) return;
+  const T a = (T)sc->alpha;
+  __shared__ double sa[kThreads], sb[kThreads];
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
+    d[i] = fma(a, p[i], d[i]);
+    const T ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    T zi = ri;
+    if (dinv) {
+      zi = dinv[i] * ri;
+      z[i] = zi;
+    }
+    rr = fma((double)ri, (double)ri, rr);
+    rz = fma((double)ri, (double)zi, rz);
+  }
+  sa[threadIdx.x] = rr;
+  sb[threadIdx.x] = rz;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sa[0];
+    part[kDotBlocks + blockIdx.x] = sb[0];
+  }
+}
+
+// beta = rz' / rz, the convergence test and the iteration count
+__global__ void __launch_bounds__(kThreads) cg_beta(const double* __restrict__ part, CgScalars* sc) {
+  __shared__ double sa[kThreads], sb[kThreads];
+  __shared__ int done;
+  if (threadIdx.x == 0) done = sc->done;
+  __syncthreads();
+  if (done) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) {
+    a += part[i];
+    b += part[kDotBlocks + i];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double rr = sa[0], rz1 = sb[0];
+    sc->beta = rz1 / sc->rz;
+    sc->rz = rz1;
+    sc->rr = rr;
+    sc->iters += 1;
+    if (!(rr > sc->stop) || !(rr > 0.0) || sc->iters >= sc->maxit) sc->done = 1;
+  }
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void cg_direction(T* __restrict__ p, const T* __restrict__ z, const CgScalars* __restrict__ sc, int64_t n) {
+  if (sc->done) return;
+  const T bt = (T)sc->beta;
+  GRID_STRIDE(i, n) p[i] = fma(bt, p[i], z[i]);
+}
+
+// the partial sums of a.b and c.e (kDotBlocks each) into part
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dot2_partial(const T* __restrict__ a, const T* __restrict__ b,
+                                                         const T* __restrict__ c, const T* __restrict__ e,
+                                                         int64_t n, double* __restrict__ part) {
+  __shared__ double sa[kThreads], sb[kThreads];
+  double x = 0.0, w = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
+    x = fma((double)a[i], (double)b[i], x);
+    w = fma((double)c[i], (double)e[i], w);
+  }
+  sa[threadIdx.x] = x;
+  sb[threadIdx.x] = w;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sa[0];
+    part[kDotBlocks + blockIdx.x] = sb[0];
+  }
+}
+
 // Preconditioned CG (Jacobi when dinv is given) on A d = rhs from d = 0, until
 // ||r|| <= tol * ||rhs|| or maxit iterations.
 template <typename T>
 gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* r, T* p, T* q, T* z,
              const T* dinv, double tol, int maxit, int* iters, int* applies) {
   const int64_t n = s->n;
+  CgScalars* sc = (CgScalars*)s->d_cg;
+  CgScalars* hs = (CgScalars*)s->h_cg;
+  T* zz = dinv ? z : r;
   SYS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(T), s->st));
   SYS_CUDA(cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
-  const T* zz = r;
-  if (dinv) {
-    scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
-    zz = z;
-  }
+  if (dinv) scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
   SYS_CUDA(cudaMemcpyAsync(p, zz, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
-  double rr0 = 0.0, rz = 0.0;
-  SYS_CUDA(dot<T>(s, r, r, &rr0));
-  SYS_CUDA(dot<T>(s, r, zz, &rz));
-  const double stop = tol * tol * rr0;
-  double rr = rr0;
-  int it = 0;
-  while (it < maxit && rr > stop && rr > 0.0) {
-    gp_status g = sys_apply(s, c, cells, p, q, s->st);
-    if (g != GP_OK) return g;
-    ++*applies;
-    double pq = 0.0;
-    SYS_CUDA(dot<T>(s, p, q, &pq));
-    if (!(pq > 0.0)) break;
-    const double alpha = rz / pq;
-    axpy_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(d, p, alpha, n);
-    axpy_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(r, q, -alpha, n);
-    if (dinv) scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
-    double rz1 = 0.0;
-    SYS_CUDA(dot<T>(s, r, r, &rr));
-    if (dinv) SYS_CUDA(dot<T>(s, r, zz, &rz1));
-    else rz1 = rr;
-    xpay_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(p, zz, rz1 / rz, n);
-    rz = rz1;
-    ++it;
+  dot2_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(r, r, r, zz, n, s->part);
+  cg_init_final<<<1, kThreads, 0, s->st>>>(s->part, sc, tol, maxit);
+  SYS_CUDA(cudaGetLastError());
+  // one block of iterations, captured once and replayed
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  SYS_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  gp_status g = GP_OK;
+  for (int i = 0; i < kCgBlock && g == GP_OK; ++i) {
+    g = sys_apply(s, c, cells, p, q, s->st, false);
+    if (g != GP_OK) break;
+    dot_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(p, q, n, s->part);
+    cg_alpha<<<1, kThreads, 0, s->st>>>(s->part, sc);
+    cg_update<T><<<kDotBlocks, kThreads, 0, s->st>>>(d, r, p, q, z, dinv, sc, n, s->part);
+    cg_beta<<<1, kThreads, 0, s->st>>>(s->part, sc);
+    cg_direction<T><<<kVecBlocks, kThreads, 0, s->st>>>(p, zz, sc, n);
   }
-  *iters = it;
+  const cudaError_t ec = cudaStreamEndCapture(s->st, &graph);
+  if (g != GP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return g;
+  }
+  SYS_CUDA(ec);
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  int blocks = 0;
+  while (e == cudaSuccess) {
+    e = cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess || hs->done) break;
+    e = cudaGraphLaunch(exec, s->st);
+    ++blocks;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  SYS_CUDA(e);
+  *iters = hs->iters;
+  *applies += blocks * kCgBlock;
   return GP_OK;
 }
 
@@ -260,8 +447,10 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->ri32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->p32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->q32, n4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->part, (kDotBlocks + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, (2 * kDotBlocks + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_cg, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_cg, sizeof(CgScalars));
   if (e != cudaSuccess) return cleanup(e);
   *out = s;
   return GP_OK;
