@@ -1,4 +1,4 @@
-// Mass + Laplace stiffness of the active cells, y += (M_active + K_active) x, for
+// Mass + Laplace stiffness of the active cells, y (+)= (wm M_active + ws K_active) x, for
 // the model SPD system (M_active + K_active + G) u = b of the defect-correction
 // solver.  Every active cell is integrated as a full cube (no cut quadrature):
 // the interior-cell evaluation of Sec. 2.5.2, with the k+1 Gauss points per
@@ -9,9 +9,13 @@
 // is applied by sum factorisation: a = M^ x, b = S^ x along x; c = M^ a, d = S^ a,
 // e = M^ b along y; y_K = M^ (h^3 c + h (d + e)) + S^ (h c) along z (3D), or
 // y_K = M^ (h^2 a + b) + S^ a along y (2D).  One thread per x-line of a cell; the y
-// and z passes go through shared memory in place.  Cells of one parity colour share
-// no node, so the launch for a colour adds its cells' results with plain
-// read-modify-writes; the colours run in a fixed order (bitwise reproducible).
+// and z passes go through shared memory.  The float-float form renormalises after every
+// operation here (the model system's outer residual needs the full accuracy).
+//
+// Two launches, like the face operator: cell_kernel stores every cell's (k+1)^d
+// outputs, and cell_gather adds, for every node, the outputs of the (up to 2^d) active
+// cells that hold it, in a fixed order: no atomics, no colour phases, bitwise
+// reproducible.
 #pragma once
 
 #include <cstdint>
@@ -28,36 +32,43 @@ struct CellShape {
   static constexpr int NODES = R * K1;                      // nodes per cell
   static constexpr int CB = (256 / R) > 0 ? 256 / R : 1;   // cells per CTA
   static constexpr int NT = CB * R;
+  static constexpr int NWC = (D == 3) ? 8 : 4;              // cells holding a node
+  static constexpr int KR = (D == 3) ? K * K : K;           // x-rows per owner cell
 };
 
 template <typename V, int K>
 struct CellConsts {
   V m[K + 1][K + 1];  // reference mass
   V s[K + 1][K + 1];  // reference stiffness
-  V hm;               // h^d
-  V hs;               // h^(d-2)
+  V hm;               // wm h^d
+  V hs;               // ws h^(d-2)
 };
 
-struct CellArgs {
-  const int32_t* crow;  // [ncell][R] compact index of each x-line start
-  int32_t c0, c1;       // cells [c0, c1) of one colour
+// Device tables of the cell operator (see Plan::crow, cwin, corow).
+struct CellTabs {
+  const int32_t* crow = nullptr;   // [ncact][R] compact index of each x-line start
+  int32_t ncact = 0;
+  const int32_t* cwin = nullptr;   // [ncown][NWC] active-cell index of (ci - s_x, cj - s_y, cl - s_z)
+  const int32_t* corow = nullptr;  // [KR][ncown] compact index of node (ci k, cj k + q, cl k + r)
+  int32_t ncown = 0;
+  int32_t n_active = 0;
+  void* wc = nullptr;              // [ncact][NODES] cell outputs (scratch)
 };
 
 template <int D, int K, class A>
 __global__ void __launch_bounds__(CellShape<D, K>::NT)
-cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y, const CellArgs ca,
-            const __grid_constant__ CellConsts<typename A::V, K> c) {
+cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc, const int32_t* __restrict__ crow,
+            const int32_t ncact, const __grid_constant__ CellConsts<typename A::V, K> c) {
   using S = CellShape<D, K>;
   using V = typename A::V;
-  using IO = typename A::IO;
   constexpr int K1 = S::K1, R = S::R, NODES = S::NODES, CB = S::CB;
   __shared__ V sa[CB][NODES];
   __shared__ V sb[CB][NODES];
   const int t = threadIdx.x;
   const int cl = t / R, line = t - cl * R;
-  const int cell = ca.c0 + blockIdx.x * CB + cl;
-  const bool valid = cell < ca.c1;
-  const int32_t row = valid ? __ldg(ca.crow + (size_t)cell * R + line) : 0;
+  const int cell = blockIdx.x * CB + cl;
+  const bool valid = cell < ncact;
+  const int32_t row = valid ? __ldg(crow + (size_t)cell * R + line) : 0;
 
   // ---- x pass: a = M^ x, b = S^ x on this thread's x-line
   V xl[K1];
@@ -76,6 +87,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y
   }
   __syncthreads();
 
+  V yout[K1];
   if constexpr (D == 3) {
     // ---- y pass on the line (i1, i3): f = h^3 M^ a + h (S^ a + M^ b), g = h M^ a
     {
@@ -100,7 +112,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y
       }
     }
     __syncthreads();
-    // ---- z pass on the line (i1, i2): y = M^ f + S^ g
+    // ---- z pass on the line (i1, i2): y = M^ f + S^ g, stored along z
     {
       const int i1 = line % K1, i2 = line / K1;
       V fz[K1], gz[K1];
@@ -114,10 +126,14 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y
         V yv = vzero<V>();
 #pragma unroll
         for (int q = 0; q < K1; ++q) yv = vfma(c.s[p][q], gz[q], vfma(c.m[p][q], fz[q], yv));
-        sa[cl][i1 + K1 * (i2 + K1 * p)] = yv;
+        yout[p] = yv;
+      }
+      if (valid) {
+        V* dst = wc + (size_t)cell * NODES;
+#pragma unroll
+        for (int p = 0; p < K1; ++p) dst[i1 + K1 * (i2 + K1 * p)] = yout[p];
       }
     }
-    __syncthreads();
   } else {
     // ---- y pass on the line i1: y = M^ (h^2 a + b) + S^ a
     V ay[K1], by[K1];
@@ -135,25 +151,68 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ y
         yv = vfma(c.m[p][q], f, yv);
         yv = vfma(c.s[p][q], vfma(c.hs, ay[q], vzero<V>()), yv);
       }
-      sa[cl][line + K1 * p] = yv;
+      yout[p] = yv;
     }
-    __syncthreads();
-  }
-
-  // ---- add the cell's result on this thread's x-line
-  if (valid) {
+    if (valid) {
+      V* dst = wc + (size_t)cell * NODES;
 #pragma unroll
-    for (int i = 0; i < K1; ++i) {
-      const int idx = row + i;
-      y[idx] = to_io(vadd(from_io(y[idx], (V*)nullptr), sa[cl][i + K1 * line]), (IO*)nullptr);
+      for (int p = 0; p < K1; ++p) dst[line + K1 * p] = yout[p];
     }
   }
 }
 
-// Launches the parity colours in order; y += (wm M_active + ws K_active) x.
+// One thread per x-row (q, r) of an owner cell: its k nodes p add the outputs of the cells
+// (ci - s_x, cj - s_y, cl - s_z) that hold them (s_y = 1 only for q = 0, s_z = 1 only for
+// r = 0, s_x = 1 only for p = 0), in the order w = s_x + 2 s_y + 4 s_z.
 template <int D, int K, class A>
-cudaError_t run_cells(const void* x, void* y, const int32_t* crow, const int32_t* cstart, const double* m,
-                      const double* s, double h, double wm, double ws, cudaStream_t st) {
+__global__ void __launch_bounds__(256)
+cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y, const int add, const CellTabs ct) {
+  using S = CellShape<D, K>;
+  using V = typename A::V;
+  using IO = typename A::IO;
+  constexpr int K1 = S::K1, NODES = S::NODES, NWC = S::NWC, KR = S::KR;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ct.ncown * KR) return;
+  const int own = g / KR, t = g - own * KR;
+  const int q = t % K, r = (D == 3) ? t / K : 0;
+  const int base = __ldg(ct.corow + (size_t)t * ct.ncown + own);
+  if (base < 0) return;
+  Sum<V> acc[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();
+  bool any0 = false, anyp = false;
+#pragma unroll
+  for (int w = 0; w < NWC; ++w) {
+    const int sx = w & 1, sy = (w >> 1) & 1, sz = (w >> 2) & 1;
+    if ((sy && q != 0) || (sz && r != 0)) continue;
+    const int cidx = __ldg(ct.cwin + (size_t)own * NWC + w);
+    if (cidx < 0) continue;
+    const int ly = q + sy * K, lz = r + sz * K;
+    const V* src = wc + (size_t)cidx * NODES + K1 * (ly + (D == 3 ? K1 * lz : 0));
+    if (sx == 0) {
+#pragma unroll
+      for (int p = 0; p < K; ++p) sum_add(acc[p], src[p]);
+      any0 = anyp = true;
+    } else {
+      sum_add(acc[0], src[K]);
+      any0 = true;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    if (p == 0 ? !any0 : !anyp) continue;
+    const int idx = base + p;
+    if (idx >= ct.n_active) break;
+    const V sv = dot_value(acc[p]);
+    const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), sv) : sv;
+    y[idx] = to_io(outv, (IO*)nullptr);
+  }
+}
+
+// y (+)= (wm M_active + ws K_active) x: the cell kernel, then the gather (add = 1: onto y).
+template <int D, int K, class A>
+cudaError_t run_cells(const void* x, void* y, const CellTabs& ct, const double* m, const double* s, double h,
+                      double wm, double ws, int add, cudaStream_t st) {
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
@@ -165,16 +224,12 @@ cudaError_t run_cells(const void* x, void* y, const int32_t* crow, const int32_t
     }
   c.hm = from_host<V>(wm * (D == 3 ? h * h * h : h * h));
   c.hs = from_host<V>(ws * (D == 3 ? h : 1.0));
-  const int ncol = D == 3 ? 8 : 4;
-  for (int col = 0; col < ncol; ++col) {
-    CellArgs ca;
-    ca.crow = crow;
-    ca.c0 = cstart[col];
-    ca.c1 = cstart[col + 1];
-    const int ncell = ca.c1 - ca.c0;
-    if (ncell <= 0) continue;
-    cell_kernel<D, K, A><<<(ncell + S::CB - 1) / S::CB, S::NT, 0, st>>>((const IO*)x, (IO*)y, ca, c);
-  }
+  if (ct.ncact <= 0) return cudaSuccess;
+  cell_kernel<D, K, A><<<(ct.ncact + S::CB - 1) / S::CB, S::NT, 0, st>>>((const IO*)x, (V*)ct.wc, ct.crow, ct.ncact,
+                                                                          c);
+  const int64_t rows = (int64_t)ct.ncown * S::KR;
+  if (rows > 0)
+    cell_gather<D, K, A><<<(int)((rows + 255) / 256), 256, 0, st>>>((const V*)ct.wc, (IO*)y, add, ct);
   return cudaGetLastError();
 }
 

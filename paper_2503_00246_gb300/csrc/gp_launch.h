@@ -254,10 +254,10 @@ BatchOps batch_ops_ff_d3();
   };                                                                                                    \
   return ops;
 
-// y += (M_active + K_active) x over the active cells (parity colours in order).
-// wm, ws: weights of the mass and the stiffness (1, 1 for the model system's M + K).
-using CellsFn = cudaError_t (*)(int k, const void* x, void* y, const int32_t* crow, const int32_t* cstart,
-                                const double* m, const double* s, double h, double wm, double ws, cudaStream_t st);
+// y (+)= (wm M_active + ws K_active) x over the active cells (cell kernel + gather; add = 1:
+// onto y, 0: overwrite the nodes of active cells).
+using CellsFn = cudaError_t (*)(int k, const void* x, void* y, const CellTabs& ct, const double* m, const double* s,
+                                double h, double wm, double ws, int add, cudaStream_t st);
 CellsFn cells_f64_d2();
 CellsFn cells_f64_d3();
 CellsFn cells_f32_d2();
@@ -265,20 +265,16 @@ CellsFn cells_f32_d3();
 CellsFn cells_ff_d2();
 CellsFn cells_ff_d3();
 
-#define GP_CELLS_FN(D, A)                                                                               \
-  return [](int k, const void* x, void* y, const int32_t* crow, const int32_t* cstart, const double* m, \
-            const double* s, double h, double wm, double ws, cudaStream_t st) -> cudaError_t {          \
-    switch (k) {                                                                                        \
-      case 1: return run_cells<D, 1, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 2: return run_cells<D, 2, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 3: return run_cells<D, 3, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 4: return run_cells<D, 4, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 5: return run_cells<D, 5, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 6: return run_cells<D, 6, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 7: return run_cells<D, 7, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      case 8: return run_cells<D, 8, A>(x, y, crow, cstart, m, s, h, wm, ws, st);                               \
-      default: return cudaErrorInvalidValue;                                                            \
-    }                                                                                                   \
+#define GP_CELLS_CASE(D, A, K) \
+  case K: return run_cells<D, K, A>(x, y, ct, m, s, h, wm, ws, add, st);
+#define GP_CELLS_FN(D, A)                                                                                 \
+  return [](int k, const void* x, void* y, const CellTabs& ct, const double* m, const double* s, double h, \
+            double wm, double ws, int add, cudaStream_t st) -> cudaError_t {                             \
+    switch (k) {                                                                                          \
+      GP_CELLS_CASE(D, A, 1) GP_CELLS_CASE(D, A, 2) GP_CELLS_CASE(D, A, 3) GP_CELLS_CASE(D, A, 4)         \
+      GP_CELLS_CASE(D, A, 5) GP_CELLS_CASE(D, A, 6) GP_CELLS_CASE(D, A, 7) GP_CELLS_CASE(D, A, 8)         \
+      default: return cudaErrorInvalidValue;                                                              \
+    }                                                                                                     \
   };
 
 #define GP_DISPATCH_K(D, A, Ar, st)                    \

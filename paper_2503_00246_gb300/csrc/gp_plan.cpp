@@ -181,29 +181,63 @@ void reference_stiffness(int k, std::vector<double>& stiff) {
 void build_cell_table(Plan& p) {
   const int d = p.dim, n = p.n, k = p.k;
   const int R1 = d == 3 ? (k + 1) * (k + 1) : k + 1;
-  std::vector<int64_t> byc[8];
-  for (int64_t c = 0; c < p.ncell; ++c) {
-    if (p.cls[c] == OUTSIDE) continue;
-    int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
-    byc[(ci & 1) + 2 * (cj & 1) + 4 * (cl & 1)].push_back(c);
-  }
+  const int n1 = n + 1;
+  // active cells, lexicographic; x-line starts of each
+  std::vector<int32_t> act_of(p.ncell, -1);
   p.ncact = 0;
-  for (int col = 0; col < 8; ++col) p.ncact += (int64_t)byc[col].size();
+  for (int64_t c = 0; c < p.ncell; ++c)
+    if (p.cls[c] != OUTSIDE) act_of[c] = (int32_t)p.ncact++;
   p.crow.assign((size_t)p.ncact * R1, 0);
-  int64_t pos = 0;
-  for (int col = 0; col < 8; ++col) {
-    p.cstart[col] = (int32_t)pos;
-    for (int64_t c : byc[col]) {
-      int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
-      for (int t = 0; t < R1; ++t) {
-        int q = t % (k + 1), r = t / (k + 1);
-        int64_t row = (int64_t)(cj * k + q) + (d == 3 ? (int64_t)p.nl * (cl * k + r) : 0);
-        p.crow[(size_t)pos * R1 + t] = (int32_t)p.compact(ci * k, row);
-      }
-      ++pos;
+  for (int64_t c = 0; c < p.ncell; ++c) {
+    const int32_t a = act_of[c];
+    if (a < 0) continue;
+    const int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+    for (int t = 0; t < R1; ++t) {
+      const int q = t % (k + 1), r = t / (k + 1);
+      const int64_t row = (int64_t)(cj * k + q) + (d == 3 ? (int64_t)p.nl * (cl * k + r) : 0);
+      p.crow[(size_t)a * R1 + t] = (int32_t)p.compact(ci * k, row);
     }
   }
-  p.cstart[8] = (int32_t)pos;
+  // owner cells (coordinates in [0, n]) of the active nodes, lexicographic; their window of
+  // the 2^d cells (ci - s_x, cj - s_y, cl - s_z), s in {0,1}^d, that hold their nodes
+  std::vector<uint8_t> own((size_t)n1 * n1 * (d == 3 ? n1 : 1), 0);
+  for (int64_t c = 0; c < p.ncell; ++c) {
+    if (act_of[c] < 0) continue;
+    const int ci = (int)(c % n), cj = (int)((c / n) % n), cl = d == 3 ? (int)(c / ((int64_t)n * n)) : 0;
+    for (int dz = 0; dz <= (d == 3 ? 1 : 0); ++dz)
+      for (int dy = 0; dy <= 1; ++dy)
+        for (int dx = 0; dx <= 1; ++dx)
+          own[(ci + dx) + (size_t)n1 * ((cj + dy) + (size_t)n1 * (cl + dz))] = 1;
+  }
+  const int NWC = d == 3 ? 8 : 4;
+  const int KR = d == 3 ? k * k : k;
+  p.cwin.clear();
+  std::vector<int64_t> owners;
+  for (size_t o = 0; o < own.size(); ++o)
+    if (own[o]) owners.push_back((int64_t)o);
+  p.ncown = (int64_t)owners.size();
+  p.cwin.assign((size_t)p.ncown * NWC, -1);
+  p.corow.assign((size_t)KR * p.ncown, -1);
+  for (int64_t i = 0; i < p.ncown; ++i) {
+    const int64_t o = owners[i];
+    const int ci = (int)(o % n1), cj = (int)((o / n1) % n1), cl = d == 3 ? (int)(o / ((int64_t)n1 * n1)) : 0;
+    for (int w = 0; w < NWC; ++w) {
+      const int sx = w & 1, sy = (w >> 1) & 1, sz = (w >> 2) & 1;
+      const int x = ci - sx, y = cj - sy, z = cl - sz;
+      if (x < 0 || x >= n || y < 0 || y >= n || (d == 3 && (z < 0 || z >= n))) continue;
+      p.cwin[(size_t)i * NWC + w] = act_of[x + (int64_t)n * (y + (int64_t)n * z)];
+    }
+    for (int t = 0; t < KR; ++t) {
+      const int q = t % k, r = t / k;
+      const int X = ci * k, Y = cj * k + q, Z = cl * k + r;
+      int64_t cidx = -1;
+      if (X < p.nl && Y < p.nl && (d == 2 || Z < p.nl)) {
+        const int64_t row = (int64_t)Y + (d == 3 ? (int64_t)p.nl * Z : 0);
+        cidx = p.compact(X, row);
+      }
+      p.corow[(size_t)t * p.ncown + i] = (int32_t)cidx;
+    }
+  }
 }
 
 // Diagonal of the model system: per active cell h^d M_ii M_jj M_kk + h^(d-2) (S_ii M_jj M_kk +

@@ -58,12 +58,16 @@ struct Plan {
   int64_t num_lift_cells() const { return (int64_t)lcell.size() / 4; }
   int64_t num_zero_runs() const { return (int64_t)zruns.size() / 2; }
 
-  // active cells for the mass + stiffness operator, grouped by the parity colour
-  // (ci&1) + 2 (cj&1) + 4 (cl&1): cells of one colour share no node
+  // active cells for the mass + stiffness operator (lexicographic)
   std::vector<int32_t> crow;      // ncact x (k+1)^(d-1): compact index of (ci k, cj k + q, cl k + r)
-  int32_t cstart[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int64_t num_active_cells() const { return ncact; }
   int64_t ncact = 0;
+  // owner cells of the active nodes (coordinates in [0, n], lexicographic): per owner the
+  // active-cell index of the 2^d cells (ci - s_x, cj - s_y, cl - s_z) (-1 if none), and per
+  // x-row (q, r) the compact index of node (ci k, cj k + q, cl k + r) ([KR][ncown], -1 if none)
+  std::vector<int32_t> cwin;
+  std::vector<int32_t> corow;
+  int64_t ncown = 0;
 
   // slab partition (Sec. 2.7): cell layers [part_lo, part_hi) along the last axis.  The
   // vector is the global numbering restricted to the lattice planes [part_lo k,
@@ -84,6 +88,12 @@ struct Plan {
   int64_t compact(int X, int64_t row) const;
 };
 
+inline int64_t ipow_host(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
 gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* opts,
                      Plan& p, std::string& err);
 void active_coords(const Plan& p, double* xyz);
@@ -97,7 +107,7 @@ void gauss_lobatto_01(int k, std::vector<double>& x);
 void reference_1d(int k, const std::vector<double>& gl, std::vector<double>& mass,
                   std::vector<double>& jumps);
 void reference_stiffness(int k, std::vector<double>& stiff);
-// Builds crow / cstart (the active-cell table of the mass + stiffness operator).
+// Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // diag(M_active + K_active + G) in FP64 (needs the cell table).
 void build_diagonal(const Plan& p, std::vector<double>& diag);

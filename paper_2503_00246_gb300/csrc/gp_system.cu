@@ -21,7 +21,10 @@ struct gp_system {
   int device = -1;
   int64_t n = 0;
   int32_t* d_crow = nullptr;
-  int32_t cstart[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t* d_cwin = nullptr;
+  int32_t* d_corow = nullptr;
+  void* d_wc = nullptr;     // cell outputs (scratch, 8 bytes per value)
+  gp::CellTabs ct{};
   gp::CellsFn cells_hi = nullptr, cells_lo = nullptr;
   // solver vectors
   double *r = nullptr, *p = nullptr, *q = nullptr, *dd = nullptr, *z = nullptr, *ri = nullptr;
@@ -123,7 +126,7 @@ gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, v
   gp_status g = gpi::launch(c, x, y, 0, st, nullptr, trace);
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
-  const cudaError_t e = cells(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, st);
+  const cudaError_t e = cells(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 1, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
@@ -135,8 +138,8 @@ gp::CellsFn cells_for(const gp::Plan& p) {
 }
 
 void sys_free(gp_system* s) {
-  void* ptrs[] = {s->d_crow, s->r, s->p, s->q, s->dd, s->z, s->ri, s->r32, s->d32, s->ri32, s->p32, s->q32,
-                  s->z32, s->dinv, s->dinv32, s->part, s->d_cg};
+  void* ptrs[] = {s->d_crow, s->d_cwin, s->d_corow, s->d_wc, s->r, s->p, s->q, s->dd, s->z, s->ri, s->r32,
+                  s->d32, s->ri32, s->p32, s->q32, s->z32, s->dinv, s->dinv32, s->part, s->d_cg};
   for (void* v : ptrs)
     if (v) cudaFree(v);
   if (s->h_res) cudaFreeHost(s->h_res);
@@ -406,7 +409,6 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   DeviceGuard dg(s->device);
   gp::Plan& p = hi->plan;
   if (p.crow.empty() && p.n_active > 0) gp::build_cell_table(p);
-  std::memcpy(s->cstart, p.cstart, sizeof(s->cstart));
   s->cells_hi = cells_for(p);
   if (lo) s->cells_lo = cells_for(lo->plan);
   auto cleanup = [&](cudaError_t e) {
@@ -416,9 +418,24 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
     return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
   };
   cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess && !p.crow.empty()) e = cudaMalloc(&s->d_crow, p.crow.size() * sizeof(int32_t));
-  if (e == cudaSuccess && !p.crow.empty())
-    e = cudaMemcpy(s->d_crow, p.crow.data(), p.crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  auto upload = [](int32_t** dst, const std::vector<int32_t>& v) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
+    cudaError_t r = cudaMalloc((void**)dst, v.size() * sizeof(int32_t));
+    if (r == cudaSuccess) r = cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    return r;
+  };
+  if (e == cudaSuccess) e = upload(&s->d_crow, p.crow);
+  if (e == cudaSuccess) e = upload(&s->d_cwin, p.cwin);
+  if (e == cudaSuccess) e = upload(&s->d_corow, p.corow);
+  const size_t nodes = (size_t)gp::ipow_host(p.k + 1, p.dim);
+  if (e == cudaSuccess && p.ncact > 0) e = cudaMalloc(&s->d_wc, (size_t)p.ncact * nodes * 8);
+  s->ct.crow = s->d_crow;
+  s->ct.ncact = (int32_t)p.ncact;
+  s->ct.cwin = s->d_cwin;
+  s->ct.corow = s->d_corow;
+  s->ct.ncown = (int32_t)p.ncown;
+  s->ct.n_active = (int32_t)p.n_active;
+  s->ct.wc = s->d_wc;
   const size_t n8 = (size_t)std::max<int64_t>(s->n, 1) * 8, n4 = (size_t)std::max<int64_t>(s->n, 1) * 4;
   if (e == cudaSuccess) e = cudaMalloc(&s->r, n8);
   if (e == cudaSuccess) e = cudaMalloc(&s->p, n8);
@@ -478,8 +495,8 @@ gp_status gp_system_cells(gp_system* s, int which, double mass_weight, double st
   const cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(y, 0, (size_t)s->n * c->elem, st);
   if (e == cudaSuccess)
-    e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->d_crow, s->cstart, p.mass.data(), p.stiff.data(),
-                                                   p.h, mass_weight, stiff_weight, st);
+    e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(), p.h,
+                                                   mass_weight, stiff_weight, 0, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
