@@ -97,6 +97,9 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   Plane* sb2 = buf + fb;                                  // [fb][K][L], 3D only
   __shared__ V sm[K1][K1];
   const int nt = (int)blockDim.x;
+  // the lift may start its prologue as soon as every face CTA is running (programmatic
+  // dependent launch; it waits for this grid's completion before it reads W)
+  asm volatile("griddepcontrol.launch_dependents;");
 
   if (blk < fa.nzblocks) {
     // zero fill of the active DoFs outside every face patch (overwrite form only):
@@ -474,6 +477,8 @@ __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, 
     win[ln][w] = (cell0 + ln < la.nlift) ? __ldg(la.lwin + (size_t)cell0 * NW + idx) : -1;
   }
   __syncthreads();
+  // wait for the face kernel (a no-op unless launched as its programmatic dependent)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // one pass: item -> (row type m, cell, row of that type); items sorted by type
   const int E1 = cb * S::count(0);
   const int E2 = E1 + cb * S::count(1);

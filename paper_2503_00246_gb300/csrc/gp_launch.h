@@ -134,9 +134,27 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
     face_kernel<D, K, A><<<nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>((const IO*)Ar.x, (V*)Ar.tp,
                                                                           (IO*)Ar.y, fa, t.fb, c);
   if (Ar.ev) cudaEventRecord(Ar.ev[1], st);
-  if (nlb > 0 && faces && (Ar.which & 2))
-    lift_kernel<D, K, A><<<nlb, t.lnt, lift_smem<D, K>(t.lcb), st>>>((const V*)Ar.tp, (IO*)Ar.y, Ar.add, Ar.la,
-                                                                     t.lcb);
+  if (nlb > 0 && faces && (Ar.which & 2)) {
+    if (Ar.ev || !(Ar.which & 1)) {
+      lift_kernel<D, K, A><<<nlb, t.lnt, lift_smem<D, K>(t.lcb), st>>>((const V*)Ar.tp, (IO*)Ar.y, Ar.add, Ar.la,
+                                                                       t.lcb);
+    } else {
+      // programmatic dependent launch: the lift's CTAs start while the face grid drains
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nlb);
+      cfg.blockDim = dim3((unsigned)t.lnt);
+      cfg.dynamicSmemBytes = lift_smem<D, K>(t.lcb);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, lift_kernel<D, K, A>, (const V*)Ar.tp, (IO*)Ar.y, Ar.add, Ar.la,
+                                               (int)t.lcb);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (Ar.ev) cudaEventRecord(Ar.ev[2], st);
   return cudaGetLastError();
 }
