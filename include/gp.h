@@ -216,7 +216,11 @@ gp_status gp_tiles_lookup(int device, int dim, int degree, int precision, gp_til
  *   scale k doubles, s_j = c_j h^{d-2} (the one FP64 factor per order). */
 gp_status gp_reference_1d(const gp_ctx* ctx, double* mass, double* jumps, double* scale);
 
-/* y = G x (y is overwritten on every active DoF). */
+/* y = G x (y is overwritten on every active DoF).  Stream-ordered: work launched
+ * normally on the same stream afterwards sees the complete y.  The second kernel lets
+ * programmatic dependents start early (programmatic dependent launch): a kernel of the
+ * caller launched with programmatic stream serialization right after this call must
+ * wait for its prerequisite grid (griddepcontrol.wait) before it reads y. */
 gp_status gp_apply(gp_ctx* ctx, const void* x, void* y, void* stream);
 
 /* y += G x (only DoFs touched by a ghost face are read and written). */

@@ -15,7 +15,9 @@
 // Two launches, like the face operator: cell_kernel stores every cell's (k+1)^d
 // outputs, and cell_gather adds, for every node, the outputs of the (up to 2^d) active
 // cells that hold it, in a fixed order: no atomics, no colour phases, bitwise
-// reproducible.
+// reproducible.  Both are programmatic dependents of the kernel before them: cell_kernel
+// reads only x and the tables, so it runs while the ghost-penalty lift drains and waits
+// for it only before it exits; cell_gather waits for cell_kernel before it touches y.
 #pragma once
 
 #include <cstdint>
@@ -49,11 +51,17 @@ struct CellTabs {
   const int32_t* crow = nullptr;   // [ncact][R] compact index of each x-line start
   int32_t ncact = 0;
   const int32_t* cwin = nullptr;   // [ncown][NWC] active-cell index of (ci - s_x, cj - s_y, cl - s_z)
-  const int32_t* corow = nullptr;  // [KR][ncown] compact index of node (ci k, cj k + q, cl k + r)
+  const int32_t* corow = nullptr;  // [ncown][KR] compact index of node (ci k, cj k + q, cl k + r)
   int32_t ncown = 0;
   int32_t n_active = 0;
   void* wc = nullptr;              // [ncact][NODES] cell outputs (scratch)
+  // optional fused inner product for CG: per gather CTA, sum over its nodes of
+  // dotp[i] * y[i] (the stored result) into dotpart[blockIdx.x] (fixed order)
+  const void* dotp = nullptr;
+  double* dotpart = nullptr;
 };
+
+constexpr int GATHER_THREADS = 256;
 
 template <int D, int K, class A>
 __global__ void __launch_bounds__(CellShape<D, K>::NT)
@@ -69,6 +77,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
   const int cell = blockIdx.x * CB + cl;
   const bool valid = cell < ncact;
   const int32_t row = valid ? __ldg(crow + (size_t)cell * R + line) : 0;
+  asm volatile("griddepcontrol.launch_dependents;");
 
   // ---- x pass: a = M^ x, b = S^ x on this thread's x-line
   V xl[K1];
@@ -134,6 +143,8 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
         for (int p = 0; p < K1; ++p) dst[i1 + K1 * (i2 + K1 * p)] = yout[p];
       }
     }
+    // the completion of this grid stands for the completion of the kernel before it
+    asm volatile("griddepcontrol.wait;" ::: "memory");
   } else {
     // ---- y pass on the line i1: y = M^ (h^2 a + b) + S^ a
     V ay[K1], by[K1];
@@ -158,6 +169,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
 #pragma unroll
       for (int p = 0; p < K1; ++p) dst[line + K1 * p] = yout[p];
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
   }
 }
 
@@ -165,18 +177,15 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
 // (ci - s_x, cj - s_y, cl - s_z) that hold them (s_y = 1 only for q = 0, s_z = 1 only for
 // r = 0, s_x = 1 only for p = 0), in the order w = s_x + 2 s_y + 4 s_z.
 template <int D, int K, class A>
-__global__ void __launch_bounds__(256)
-cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y, const int add, const CellTabs ct) {
+__device__ __forceinline__ double gather_row(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y,
+                                             const int add, const CellTabs& ct, const int own, const int t,
+                                             const int base) {
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
-  constexpr int K1 = S::K1, NODES = S::NODES, NWC = S::NWC, KR = S::KR;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ct.ncown * KR) return;
-  const int own = g / KR, t = g - own * KR;
+  constexpr int K1 = S::K1, NODES = S::NODES, NWC = S::NWC;
   const int q = t % K, r = (D == 3) ? t / K : 0;
-  const int base = __ldg(ct.corow + (size_t)t * ct.ncown + own);
-  if (base < 0) return;
+  double dot = 0.0;
   Sum<V> acc[K];
 #pragma unroll
   for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();
@@ -205,8 +214,42 @@ cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y
     if (idx >= ct.n_active) break;
     const V sv = dot_value(acc[p]);
     const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), sv) : sv;
-    y[idx] = to_io(outv, (IO*)nullptr);
+    const IO o = to_io(outv, (IO*)nullptr);
+    y[idx] = o;
+    if (ct.dotp) dot = fma((double)((const IO*)ct.dotp)[idx], (double)o, dot);
   }
+  return dot;
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(GATHER_THREADS)
+cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y, const int add, const CellTabs ct) {
+  using S = CellShape<D, K>;
+  constexpr int KR = S::KR;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = g < ct.ncown * KR;
+  const int own = live ? g / KR : 0, t = live ? g - own * KR : 0;
+  const int base = live ? __ldg(ct.corow + (size_t)g) : -1;            // = [own][t]
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // cell outputs and y are complete
+  double dot = 0.0;
+  if (base >= 0) dot = gather_row<D, K, A>(wc, y, add, ct, own, t, base);
+  if (ct.dotpart) {
+    __shared__ double sh[GATHER_THREADS];
+    sh[threadIdx.x] = dot;
+    __syncthreads();
+    for (int o = GATHER_THREADS / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ct.dotpart[blockIdx.x] = sh[0];
+  }
+}
+
+// CTAs of the gather (the number of fused inner-product partials)
+template <int D, int K>
+inline int gather_blocks(const CellTabs& ct) {
+  const int64_t rows = (int64_t)ct.ncown * CellShape<D, K>::KR;
+  return (int)((rows + GATHER_THREADS - 1) / GATHER_THREADS);
 }
 
 // y (+)= (wm M_active + ws K_active) x: the cell kernel, then the gather (add = 1: onto y).
@@ -225,11 +268,24 @@ cudaError_t run_cells(const void* x, void* y, const CellTabs& ct, const double* 
   c.hm = from_host<V>(wm * (D == 3 ? h * h * h : h * h));
   c.hs = from_host<V>(ws * (D == 3 ? h : 1.0));
   if (ct.ncact <= 0) return cudaSuccess;
-  cell_kernel<D, K, A><<<(ct.ncact + S::CB - 1) / S::CB, S::NT, 0, st>>>((const IO*)x, (V*)ct.wc, ct.crow, ct.ncact,
-                                                                          c);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((ct.ncact + S::CB - 1) / S::CB));
+  cfg.blockDim = dim3((unsigned)S::NT);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, cell_kernel<D, K, A>, (const IO*)x, (V*)ct.wc, ct.crow, ct.ncact, c);
+  if (e != cudaSuccess) return e;
   const int64_t rows = (int64_t)ct.ncown * S::KR;
-  if (rows > 0)
-    cell_gather<D, K, A><<<(int)((rows + 255) / 256), 256, 0, st>>>((const V*)ct.wc, (IO*)y, add, ct);
+  if (rows > 0) {
+    cfg.gridDim = dim3((unsigned)gather_blocks<D, K>(ct));
+    cfg.blockDim = dim3((unsigned)GATHER_THREADS);
+    e = cudaLaunchKernelEx(&cfg, cell_gather<D, K, A>, (const V*)ct.wc, (IO*)y, add, ct);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

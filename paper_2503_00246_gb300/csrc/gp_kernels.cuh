@@ -74,7 +74,7 @@ constexpr int ZGROUP = 16;  // zero runs per zero-fill CTA
 
 struct LiftArgs {
   const int32_t* lwin;    // [nlift][NW] candidate face ids of each owner cell (-1 if none)
-  const int32_t* lrow;    // [KR][nlift] compact index of node (ci k, cj k + q, cl k + r)
+  const int32_t* lrow;    // [nlift][KR] compact index of node (ci k, cj k + q, cl k + r)
   int32_t nlift;
   int32_t n_active;
 };
@@ -477,8 +477,10 @@ __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, 
     win[ln][w] = (cell0 + ln < la.nlift) ? __ldg(la.lwin + (size_t)cell0 * NW + idx) : -1;
   }
   __syncthreads();
-  // wait for the face kernel (a no-op unless launched as its programmatic dependent)
+  // wait for the face kernel (a no-op unless launched as its programmatic dependent), and
+  // let a programmatic dependent of this grid start (the cell operator of the model system)
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   // one pass: item -> (row type m, cell, row of that type); items sorted by type
   const int E1 = cb * S::count(0);
   const int E2 = E1 + cb * S::count(1);
@@ -501,7 +503,7 @@ __device__ __forceinline__ void lift_body(const typename A::V* __restrict__ wp, 
       if (D == 3 && !(m & 2)) { r = 1 + rem % (K - 1); }
     }
     const int row = q + (D == 3 ? K * r : 0);
-    const int base = __ldg(la.lrow + (size_t)row * la.nlift + cell);
+    const int base = __ldg(la.lrow + (size_t)cell * S::KR + row);
     Sum<V> acc[K];
 #pragma unroll
     for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();

@@ -235,7 +235,7 @@ void build_cell_table(Plan& p) {
         const int64_t row = (int64_t)Y + (d == 3 ? (int64_t)p.nl * Z : 0);
         cidx = p.compact(X, row);
       }
-      p.corow[(size_t)t * p.ncown + i] = (int32_t)cidx;
+      p.corow[(size_t)i * KR + t] = (int32_t)cidx;
     }
   }
 }
@@ -838,7 +838,7 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
           int64_t row = (int64_t)Y + (d == 3 ? (int64_t)p.nl * Z : 0);
           cidx = p.compact(X, row);
         }
-        p.lrow[(size_t)t * nlift + i] = (int32_t)cidx;
+        p.lrow[(size_t)i * KR + t] = (int32_t)cidx;
       }
     }
   }

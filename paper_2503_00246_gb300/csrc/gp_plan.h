@@ -47,7 +47,7 @@ struct Plan {
   std::vector<int32_t> runs;      // (X0, X1) inclusive pairs
 
   // lift work: owner cells (ci, cj, cl, 0) with coordinates in [0, n], sorted by the
-  // pattern of faces whose patch reaches them; lrow[row][cell] is the compact index of
+  // pattern of faces whose patch reaches them; lrow[cell][row] is the compact index of
   // node (ci*k, cj*k+q, cl*k+r), row = q + k r, or -1 if that node is inactive
   std::vector<int32_t> lcell;
   std::vector<int32_t> lrow;
@@ -64,7 +64,7 @@ struct Plan {
   int64_t ncact = 0;
   // owner cells of the active nodes (coordinates in [0, n], lexicographic): per owner the
   // active-cell index of the 2^d cells (ci - s_x, cj - s_y, cl - s_z) (-1 if none), and per
-  // x-row (q, r) the compact index of node (ci k, cj k + q, cl k + r) ([KR][ncown], -1 if none)
+  // x-row (q, r) the compact index of node (ci k, cj k + q, cl k + r) ([ncown][KR], -1 if none)
   std::vector<int32_t> cwin;
   std::vector<int32_t> corow;
   int64_t ncown = 0;

@@ -25,6 +25,7 @@ struct gp_system {
   int32_t* d_corow = nullptr;
   void* d_wc = nullptr;     // cell outputs (scratch, 8 bytes per value)
   gp::CellTabs ct{};
+  int nparts = 0;           // CTAs of the cell gather (fused inner-product partials)
   gp::CellsFn cells_hi = nullptr, cells_lo = nullptr;
   // solver vectors
   double *r = nullptr, *p = nullptr, *q = nullptr, *dd = nullptr, *z = nullptr, *ri = nullptr;
@@ -121,12 +122,17 @@ cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
 }
 
 // y = A x with the operator of context c (G, then the cell colours adding on top)
+// y = A x; with dotp, the cell gather also leaves the partial sums of dotp . y (one per
+// gather CTA, s->nparts of them) in s->part.
 gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st,
-                    bool trace = true) {
+                    bool trace = true, const void* dotp = nullptr) {
   gp_status g = gpi::launch(c, x, y, 0, st, nullptr, trace);
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
-  const cudaError_t e = cells(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 1, st);
+  gp::CellTabs ct = s->ct;
+  ct.dotp = dotp;
+  ct.dotpart = dotp ? s->part : nullptr;
+  const cudaError_t e = cells(p.k, x, y, ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 1, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
@@ -201,11 +207,12 @@ __global__ void __launch_bounds__(kThreads) cg_init_final(const double* __restri
   }
 }
 
-// alpha = rz / (p.q) from the partial sums of p.q
-__global__ void __launch_bounds__(kThreads) cg_alpha(const double* __restrict__ part, CgScalars* sc) {
+// alpha = rz / (p.q) from the nparts partial sums of p.q
+__global__ void __launch_bounds__(kThreads) cg_alpha(const double* __restrict__ part, const int nparts,
+                                                     CgScalars* sc) {
   __shared__ double sh[kThreads];
   double a = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) a += part[i];
+  for (int i = threadIdx.x; i < nparts; i += kThreads) a += part[i];
   sh[threadIdx.x] = a;
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
@@ -350,10 +357,9 @@ gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* 
   SYS_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   gp_status g = GP_OK;
   for (int i = 0; i < kCgBlock && g == GP_OK; ++i) {
-    g = sys_apply(s, c, cells, p, q, s->st, false);
+    g = sys_apply(s, c, cells, p, q, s->st, false, p);   // q = A p and the partial sums of p . q
     if (g != GP_OK) break;
-    dot_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(p, q, n, s->part);
-    cg_alpha<<<1, kThreads, 0, s->st>>>(s->part, sc);
+    cg_alpha<<<1, kThreads, 0, s->st>>>(s->part, s->nparts, sc);
     cg_update<T><<<kDotBlocks, kThreads, 0, s->st>>>(d, r, p, q, z, dinv, sc, n, s->part);
     cg_beta<<<1, kThreads, 0, s->st>>>(s->part, sc);
     cg_direction<T><<<kVecBlocks, kThreads, 0, s->st>>>(p, zz, sc, n);
@@ -464,7 +470,9 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->ri32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->p32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->q32, n4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->part, (2 * kDotBlocks + 1) * sizeof(double));
+  s->nparts = (int)(((int64_t)p.ncown * gp::ipow_host(p.k, p.dim - 1) + gp::GATHER_THREADS - 1) / gp::GATHER_THREADS);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&s->part, (size_t)std::max<int64_t>(2 * kDotBlocks + 1, s->nparts) * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_cg, sizeof(CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_cg, sizeof(CgScalars));
@@ -493,10 +501,9 @@ gp_status gp_system_cells(gp_system* s, int which, double mass_weight, double st
   DeviceGuard dg(s->device);
   const gp::Plan& p = c->plan;
   const cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(y, 0, (size_t)s->n * c->elem, st);
-  if (e == cudaSuccess)
-    e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(), p.h,
-                                                   mass_weight, stiff_weight, 0, st);
+  // the gather overwrites every active DoF (each is a node of an active cell)
+  const cudaError_t e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(),
+                                                                 p.h, mass_weight, stiff_weight, 0, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
