@@ -145,11 +145,12 @@ def _check(status, ctx=None):
 class Context:
     """Owns a gp_ctx handle (gp_destroy on close / garbage collection)."""
 
-    def __init__(self, handle, precision, dim, degree):
+    def __init__(self, handle, precision, dim, degree, device=0):
         self.handle = handle
         self.precision = precision
         self.dim = dim
         self.degree = degree
+        self.device = device
         n = C.c_int64()
         _check(lib.gp_num_active_dofs(handle, C.byref(n)), self)
         self.n_active = n.value
@@ -177,7 +178,7 @@ class Context:
 def gp_setup(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts) -> Context:
     h = C.c_void_p()
     _check(lib.gp_setup(C.byref(mesh), C.byref(levelset), C.byref(opts), C.byref(h)))
-    return Context(h.value, opts.precision, mesh.dim, opts.degree)
+    return Context(h.value, opts.precision, mesh.dim, opts.degree, opts.device)
 
 
 def gp_destroy(ctx: Context):
@@ -435,6 +436,39 @@ def gp_tiles_lookup(device: int, dim: int, degree: int, precision: int):
     if lib.gp_tiles_lookup(device, dim, degree, precision, C.byref(t)) != GP_OK:
         return None
     return _tiles_dict(t)
+
+
+def tiles_cache_path() -> str:
+    """The autotuner's cache file: $GP_TILES_CACHE, else ~/.cache/gp_gb300/tiles.json."""
+    return os.environ.get("GP_TILES_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "gp_gb300",
+                                                             "tiles.json")
+
+
+def autotune_cached(ctx: Context, reps: int = 10, path: str | None = None) -> dict:
+    """Tile shapes for ctx from the cache file, keyed by (GPU name, d, k, precision); on a miss
+    gp_autotune times the candidates and the result is written back.  Either way the shape is
+    set on ctx and recorded in the library's table for new contexts."""
+    import json
+    import torch
+    path = path or tiles_cache_path()
+    key = f"{torch.cuda.get_device_name(ctx.device)}|d{ctx.dim}|k{ctx.degree}|p{ctx.precision}"
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        tiles = cache[key]
+        gp_set_tiles(ctx, tiles)
+        gp_tiles_record(ctx.device, ctx.dim, ctx.degree, ctx.precision, tiles)
+        return tiles
+    tiles, _ = gp_autotune(ctx, reps)
+    cache[key] = tiles
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return tiles
 
 
 def gp_partition_info(ctx: Context) -> dict:

@@ -87,3 +87,19 @@ def test_batch_with_tuned_groups_equals_single_applies(gplib, cuda):
             cuda.cuda.synchronize()
             assert cuda.equal(y[s], yr)
     gplib.gp_batch_destroy(b)
+
+
+def test_autotune_cache_file(gplib, cuda, tmp_path):
+    import json
+    path = str(tmp_path / "tiles.json")
+    pr = W.small_ball(3, 16, 2, seed=12)
+    ctx = gplib.setup_problem(pr, precision=1)
+    t1 = gplib.autotune_cached(ctx, reps=2, path=path)
+    data = json.load(open(path))
+    assert len(data) == 1 and list(data.values())[0] == t1 and "|d3|k2|p1" in list(data)[0]
+    # a hit sets the stored shape without timing
+    data[list(data)[0]] = {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
+    json.dump(data, open(path, "w"))
+    ctx2 = gplib.setup_problem(pr, precision=1)
+    assert gplib.autotune_cached(ctx2, path=path) == {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
+    assert gplib.gp_get_tiles(ctx2) == {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
