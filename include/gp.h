@@ -104,7 +104,16 @@ typedef struct {
   int part_lo, part_hi;     /* 0, 0: the whole mesh.  Otherwise this context is the slab
                                partition of cell layers [part_lo, part_hi) along the last
                                axis (y in 2D, z in 3D); see gp_partition_info */
+  int stabilization;        /* GP_STAB_GHOST (0, the ghost penalty) or GP_STAB_MACRO */
 } gp_opts;
+
+/* Stabilisations.  GP_STAB_MACRO is the macro-patch alternative the paper names next to the
+ * ghost penalty (Sec. 2.2): per ghost face, gamma times the integral over each of its two
+ * cells of the square of (the function there - the extension of the neighbour cell's
+ * polynomial into it).  On the Cartesian patch it has the same Kronecker form,
+ * gamma h^d (M^ x ... x G^mp), with a 1D matrix G^mp of rank k; weights and nweights are
+ * ignored. */
+enum { GP_STAB_GHOST = 0, GP_STAB_MACRO = 1 };
 
 /* Classify cells, collect the ghost faces, number the active DoFs, build the
  * 1D matrices in FP64 and upload the face tables (Sec. 2, Sec. 2.4, Sec. 2.7).
@@ -269,7 +278,7 @@ gp_status gp_profile_read(gp_ctx* ctx, double ms[2], int64_t* calls);
 /* Batched form: several independent problems, nrhs right-hand sides each, replayed
  * as one CUDA graph (the batched workload of many meshes of uneven n, k and
  * geometry).  gp_batch_create groups the problems by (dimension, degree,
- * arithmetic); every (problem, right-hand side) pair gets its own face-output
+ * arithmetic, stabilisation); every (problem, right-hand side) pair gets its own face-output
  * buffer, and one face launch plus one lift launch per group cover all pairs.  The
  * graph also holds the host-to-device copy of the table of x / y pointers, so each
  * gp_batch_apply writes that table (pinned host memory) and launches the graph.

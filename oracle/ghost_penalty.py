@@ -104,10 +104,15 @@ class Oracle:
 
     def A(self, axis: int) -> np.ndarray:
         """One explicit face matrix per axis: on a uniform Cartesian mesh every
-        face of a given normal direction has the same matrix (Sec. 2.2)."""
+        face of a given normal direction has the same matrix (Sec. 2.2).  For a
+        problem with the macro-patch stabilisation, its matrix (oracle.macro_patch)."""
         if axis not in self._A:
             pr = self.pr
-            self._A[axis] = face_matrix(pr.dim, pr.degree, pr.h, axis, pr.cweights())
+            if getattr(pr, "stabilization", 0) == 1:
+                from .macro_patch import face_matrix_macro
+                self._A[axis] = face_matrix_macro(pr.dim, pr.degree, pr.h, axis, pr.gamma)
+            else:
+                self._A[axis] = face_matrix(pr.dim, pr.degree, pr.h, axis, pr.cweights())
         return self._A[axis]
 
     def patch_index(self, axis: int) -> np.ndarray:

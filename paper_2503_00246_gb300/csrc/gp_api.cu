@@ -465,11 +465,11 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
   b->nrhs = nrhs;
   b->ctxs.assign(ctxs, ctxs + nprob);
   DeviceGuard dg(b->device);
-  // group problems by (dimension, degree, arithmetic)
-  std::map<std::tuple<int, int, int>, int> key;
+  // group problems by (dimension, degree, arithmetic, stabilisation)
+  std::map<std::tuple<int, int, int, int>, int> key;   // (d, k, arithmetic, stabilisation): one set of 1D data
   for (int p = 0; p < nprob; ++p) {
     const gp::Plan& pl = ctxs[p]->plan;
-    auto kk = std::make_tuple(pl.dim, pl.k, pl.precision);
+    auto kk = std::make_tuple(pl.dim, pl.k, pl.precision, pl.stabilization);
     auto it = key.find(kk);
     int gi;
     if (it == key.end()) {

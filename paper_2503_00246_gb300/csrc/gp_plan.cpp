@@ -148,6 +148,107 @@ void reference_1d(int k, const std::vector<double>& /*gl*/, std::vector<double>&
     }
 }
 
+// Macro-patch stabilisation (the alternative named in Sec. 2.2): on the two-cell patch
+// [0,1] u [1,2] of a face, the difference between the polynomial on one cell and the
+// extension of the neighbour's polynomial into it, squared and integrated over both cells:
+//   G^mp = sum_q w_q (d_q d_q^T + e_q e_q^T),
+//   d_q[b] = [b >= k] l_{b-k}(t_q) - [b <= k] l_b(1 + t_q)       (K+, the K- polynomial extended),
+//   e_q[b] = [b <= k] l_b(t_q) - [b >= k] l_{b-k}(t_q - 1)       (K-, the K+ polynomial extended),
+// with the k+1 Gauss points t_q of [0,1] (exact: the integrands have degree 2k).  G^mp is
+// mirror symmetric and vanishes exactly on the patch interpolants of global polynomials of
+// degree <= k, the null space of the ghost-penalty matrix, so it has rank k and the same range:
+// G^mp = sum_j lambda_j v_j v_j^T with eigenvectors of alternating parity, odd orders (j = 1,
+// 3, ...) mirror symmetric and even orders antisymmetric, like the jump vectors g_j.  The face
+// kernels then apply it unchanged with v_j in place of g_j and lambda_j in place of c_j.
+// Eigenvectors by cyclic Jacobi rotations in long double.
+static R lagrange_at(const std::vector<R>& gl, int m, R x) {
+  R v = 1;
+  for (size_t i = 0; i < gl.size(); ++i)
+    if ((int)i != m) v *= (x - gl[i]) / (gl[m] - gl[i]);
+  return v;
+}
+
+bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda) {
+  const int N = k + 1, NN = 2 * k + 1;
+  std::vector<R> gl, tq, wq;
+  gauss_lobatto_01_r(k, gl);
+  gauss_legendre_01(N, tq, wq);
+  std::vector<R> A(NN * NN, R(0)), d(NN), e(NN);
+  for (int q = 0; q < N; ++q) {
+    for (int b = 0; b < NN; ++b) {
+      d[b] = (b >= k ? lagrange_at(gl, b - k, tq[q]) : R(0)) - (b <= k ? lagrange_at(gl, b, 1 + tq[q]) : R(0));
+      e[b] = (b <= k ? lagrange_at(gl, b, tq[q]) : R(0)) - (b >= k ? lagrange_at(gl, b - k, tq[q] - 1) : R(0));
+    }
+    for (int a = 0; a < NN; ++a)
+      for (int b = 0; b < NN; ++b) A[a * NN + b] += wq[q] * (d[a] * d[b] + e[a] * e[b]);
+  }
+  // cyclic Jacobi: A = V diag(ev) V^T
+  std::vector<R> V(NN * NN, R(0));
+  for (int i = 0; i < NN; ++i) V[i * NN + i] = 1;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    R off = 0, tot = 0;
+    for (int a = 0; a < NN; ++a)
+      for (int b = 0; b < NN; ++b) {
+        tot += A[a * NN + b] * A[a * NN + b];
+        if (a != b) off += A[a * NN + b] * A[a * NN + b];
+      }
+    if (off <= tot * R(1e-36)) break;
+    for (int p = 0; p < NN; ++p)
+      for (int q = p + 1; q < NN; ++q) {
+        const R apq = A[p * NN + q];
+        if (apq == 0) continue;
+        const R theta = (A[q * NN + q] - A[p * NN + p]) / (2 * apq);
+        const R t = (theta >= 0 ? 1 : -1) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        const R c = 1 / std::sqrt(t * t + 1), sn = t * c;
+        for (int r = 0; r < NN; ++r) {          // A <- J^T A J, V <- V J
+          const R arp = A[r * NN + p], arq = A[r * NN + q];
+          A[r * NN + p] = c * arp - sn * arq;
+          A[r * NN + q] = sn * arp + c * arq;
+        }
+        for (int r = 0; r < NN; ++r) {
+          const R apr = A[p * NN + r], aqr = A[q * NN + r];
+          A[p * NN + r] = c * apr - sn * aqr;
+          A[q * NN + r] = sn * apr + c * aqr;
+        }
+        for (int r = 0; r < NN; ++r) {
+          const R vrp = V[r * NN + p], vrq = V[r * NN + q];
+          V[r * NN + p] = c * vrp - sn * vrq;
+          V[r * NN + q] = sn * vrp + c * vrq;
+        }
+      }
+  }
+  // the k largest eigenvalues; parity of each eigenvector
+  std::vector<int> order(NN);
+  for (int i = 0; i < NN; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return A[a * NN + a] > A[b * NN + b]; });
+  R top = A[order[0] * NN + order[0]];
+  std::vector<int> sym, anti;
+  for (int r = 0; r < k; ++r) {
+    const int c = order[r];
+    R ds = 0, da = 0;
+    for (int b = 0; b < NN; ++b) {
+      ds += std::fabs(V[b * NN + c] - V[(NN - 1 - b) * NN + c]);
+      da += std::fabs(V[b * NN + c] + V[(NN - 1 - b) * NN + c]);
+    }
+    (ds < da ? sym : anti).push_back(c);
+  }
+  // a rank-k matrix: the (k+1)-th eigenvalue is rounding noise
+  if (k < NN && A[order[k] * NN + order[k]] > top * R(1e-12)) return false;
+  if ((int)sym.size() != (k + 1) / 2 || (int)anti.size() != k / 2) return false;
+  vecs.assign((size_t)k * NN, 0.0);
+  lambda.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    const int c = (j % 2 == 0) ? sym[j / 2] : anti[j / 2];
+    lambda[j] = (double)A[c * NN + c];
+    for (int b = 0; b < NN; ++b) {
+      // exact mirror symmetry, so that the kernels' even-odd split is exact
+      const R v = V[b * NN + c], w = V[(NN - 1 - b) * NN + c];
+      vecs[(size_t)j * NN + b] = (double)((j % 2 == 0) ? (v + w) / 2 : (v - w) / 2);
+    }
+  }
+  return true;
+}
+
 // S^[a][b] = int_0^1 l_a' l_b' with k+1 Gauss points (exact for degree 2k-2); the
 // derivative of l_m is evaluated as sum_i 1/(x_m - x_i) prod_{l != m, i} (x - x_l)/(x_m - x_l),
 // which stays finite when a Gauss point coincides with a node.
@@ -848,6 +949,16 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
   reference_1d(k, p.gl, p.mass, p.jumps);
   reference_stiffness(k, p.stiff);
   p.scale.resize(k);
+  p.stabilization = opts->stabilization;
+  if (opts->stabilization == GP_STAB_MACRO) {
+    // macro patch: gamma h^d sum_j lambda_j (M^ x ... x v_j v_j^T)  (volume integral: h per direction)
+    std::vector<double> lam;
+    if (!macro_patch_1d(k, p.jumps, lam)) { err = "internal: macro-patch matrix not of rank k"; return GP_EINVAL; }
+    const double hv = d == 3 ? h * h * h : h * h;
+    for (int j = 0; j < k; ++j) p.scale[j] = opts->gamma * lam[j] * hv;
+    return GP_OK;
+  }
+  if (opts->stabilization != GP_STAB_GHOST) { err = "unknown stabilization"; return GP_EINVAL; }
   const double hd = d == 3 ? h : 1.0;
   for (int j = 0; j < k; ++j) {
     double c = opts->nweights == k ? opts->weights[j] : opts->gamma;

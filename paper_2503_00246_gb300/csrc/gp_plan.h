@@ -82,7 +82,8 @@ struct Plan {
   std::vector<double> stiff;      // (k+1)^2: int_0^1 l_a' l_b' 
   std::vector<double> mass;       // (k+1)^2
   std::vector<double> jumps;      // k x (2k+1)
-  std::vector<double> scale;      // k: c_j h^(dim-2)
+  std::vector<double> scale;      // k: c_j h^(dim-2) (macro patch: gamma lambda_j h^dim)
+  int stabilization = GP_STAB_GHOST;
 
   int64_t num_faces() const { return (int64_t)face_cell.size(); }
   int64_t compact(int X, int64_t row) const;
@@ -107,6 +108,9 @@ void gauss_lobatto_01(int k, std::vector<double>& x);
 void reference_1d(int k, const std::vector<double>& gl, std::vector<double>& mass,
                   std::vector<double>& jumps);
 void reference_stiffness(int k, std::vector<double>& stiff);
+// Macro-patch 1D data: k mirror-(anti)symmetric vectors (k x (2k+1)) and weights lambda_j;
+// false if the matrix is not of rank k with the expected parities.
+bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // diag(M_active + K_active + G) in FP64 (needs the cell table).

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgp.so")
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_EDEVICE, GP_EUNSUPPORTED = range(6)
 GP_FP64, GP_FP32, GP_FP64_FF = 0, 1, 2
 GP_LS_BALLS, GP_LS_GYROID, GP_LS_CALLBACK, GP_LS_CONST = 1, 2, 3, 4
+GP_STAB_GHOST, GP_STAB_MACRO = 0, 1
 _STATUS = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ECUDA", 4: "GP_EDEVICE",
            5: "GP_EUNSUPPORTED"}
 
@@ -57,7 +58,7 @@ class gp_solve_stats(C.Structure):
 class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
-                ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int)]
+                ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int), ("stabilization", C.c_int)]
 
 
 class gp_tiles(C.Structure):
@@ -551,6 +552,7 @@ def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=N
     opts.precision = precision
     opts.all_faces = 1 if pr.all_faces else 0
     opts.device = device
+    opts.stabilization = int(getattr(pr, "stabilization", 0))
     if part is not None:
         opts.part_lo, opts.part_hi = int(part[0]), int(part[1])
     return mesh, ls, opts, keep

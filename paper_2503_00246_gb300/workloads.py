@@ -47,6 +47,7 @@ class Problem:
     ls_value: float = 1.0       # constant level set (every cell inside when > 0)
     all_faces: bool = False     # treat every interior face of the active mesh as a penalised face
     seed: int = BASE_SEED
+    stabilization: int = 0      # 0: ghost penalty; 1: macro patch (gamma, no per-order weights)
 
     @property
     def h(self) -> float:

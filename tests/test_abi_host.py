@@ -199,3 +199,28 @@ def test_jump_vectors_mirror_symmetry(gplib, k):
         assert np.abs(row[::-1] * (-1) ** (j + 1) - row).max() <= 1e-14 * scale
         if j % 2 == 0:
             assert abs(row[k]) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 4), (2, 8), (3, 2), (3, 3), (3, 5)])
+def test_macro_patch_1d_data_matches_oracle(gplib, dim, k):
+    # the host's rank-k form gamma h^d sum_j lambda_j (M^ x ... x v_j v_j^T) against the oracle's
+    # explicit macro-patch face matrix (no factorisation there)
+    from oracle.macro_patch import face_matrix_macro
+    pr = W.small_ball(dim, 8, k, seed=4)
+    pr.stabilization = gplib.GP_STAB_MACRO
+    ctx = gplib.setup_problem(pr, device=-1)
+    mass, g, s = gplib.gp_reference_1d(ctx)
+    M = np.asarray(mass).reshape(k + 1, k + 1)
+    g = np.asarray(g).reshape(k, 2 * k + 1)
+    s = np.asarray(s)
+    G = sum(s[j] * np.outer(g[j], g[j]) for j in range(k))
+    # mirror parities alternate (odd orders symmetric), as the face kernel's even-odd split assumes
+    for j in range(k):
+        assert np.abs(g[j][::-1] * (1 if j % 2 == 0 else -1) - g[j]).max() <= 1e-15 * np.abs(g[j]).max()
+    for axis in range(dim):
+        fac = [G if a == axis else M for a in range(dim)]
+        K = fac[-1]
+        for f in reversed(fac[:-1]):
+            K = np.kron(K, f)
+        A = face_matrix_macro(dim, k, pr.h, axis, pr.gamma)
+        assert np.abs(A - K).max() <= 1e-11 * np.abs(A).max(), axis
