@@ -341,6 +341,17 @@ void build_cell_table(Plan& p) {
   }
 }
 
+bool check_cell_table(const Plan& p) {
+  const int64_t na = p.n_active, K1 = p.k + 1;
+  for (int32_t r : p.crow)
+    if (r < 0 || r + K1 > na) return false;
+  for (int32_t c : p.cwin)
+    if (c < -1 || c >= p.ncact) return false;
+  for (int32_t r : p.corow)
+    if (r < -1 || r >= na) return false;
+  return true;
+}
+
 // Diagonal of the model system: per active cell h^d M_ii M_jj M_kk + h^(d-2) (S_ii M_jj M_kk +
 // M_ii S_jj M_kk + M_ii M_jj S_kk) at local node (i, j, k); per ghost face
 // sum_j s_j g_j[b]^2 times the tangential M^ diagonals at patch node (b, tau).
@@ -431,7 +442,7 @@ static void classify_balls(const Plan& p, const gp_levelset* ls, int n, std::vec
 
 // Sampled classification with a Lipschitz margin: phi on an (m+1)^d lattice
 // per cell; inside if min > margin, outside if max < -margin, else cut.
-static void classify_sampled(const Plan& p, const gp_levelset* ls, int n, double domain_hi0,
+static bool classify_sampled(const Plan& p, const gp_levelset* ls, int n, double domain_hi0,
                              std::vector<int8_t>& cls) {
   const int d = p.dim;
   const int m = ls->samples > 0 ? ls->samples : 4;
@@ -470,11 +481,13 @@ static void classify_sampled(const Plan& p, const gp_levelset* ls, int n, double
       for (int b = 0; b <= m; ++b)
         for (int a = 0; a <= m; ++a) {
           double v = phi(ix * m + a, iy * m + b, iz * m + c);
+          if (!std::isfinite(v)) return false;
           mn = std::min(mn, v);
           mx = std::max(mx, v);
         }
     cls[cell] = (mx < -margin) ? OUTSIDE : ((mn > margin) ? INSIDE : CUT);
   }
+  return true;
 }
 
 // ----------------------------------------------------------- numbering --
@@ -599,11 +612,14 @@ static gp_status classify_mesh(const gp_mesh* mesh, const gp_levelset* ls, const
       break;
     case GP_LS_GYROID:
       if (d != 3) { err = "the gyroid level set is 3D"; return GP_EINVAL; }
-      classify_sampled(p, ls, n, mesh->hi[0], p.cls);
+      if (!classify_sampled(p, ls, n, mesh->hi[0], p.cls)) { err = "the level set is not finite"; return GP_EINVAL; }
       break;
     case GP_LS_CALLBACK:
       if (!ls->fn || !(ls->lipschitz > 0)) { err = "callback level set needs fn and lipschitz > 0"; return GP_EINVAL; }
-      classify_sampled(p, ls, n, mesh->hi[0], p.cls);
+      if (!classify_sampled(p, ls, n, mesh->hi[0], p.cls)) {
+        err = "the level-set callback returned a value that is not finite";
+        return GP_EINVAL;
+      }
       break;
     default:
       err = "unknown level-set kind";
@@ -942,6 +958,29 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
         p.lrow[(size_t)i * KR + t] = (int32_t)cidx;
       }
     }
+  }
+
+  // ---- bounds of every index the kernels read or write (the GPU has no bounds checker here)
+  {
+    const int64_t na = p.n_active, K1 = k + 1, NN = 2 * k + 1;
+    const int R1 = d == 3 ? (int)(NN * K1) : (int)NN;
+    for (int a = 0; a < d; ++a) {
+      const int64_t rows = (int64_t)(p.fstart[a + 1] - p.fstart[a]) * (a == 0 ? L : R1);
+      const int64_t span = a == 0 ? NN : K1;          // contiguous values read from each row start
+      for (int64_t i = 0; i < rows; ++i) {
+        const int64_t r = p.frows[p.rbase[a] + i];
+        if (r < 0 || r + span > na) { err = "internal: face row outside the active DoFs"; return GP_EINVAL; }
+      }
+    }
+    for (int32_t f : p.lwin)
+      if (f < -1 || f >= (int32_t)nf) { err = "internal: lift window outside the face list"; return GP_EINVAL; }
+    for (int32_t r : p.lrow)
+      if (r < -1 || r >= na) { err = "internal: lift row outside the active DoFs"; return GP_EINVAL; }
+    for (size_t i = 0; i + 1 < p.zruns.size(); i += 2)
+      if (p.zruns[i] < 0 || p.zruns[i + 1] < 1 || p.zruns[i + 1] > ZRUN_MAX || p.zruns[i] + p.zruns[i + 1] > na) {
+        err = "internal: zero run outside the active DoFs";
+        return GP_EINVAL;
+      }
   }
 
   // ---- 1D reference data and the per-order scale c_j h^(d-2)

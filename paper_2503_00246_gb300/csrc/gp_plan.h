@@ -113,6 +113,8 @@ void reference_stiffness(int k, std::vector<double>& stiff);
 bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
+// Every index of the cell table inside the active DoFs and the active cells.
+bool check_cell_table(const Plan& p);
 // diag(M_active + K_active + G) in FP64 (needs the cell table).
 void build_diagonal(const Plan& p, std::vector<double>& diag);
 

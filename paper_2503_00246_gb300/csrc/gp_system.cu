@@ -415,6 +415,10 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   DeviceGuard dg(s->device);
   gp::Plan& p = hi->plan;
   if (p.crow.empty() && p.n_active > 0) gp::build_cell_table(p);
+  if (!gp::check_cell_table(p)) {
+    delete s;
+    return fail(nullptr, GP_EINVAL, "internal: cell table outside the active DoFs");
+  }
   s->cells_hi = cells_for(p);
   if (lo) s->cells_lo = cells_for(lo->plan);
   auto cleanup = [&](cudaError_t e) {

@@ -224,3 +224,32 @@ def test_macro_patch_1d_data_matches_oracle(gplib, dim, k):
             K = np.kron(K, f)
         A = face_matrix_macro(dim, k, pr.h, axis, pr.gamma)
         assert np.abs(A - K).max() <= 1e-11 * np.abs(A).max(), axis
+
+
+def test_callback_level_set_and_non_finite_values(gplib):
+    # a callback ball phi = r - |x - c| (Lipschitz 1) classifies like the exact ball test up to
+    # the sampling margin: every exactly inside/outside cell keeps its class or becomes cut
+    import math
+    pr = W.small_ball(3, 12, 2, radius=0.6, seed=9)
+    c = np.asarray(pr.centers, dtype=np.float64).reshape(-1, 3)[0]
+    exact = gplib.setup_problem(pr, device=-1)
+    mesh, ls, opts, keep = gplib.structs_for(pr, device=-1)
+
+    def ball(xp, user):
+        return 0.6 - math.sqrt(sum((xp[a] - c[a]) ** 2 for a in range(3)))
+    fn = gplib.LEVELSET_FN(ball)
+    ls.kind = gplib.GP_LS_CALLBACK
+    ls.fn = fn
+    ls.lipschitz = 1.0
+    ctx = gplib.gp_setup(mesh, ls, opts)
+    ce = gplib.gp_cell_classes(exact, 12 ** 3)
+    cc = gplib.gp_cell_classes(ctx, 12 ** 3)
+    assert np.all((cc == ce) | (cc == 1))
+    assert np.count_nonzero(cc == 2) > 0 and np.count_nonzero(cc == 0) > 0
+
+    def bad(xp, user):
+        return float("nan") if xp[0] > 0.5 else 1.0
+    ls.fn = gplib.LEVELSET_FN(bad)
+    with pytest.raises(gplib.GpError) as e:
+        gplib.gp_setup(mesh, ls, opts)
+    assert e.value.status == gplib.GP_EINVAL and "finite" in str(e.value)
