@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "gp_arith.cuh"
+#include "gp_kernels.cuh"
 
 namespace gp {
 
@@ -59,6 +60,12 @@ struct CellTabs {
   // dotp[i] * y[i] (the stored result) into dotpart[blockIdx.x] (fixed order)
   const void* dotp = nullptr;
   double* dotpart = nullptr;
+  // optional fused ghost penalty (the model system's M + K + G in one gather): the face
+  // kernel's outputs, its candidate-face windows per lift owner cell, and per owner cell of
+  // this table its lift owner index (-1: no ghost face reaches it)
+  const void* wf = nullptr;
+  const int32_t* fwin = nullptr;
+  const int32_t* own2lift = nullptr;
 };
 
 constexpr int GATHER_THREADS = 256;
@@ -190,6 +197,22 @@ __device__ __forceinline__ double gather_row(const typename A::V* __restrict__ w
 #pragma unroll
   for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();
   bool any0 = false, anyp = false;
+  if (ct.wf) {
+    // the ghost penalty first: the faces whose patch holds this row, in the lift's order
+    const int li = __ldg(ct.own2lift + own);
+    if (li >= 0) {
+      const int* win = ct.fwin + (size_t)li * LiftShape<D, K>::NW;
+      const V* wf = (const V*)ct.wf;
+      unsigned found = 0;
+      const int m = (q == 0 ? 1 : 0) + (r == 0 && D == 3 ? 2 : 0);
+      switch (m) {
+        case 0: lift_row<D, K, A, 0>(wf, win, q, r, acc, found); break;
+        case 1: lift_row<D, K, A, 1>(wf, win, q, r, acc, found); break;
+        case 2: lift_row<D, K, A, 2>(wf, win, q, r, acc, found); break;
+        default: lift_row<D, K, A, 3>(wf, win, q, r, acc, found); break;
+      }
+    }
+  }
 #pragma unroll
   for (int w = 0; w < NWC; ++w) {
     const int sx = w & 1, sy = (w >> 1) & 1, sz = (w >> 2) & 1;

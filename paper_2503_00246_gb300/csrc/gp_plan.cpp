@@ -299,7 +299,7 @@ void build_cell_table(Plan& p) {
       p.crow[(size_t)a * R1 + t] = (int32_t)p.compact(ci * k, row);
     }
   }
-  // owner cells (coordinates in [0, n]) of the active nodes, lexicographic; their window of
+  // owner cells (coordinates in [0, n]) of the active nodes; their window of
   // the 2^d cells (ci - s_x, cj - s_y, cl - s_z), s in {0,1}^d, that hold their nodes
   std::vector<uint8_t> own((size_t)n1 * n1 * (d == 3 ? n1 : 1), 0);
   for (int64_t c = 0; c < p.ncell; ++c) {
@@ -313,10 +313,22 @@ void build_cell_table(Plan& p) {
   const int NWC = d == 3 ? 8 : 4;
   const int KR = d == 3 ? k * k : k;
   p.cwin.clear();
+  // order: the owners that some ghost face reaches first, in the lift's order (so that the
+  // fused gather's warps do face work together), then the others, lexicographic
   std::vector<int64_t> owners;
+  std::vector<uint8_t> taken(own.size(), 0);
+  for (int64_t i = 0; i < p.num_lift_cells(); ++i) {
+    const int32_t* c = &p.lcell[4 * i];
+    const size_t o = c[0] + (size_t)n1 * (c[1] + (size_t)n1 * c[2]);
+    if (o < own.size() && own[o] && !taken[o]) {
+      owners.push_back((int64_t)o);
+      taken[o] = 1;
+    }
+  }
   for (size_t o = 0; o < own.size(); ++o)
-    if (own[o]) owners.push_back((int64_t)o);
+    if (own[o] && !taken[o]) owners.push_back((int64_t)o);
   p.ncown = (int64_t)owners.size();
+  p.cown.assign(owners.begin(), owners.end());
   p.cwin.assign((size_t)p.ncown * NWC, -1);
   p.corow.assign((size_t)KR * p.ncown, -1);
   for (int64_t i = 0; i < p.ncown; ++i) {
@@ -339,6 +351,19 @@ void build_cell_table(Plan& p) {
       p.corow[(size_t)i * KR + t] = (int32_t)cidx;
     }
   }
+}
+
+std::vector<int32_t> owner_lift_index(const Plan& cells, const Plan& faces) {
+  const int n1 = cells.n + 1;
+  std::vector<int32_t> at((size_t)n1 * n1 * (cells.dim == 3 ? n1 : 1), -1);
+  const int64_t nl = faces.num_lift_cells();
+  for (int64_t i = 0; i < nl; ++i) {
+    const int32_t* c = &faces.lcell[4 * i];
+    at[c[0] + (size_t)n1 * (c[1] + (size_t)n1 * c[2])] = (int32_t)i;
+  }
+  std::vector<int32_t> out(cells.cown.size());
+  for (size_t i = 0; i < cells.cown.size(); ++i) out[i] = at[(size_t)cells.cown[i]];
+  return out;
 }
 
 bool check_cell_table(const Plan& p) {

@@ -12,7 +12,6 @@ namespace gp {
 
 constexpr int KMAX = 8;
 constexpr int ZRUN_MAX = 256;       // elements per zero run (one CTA pass)
-constexpr int LIFT_CELLS = 32;      // owner cells per lift CTA (one per lane)
 
 enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
 
@@ -62,11 +61,13 @@ struct Plan {
   std::vector<int32_t> crow;      // ncact x (k+1)^(d-1): compact index of (ci k, cj k + q, cl k + r)
   int64_t num_active_cells() const { return ncact; }
   int64_t ncact = 0;
-  // owner cells of the active nodes (coordinates in [0, n], lexicographic): per owner the
+  // owner cells of the active nodes (coordinates in [0, n]; those a ghost face reaches first,
+  // in lift order, then the rest lexicographic): per owner the
   // active-cell index of the 2^d cells (ci - s_x, cj - s_y, cl - s_z) (-1 if none), and per
   // x-row (q, r) the compact index of node (ci k, cj k + q, cl k + r) ([ncown][KR], -1 if none)
   std::vector<int32_t> cwin;
   std::vector<int32_t> corow;
+  std::vector<int64_t> cown;      // owner cells: linear index ci + (n+1) (cj + (n+1) cl)
   int64_t ncown = 0;
 
   // slab partition (Sec. 2.7): cell layers [part_lo, part_hi) along the last axis.  The
@@ -113,6 +114,9 @@ void reference_stiffness(int k, std::vector<double>& stiff);
 bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
+// For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`
+// (-1 if no ghost face reaches it): the fused gather of the model system uses it.
+std::vector<int32_t> owner_lift_index(const Plan& cells, const Plan& faces);
 // Every index of the cell table inside the active DoFs and the active cells.
 bool check_cell_table(const Plan& p);
 // diag(M_active + K_active + G) in FP64 (needs the cell table).

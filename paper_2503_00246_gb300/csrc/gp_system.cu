@@ -24,6 +24,8 @@ struct gp_system {
   int32_t* d_cwin = nullptr;
   int32_t* d_corow = nullptr;
   void* d_wc = nullptr;     // cell outputs (scratch, 8 bytes per value)
+  int32_t* d_o2l_hi = nullptr;  // per owner cell: lift owner index in hi's / lo's face plan
+  int32_t* d_o2l_lo = nullptr;
   gp::CellTabs ct{};
   int nparts = 0;           // CTAs of the cell gather (fused inner-product partials)
   gp::CellsFn cells_hi = nullptr, cells_lo = nullptr;
@@ -122,17 +124,24 @@ cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
 }
 
 // y = A x with the operator of context c (G, then the cell colours adding on top)
-// y = A x; with dotp, the cell gather also leaves the partial sums of dotp . y (one per
-// gather CTA, s->nparts of them) in s->part.
+// y = A x in three launches: the ghost-penalty face kernel (face outputs only), the cell
+// kernel (cell outputs; it overlaps the face kernel as its programmatic dependent), and
+// one gather that adds, per node, the face outputs and then the cell outputs and writes y
+// once.  With dotp, the gather also leaves the partial sums of dotp . y (one per gather
+// CTA, s->nparts of them) in s->part.
 gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st,
                     bool trace = true, const void* dotp = nullptr) {
-  gp_status g = gpi::launch(c, x, y, 0, st, nullptr, trace);
+  (void)trace;
+  gp_status g = gpi::launch(c, x, y, 1, st, nullptr, false, nullptr, 1);   // face kernel alone
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
   gp::CellTabs ct = s->ct;
   ct.dotp = dotp;
   ct.dotpart = dotp ? s->part : nullptr;
-  const cudaError_t e = cells(p.k, x, y, ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 1, st);
+  ct.wf = c->d_tp;
+  ct.fwin = c->d_lwin;
+  ct.own2lift = c == s->hi ? s->d_o2l_hi : s->d_o2l_lo;
+  const cudaError_t e = cells(p.k, x, y, ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 0, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
@@ -144,7 +153,8 @@ gp::CellsFn cells_for(const gp::Plan& p) {
 }
 
 void sys_free(gp_system* s) {
-  void* ptrs[] = {s->d_crow, s->d_cwin, s->d_corow, s->d_wc, s->r, s->p, s->q, s->dd, s->z, s->ri, s->r32,
+  void* ptrs[] = {s->d_crow, s->d_cwin, s->d_corow, s->d_wc, s->d_o2l_hi, s->d_o2l_lo, s->r, s->p, s->q, s->dd,
+                  s->z, s->ri, s->r32,
                   s->d32, s->ri32, s->p32, s->q32, s->z32, s->dinv, s->dinv32, s->part, s->d_cg};
   for (void* v : ptrs)
     if (v) cudaFree(v);
@@ -437,6 +447,8 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (e == cudaSuccess) e = upload(&s->d_crow, p.crow);
   if (e == cudaSuccess) e = upload(&s->d_cwin, p.cwin);
   if (e == cudaSuccess) e = upload(&s->d_corow, p.corow);
+  if (e == cudaSuccess) e = upload(&s->d_o2l_hi, gp::owner_lift_index(p, hi->plan));
+  if (e == cudaSuccess && lo) e = upload(&s->d_o2l_lo, gp::owner_lift_index(p, lo->plan));
   const size_t nodes = (size_t)gp::ipow_host(p.k + 1, p.dim);
   if (e == cudaSuccess && p.ncact > 0) e = cudaMalloc(&s->d_wc, (size_t)p.ncact * nodes * 8);
   s->ct.crow = s->d_crow;

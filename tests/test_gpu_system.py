@@ -80,8 +80,13 @@ def test_defect_correction_and_cg(gplib, cuda, hi):
     bd = cuda.tensor(b, dtype=cuda.float64, device="cuda")
     u_dc = cuda.zeros_like(bd)
     u_cg = cuda.zeros_like(bd)
-    st_dc = gplib.gp_system_solve(sysm, bd, u_dc, rtol=1e-10, inner_rtol=1e-4, mode=0)
-    st_cg = gplib.gp_system_solve(sysm, bd, u_cg, rtol=1e-10, mode=1)
+    # The outer residual b - A u is evaluated with the high-precision operator, so its
+    # rounding sets the attainable residual: about 2^-48 * |A| |u| / |b| for float-float,
+    # which is near 1e-10 on this problem (32 times the FP64 floor); float-float solves to
+    # 1e-9, FP64 to 1e-10.
+    rtol = 1e-10 if hi == 0 else 1e-9
+    st_dc = gplib.gp_system_solve(sysm, bd, u_dc, rtol=rtol, inner_rtol=1e-4, mode=0)
+    st_cg = gplib.gp_system_solve(sysm, bd, u_cg, rtol=rtol, mode=1)
     # without the preconditioner: more iterations to the same residual.  Compared at 1e-9:
     # the attainable residual of unpreconditioned CG is the operator's rounding (about
     # 1e-14 relative for float-float) times cond(A), which is near 1e-10 here.
@@ -91,15 +96,15 @@ def test_defect_correction_and_cg(gplib, cuda, hi):
     assert st_j9["rel_residual"] <= 1e-9 and st_n9["rel_residual"] <= 1e-9
     assert st_n9["inner"] > st_j9["inner"]
     for st in (st_dc, st_cg):
-        assert st["rel_residual"] <= 1e-10, st
+        assert st["rel_residual"] <= rtol, st
     assert st_dc["outer"] >= 2 and st_dc["lo_applies"] > 0
     for u in (u_dc, u_cg):
         un = u.cpu().numpy()
-        assert np.linalg.norm(b - A(un)) <= 1e-9 * np.linalg.norm(b)
+        assert np.linalg.norm(b - A(un)) <= 10 * rtol * np.linalg.norm(b)
     a, c = u_dc.cpu().numpy(), u_cg.cpu().numpy()
-    assert np.linalg.norm(a - c) <= 1e-7 * np.linalg.norm(c)
+    assert np.linalg.norm(a - c) <= 1e3 * rtol * np.linalg.norm(c)
     u2 = cuda.zeros_like(bd)
-    gplib.gp_system_solve(sysm, bd, u2, rtol=1e-10, inner_rtol=1e-4, mode=0)
+    gplib.gp_system_solve(sysm, bd, u2, rtol=rtol, inner_rtol=1e-4, mode=0)
     assert cuda.equal(u2, u_dc)            # fixed reduction order: bitwise reproducible
     sysm.close()
 
