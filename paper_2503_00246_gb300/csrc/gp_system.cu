@@ -123,15 +123,13 @@ cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-// y = A x with the operator of context c (G, then the cell colours adding on top)
-// y = A x in three launches: the ghost-penalty face kernel (face outputs only), the cell
-// kernel (cell outputs; it overlaps the face kernel as its programmatic dependent), and
-// one gather that adds, per node, the face outputs and then the cell outputs and writes y
-// once.  With dotp, the gather also leaves the partial sums of dotp . y (one per gather
+// y = A x with the operator of context c in three launches: the ghost-penalty face
+// kernel (face outputs only), the cell kernel (cell outputs; it overlaps the face kernel
+// as its programmatic dependent), and one gather that adds, per node, the face outputs
+// and then the cell outputs and writes y once.  With dotp, the gather also leaves the partial sums of dotp . y (one per gather
 // CTA, s->nparts of them) in s->part.
 gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st,
-                    bool trace = true, const void* dotp = nullptr) {
-  (void)trace;
+                    const void* dotp = nullptr) {
   gp_status g = gpi::launch(c, x, y, 1, st, nullptr, false, nullptr, 1);   // face kernel alone
   if (g != GP_OK) return g;
   const gp::Plan& p = c->plan;
@@ -367,7 +365,7 @@ gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* 
   SYS_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   gp_status g = GP_OK;
   for (int i = 0; i < kCgBlock && g == GP_OK; ++i) {
-    g = sys_apply(s, c, cells, p, q, s->st, false, p);   // q = A p and the partial sums of p . q
+    g = sys_apply(s, c, cells, p, q, s->st, p);   // q = A p and the partial sums of p . q
     if (g != GP_OK) break;
     cg_alpha<<<1, kThreads, 0, s->st>>>(s->part, s->nparts, sc);
     cg_update<T><<<kDotBlocks, kThreads, 0, s->st>>>(d, r, p, q, z, dinv, sc, n, s->part);
