@@ -424,8 +424,11 @@ def run_cg(args):
                        "k=4, c_j = 0.5/(j!)^2, (M_active + K_active + G) u = b, b ~ U[-1,1]",
            "n_active_dofs": hi.n_active, "ghost_faces": hi.n_faces, "setup_s": setup}
     for name, mode in (("defect_correction_fp32_inner", 0), ("pcg_fp64", 1)):
+        torch.cuda.nvtx.range_push(name)        # ncu --nvtx --nvtx-include "<name>/" picks one solver
         st = gp.gp_system_solve(sysm, b, u, rtol=1e-10, inner_rtol=args.inner_rtol, mode=mode,
-                                max_inner=args.max_inner)
+                                max_outer=args.max_outer, max_inner=args.max_inner)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         out[name] = st
     print(json.dumps(out), flush=True)
 
@@ -741,6 +744,7 @@ def main():
     ap.add_argument("--sweep-check-kmax", type=int, default=5)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--max-inner", type=int, default=200000)
+    ap.add_argument("--max-outer", type=int, default=50)
     ap.add_argument("--cg-n", type=int, default=32)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)

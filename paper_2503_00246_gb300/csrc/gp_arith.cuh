@@ -149,6 +149,36 @@ __device__ __forceinline__ void sum_add(Sum<ff64>& d, ff64 v) {
   d.c = __fadd_rn(__fadd_rn(d.c, v.lo), err);
 }
 
+// ------------------------------------------------ solver inner products --
+// IoDot<T> accumulates an inner product of two solver vectors of element type T.
+// FP64 vectors use FP64 fused multiply-adds.  FP32 vectors use the compensated
+// dot product above on the exact products of float pairs (product p and its
+// rounding error fma(a, b, -p)), so that no FP64 instruction runs per element
+// (GB300 issues 2 FP64 FMAs per clock per SM against 128 FP32); value() converts
+// the (sum, error) pair to double once.
+template <typename T>
+struct IoDot;
+template <>
+struct IoDot<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct IoDot<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);                       // two-sum of s + p
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, e), err);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // --------------------------------------------------------- memory <-> V --
 __device__ __forceinline__ float from_io(float x, float*) { return x; }
 __device__ __forceinline__ double from_io(double x, double*) { return x; }

@@ -184,15 +184,14 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
 // (ci - s_x, cj - s_y, cl - s_z) that hold them (s_y = 1 only for q = 0, s_z = 1 only for
 // r = 0, s_x = 1 only for p = 0), in the order w = s_x + 2 s_y + 4 s_z.
 template <int D, int K, class A>
-__device__ __forceinline__ double gather_row(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y,
-                                             const int add, const CellTabs& ct, const int own, const int t,
-                                             const int base) {
+__device__ __forceinline__ void gather_row(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y,
+                                           const int add, const CellTabs& ct, const int own, const int t,
+                                           const int base, IoDot<typename A::IO>& dot) {
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
   constexpr int K1 = S::K1, NODES = S::NODES, NWC = S::NWC;
   const int q = t % K, r = (D == 3) ? t / K : 0;
-  double dot = 0.0;
   Sum<V> acc[K];
 #pragma unroll
   for (int p = 0; p < K; ++p) acc[p] = sum_zero<V>();
@@ -213,21 +212,51 @@ __device__ __forceinline__ double gather_row(const typename A::V* __restrict__ w
       }
     }
   }
+  // the owner's window (2^d cell indices, one vector load), then per group of four
+  // windows (s_z fixed) every cell-output load of the row before the first add; the adds
+  // run in the window order w = s_x + 2 s_y + 4 s_z
+  int cw[NWC];
+  {
+    const int4* wv = reinterpret_cast<const int4*>(ct.cwin + (size_t)own * NWC);
 #pragma unroll
-  for (int w = 0; w < NWC; ++w) {
-    const int sx = w & 1, sy = (w >> 1) & 1, sz = (w >> 2) & 1;
-    if ((sy && q != 0) || (sz && r != 0)) continue;
-    const int cidx = __ldg(ct.cwin + (size_t)own * NWC + w);
-    if (cidx < 0) continue;
-    const int ly = q + sy * K, lz = r + sz * K;
-    const V* src = wc + (size_t)cidx * NODES + K1 * (ly + (D == 3 ? K1 * lz : 0));
-    if (sx == 0) {
+    for (int i = 0; i < NWC / 4; ++i) {
+      const int4 v4 = __ldg(wv + i);
+      cw[4 * i] = v4.x;
+      cw[4 * i + 1] = v4.y;
+      cw[4 * i + 2] = v4.z;
+      cw[4 * i + 3] = v4.w;
+    }
+  }
 #pragma unroll
-      for (int p = 0; p < K; ++p) sum_add(acc[p], src[p]);
-      any0 = anyp = true;
-    } else {
-      sum_add(acc[0], src[K]);
-      any0 = true;
+  for (int sz = 0; sz < (D == 3 ? 2 : 1); ++sz) {
+    if (sz && r != 0) break;
+    V v0[2][K], v1[2];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int w = u + 4 * sz, sx = u & 1, sy = u >> 1;
+      ok[u] = cw[w] >= 0 && !(sy && q != 0);
+      // in-bounds address even where the window is unused (cell 0, row 0)
+      const int ly = ok[u] ? q + sy * K : 0, lz = ok[u] ? r + sz * K : 0;
+      const V* src = wc + (size_t)(ok[u] ? cw[w] : 0) * NODES + K1 * (ly + (D == 3 ? K1 * lz : 0));
+      if (sx == 0) {
+#pragma unroll
+        for (int p = 0; p < K; ++p) v0[sy][p] = ok[u] ? src[p] : vzero<V>();
+      } else {
+        v1[sy] = ok[u] ? src[K] : vzero<V>();
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!ok[u]) continue;
+      if ((u & 1) == 0) {
+#pragma unroll
+        for (int p = 0; p < K; ++p) sum_add(acc[p], v0[u >> 1][p]);
+        any0 = anyp = true;
+      } else {
+        sum_add(acc[0], v1[u >> 1]);
+        any0 = true;
+      }
     }
   }
 #pragma unroll
@@ -239,9 +268,62 @@ __device__ __forceinline__ double gather_row(const typename A::V* __restrict__ w
     const V outv = add ? vadd(from_io(y[idx], (V*)nullptr), sv) : sv;
     const IO o = to_io(outv, (IO*)nullptr);
     y[idx] = o;
-    if (ct.dotp) dot = fma((double)((const IO*)ct.dotp)[idx], (double)o, dot);
+    if (ct.dotp) dot.add(((const IO*)ct.dotp)[idx], o);
   }
-  return dot;
+}
+
+// A gather CTA takes GATHER_THREADS / KR whole owner cells.  Its threads are ordered
+// by row type (q == 0, r == 0) first, so that a warp's rows take the same path through
+// the row code (the candidate ghost faces and cell windows depend on the type): 3D
+// rows (0, 0), then (0, r > 0), (q > 0, 0), (q > 0, r > 0); 2D rows q = 0, then q > 0.
+// Within a type, owner-major.
+__host__ __device__ constexpr int gather_owners_per_cta(int dim, int k) {
+  return (dim == 3 ? k * k : k) >= GATHER_THREADS ? 1 : GATHER_THREADS / (dim == 3 ? k * k : k);
+}
+inline int64_t gather_ctas(int dim, int k, int64_t ncown) {
+  const int opc = gather_owners_per_cta(dim, k);
+  return (ncown + opc - 1) / opc;
+}
+
+template <int D, int K>
+__device__ __forceinline__ bool gather_slot(const int u, int& o, int& q, int& r) {
+  constexpr int OPC = gather_owners_per_cta(D, K);
+  constexpr int C1 = K - 1;                 // rows per owner with exactly one of q, r zero (each)
+  if (u >= OPC * CellShape<D, K>::KR) return false;
+  if (u < OPC) {
+    o = u;
+    q = r = 0;
+    return true;
+  }
+  if constexpr (K == 1) {
+    return false;
+  } else if constexpr (D == 2) {
+    const int v = u - OPC;
+    o = v / C1;
+    q = 1 + (v - o * C1);
+    r = 0;
+  } else {
+    int v = u - OPC;
+    if (v < OPC * C1) {
+      o = v / C1;
+      q = 0;
+      r = 1 + (v - o * C1);
+      return true;
+    }
+    v -= OPC * C1;
+    if (v < OPC * C1) {
+      o = v / C1;
+      q = 1 + (v - o * C1);
+      r = 0;
+      return true;
+    }
+    v -= OPC * C1;
+    o = v / (C1 * C1);
+    const int j = v - o * C1 * C1;
+    q = 1 + j % C1;
+    r = 1 + j / C1;
+  }
+  return true;
 }
 
 template <int D, int K, class A>
@@ -249,16 +331,18 @@ __global__ void __launch_bounds__(GATHER_THREADS)
 cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y, const int add, const CellTabs ct) {
   using S = CellShape<D, K>;
   constexpr int KR = S::KR;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = g < ct.ncown * KR;
-  const int own = live ? g / KR : 0, t = live ? g - own * KR : 0;
-  const int base = live ? __ldg(ct.corow + (size_t)g) : -1;            // = [own][t]
+  int o = 0, q = 0, r = 0;
+  const bool slot = gather_slot<D, K>((int)threadIdx.x, o, q, r);
+  const int own = (int)blockIdx.x * gather_owners_per_cta(D, K) + o;
+  const bool live = slot && own < ct.ncown;
+  const int t = q + K * r;
+  const int base = live ? __ldg(ct.corow + (size_t)own * KR + t) : -1;
   asm volatile("griddepcontrol.wait;" ::: "memory");   // cell outputs and y are complete
-  double dot = 0.0;
-  if (base >= 0) dot = gather_row<D, K, A>(wc, y, add, ct, own, t, base);
+  IoDot<typename A::IO> dot;
+  if (base >= 0) gather_row<D, K, A>(wc, y, add, ct, own, t, base, dot);
   if (ct.dotpart) {
     __shared__ double sh[GATHER_THREADS];
-    sh[threadIdx.x] = dot;
+    sh[threadIdx.x] = dot.value();
     __syncthreads();
     for (int o = GATHER_THREADS / 2; o > 0; o >>= 1) {
       if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
@@ -271,8 +355,7 @@ cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y
 // CTAs of the gather (the number of fused inner-product partials)
 template <int D, int K>
 inline int gather_blocks(const CellTabs& ct) {
-  const int64_t rows = (int64_t)ct.ncown * CellShape<D, K>::KR;
-  return (int)((rows + GATHER_THREADS - 1) / GATHER_THREADS);
+  return (int)gather_ctas(D, K, ct.ncown);
 }
 
 // y (+)= (wm M_active + ws K_active) x: the cell kernel, then the gather (add = 1: onto y).

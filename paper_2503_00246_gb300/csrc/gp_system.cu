@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "gp_arith.cuh"
 #include "gp_internal.h"
 
 struct gp_system {
@@ -28,6 +29,8 @@ struct gp_system {
   int32_t* d_o2l_lo = nullptr;
   gp::CellTabs ct{};
   int nparts = 0;           // CTAs of the cell gather (fused inner-product partials)
+  int nblk = 0;             // CTAs of the vector reductions: 4 per SM
+  int nvec = 0;             // CTAs of the element-wise vector kernels: 8 per SM
   gp::CellsFn cells_hi = nullptr, cells_lo = nullptr;
   // solver vectors
   double *r = nullptr, *p = nullptr, *q = nullptr, *dd = nullptr, *z = nullptr, *ri = nullptr;
@@ -47,18 +50,18 @@ namespace {
 using gpi::DeviceGuard;
 using gpi::fail;
 
-constexpr int kDotBlocks = 1024;
+constexpr int kDotPerSm = 4;   // reduction CTAs per SM (the grid is a multiple of the SM count)
 constexpr int kThreads = 256;
-constexpr int kVecBlocks = 2048;
+constexpr int kVecPerSm = 8;   // CTAs per SM of the element-wise vector kernels
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dot_partial(const T* __restrict__ a, const T* __restrict__ b,
                                                         int64_t n, double* __restrict__ part) {
   __shared__ double sh[kThreads];
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads)
-    s = fma((double)a[i], (double)b[i], s);
-  sh[threadIdx.x] = s;
+  gp::IoDot<T> acc;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    acc.add(a[i], b[i]);
+  sh[threadIdx.x] = acc.value();
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
@@ -67,10 +70,11 @@ __global__ void __launch_bounds__(kThreads) dot_partial(const T* __restrict__ a,
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void __launch_bounds__(kThreads) dot_final(const double* __restrict__ part, double* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads) dot_final(const double* __restrict__ part, const int nblk,
+                                                      double* __restrict__ out) {
   __shared__ double sh[kThreads];
   double s = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) s += part[i];
+  for (int i = threadIdx.x; i < nblk; i += kThreads) s += part[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
@@ -114,10 +118,10 @@ __global__ void add64_k(double* __restrict__ u, const double* __restrict__ d, in
 
 template <typename T>
 cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
-  dot_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(a, b, s->n, s->part);
-  dot_final<<<1, kThreads, 0, s->st>>>(s->part, s->part + 2 * kDotBlocks);
+  dot_partial<T><<<s->nblk, kThreads, 0, s->st>>>(a, b, s->n, s->part);
+  dot_final<<<1, kThreads, 0, s->st>>>(s->part, s->nblk, s->part + 2 * s->nblk);
   cudaError_t e =
-      cudaMemcpyAsync(s->h_res, s->part + 2 * kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->st);
+      cudaMemcpyAsync(s->h_res, s->part + 2 * s->nblk, sizeof(double), cudaMemcpyDeviceToHost, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   *out = *s->h_res;
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -184,13 +188,13 @@ struct CgScalars {
 
 constexpr int kCgBlock = 16;
 
-__global__ void __launch_bounds__(kThreads) cg_init_final(const double* __restrict__ part, CgScalars* sc,
-                                                          double tol, int maxit) {
+__global__ void __launch_bounds__(kThreads) cg_init_final(const double* __restrict__ part, const int nblk,
+                                                          CgScalars* sc, double tol, int maxit) {
   __shared__ double sa[kThreads], sb[kThreads];
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) {
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
     a += part[i];
-    b += part[kDotBlocks + i];
+    b += part[nblk + i];
   }
   sa[threadIdx.x] = a;
   sb[threadIdx.x] = b;
@@ -238,30 +242,20 @@ __global__ void __launch_bounds__(kThreads) cg_alpha(const double* __restrict__ 
   }
 }
 
-// d += alpha p, r -= alpha q, z = dinv r (when dinv), and the partial sums of r.r, r.z
+// Four consecutive vector elements, loaded and stored as one 16-byte (FP32) or
+// 32-byte (FP64) access.  The solver's vectors are its own allocations (256-byte
+// aligned), so the n / 4 leading quads are aligned; the n % 4 tail is scalar.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) cg_update(T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
-                                                      const T* __restrict__ q, T* __restrict__ z,
-                                                      const T* __restrict__ dinv, const CgScalars* __restrict__ sc,
-                                                      int64_t n, double* __restrict__ part) {
-  if (sc->done) return;
-  const T a = (T)sc->alpha;
+struct alignas(4 * sizeof(T)) Quad {
+  T v[4];
+};
+
+// the two block sums of a thread's (a, b) partials: a into part[blockIdx.x], b into
+// part[gridDim.x + blockIdx.x] (fixed tree)
+__device__ __forceinline__ void block_sums2(double a, double b, double* __restrict__ part) {
   __shared__ double sa[kThreads], sb[kThreads];
-  double rr = 0.0, rz = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
-    d[i] = fma(a, p[i], d[i]);
-    const T ri = fma(-a, q[i], r[i]);
-    r[i] = ri;
-    T zi = ri;
-    if (dinv) {
-      zi = dinv[i] * ri;
-      z[i] = zi;
-    }
-    rr = fma((double)ri, (double)ri, rr);
-    rz = fma((double)ri, (double)zi, rz);
-  }
-  sa[threadIdx.x] = rr;
-  sb[threadIdx.x] = rz;
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
@@ -272,21 +266,69 @@ __global__ void __launch_bounds__(kThreads) cg_update(T* __restrict__ d, T* __re
   }
   if (threadIdx.x == 0) {
     part[blockIdx.x] = sa[0];
-    part[kDotBlocks + blockIdx.x] = sb[0];
+    part[gridDim.x + blockIdx.x] = sb[0];
   }
 }
 
+// d += alpha p, r -= alpha q, z = dinv r (when dinv), and the partial sums of r.r, r.z
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cg_update(T* __restrict__ d, T* __restrict__ r, const T* __restrict__ p,
+                                                      const T* __restrict__ q, T* __restrict__ z,
+                                                      const T* __restrict__ dinv, const CgScalars* __restrict__ sc,
+                                                      int64_t n, double* __restrict__ part) {
+  if (sc->done) return;
+  const T a = (T)sc->alpha;
+  gp::IoDot<T> rr, rz;
+  const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x, stride = (int64_t)gridDim.x * kThreads;
+  const int64_t n4 = n >> 2;
+  for (int64_t j = tid; j < n4; j += stride) {
+    Quad<T> dq = reinterpret_cast<const Quad<T>*>(d)[j];
+    Quad<T> rq = reinterpret_cast<const Quad<T>*>(r)[j];
+    const Quad<T> pq = reinterpret_cast<const Quad<T>*>(p)[j];
+    const Quad<T> qq = reinterpret_cast<const Quad<T>*>(q)[j];
+    Quad<T> zq;
+    if (dinv) zq = reinterpret_cast<const Quad<T>*>(dinv)[j];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      dq.v[e] = fma(a, pq.v[e], dq.v[e]);
+      const T ri = fma(-a, qq.v[e], rq.v[e]);
+      rq.v[e] = ri;
+      const T zi = dinv ? zq.v[e] * ri : ri;
+      zq.v[e] = zi;
+      rr.add(ri, ri);
+      rz.add(ri, zi);
+    }
+    reinterpret_cast<Quad<T>*>(d)[j] = dq;
+    reinterpret_cast<Quad<T>*>(r)[j] = rq;
+    if (dinv) reinterpret_cast<Quad<T>*>(z)[j] = zq;
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
+    d[i] = fma(a, p[i], d[i]);
+    const T ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    T zi = ri;
+    if (dinv) {
+      zi = dinv[i] * ri;
+      z[i] = zi;
+    }
+    rr.add(ri, ri);
+    rz.add(ri, zi);
+  }
+  block_sums2(rr.value(), rz.value(), part);
+}
+
 // beta = rz' / rz, the convergence test and the iteration count
-__global__ void __launch_bounds__(kThreads) cg_beta(const double* __restrict__ part, CgScalars* sc) {
+__global__ void __launch_bounds__(kThreads) cg_beta(const double* __restrict__ part, const int nblk,
+                                                    CgScalars* sc) {
   __shared__ double sa[kThreads], sb[kThreads];
   __shared__ int done;
   if (threadIdx.x == 0) done = sc->done;
   __syncthreads();
   if (done) return;
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += kThreads) {
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
     a += part[i];
-    b += part[kDotBlocks + i];
+    b += part[nblk + i];
   }
   sa[threadIdx.x] = a;
   sb[threadIdx.x] = b;
@@ -310,37 +352,33 @@ __global__ void __launch_bounds__(kThreads) cg_beta(const double* __restrict__ p
 
 // p = z + beta p
 template <typename T>
-__global__ void cg_direction(T* __restrict__ p, const T* __restrict__ z, const CgScalars* __restrict__ sc, int64_t n) {
+__global__ void __launch_bounds__(kThreads, kVecPerSm)
+cg_direction(T* __restrict__ p, const T* __restrict__ z, const CgScalars* __restrict__ sc, int64_t n) {
   if (sc->done) return;
   const T bt = (T)sc->beta;
-  GRID_STRIDE(i, n) p[i] = fma(bt, p[i], z[i]);
+  const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x, stride = (int64_t)gridDim.x * kThreads;
+  const int64_t n4 = n >> 2;
+  for (int64_t j = tid; j < n4; j += stride) {
+    Quad<T> pq = reinterpret_cast<const Quad<T>*>(p)[j];
+    const Quad<T> zq = reinterpret_cast<const Quad<T>*>(z)[j];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pq.v[e] = fma(bt, pq.v[e], zq.v[e]);
+    reinterpret_cast<Quad<T>*>(p)[j] = pq;
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += stride) p[i] = fma(bt, p[i], z[i]);
 }
 
-// the partial sums of a.b and c.e (kDotBlocks each) into part
+// the partial sums of a.b and c.e (one per CTA each) into part
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dot2_partial(const T* __restrict__ a, const T* __restrict__ b,
                                                          const T* __restrict__ c, const T* __restrict__ e,
                                                          int64_t n, double* __restrict__ part) {
-  __shared__ double sa[kThreads], sb[kThreads];
-  double x = 0.0, w = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
-    x = fma((double)a[i], (double)b[i], x);
-    w = fma((double)c[i], (double)e[i], w);
+  gp::IoDot<T> x, w;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    x.add(a[i], b[i]);
+    w.add(c[i], e[i]);
   }
-  sa[threadIdx.x] = x;
-  sb[threadIdx.x] = w;
-  __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      sa[threadIdx.x] += sa[threadIdx.x + o];
-      sb[threadIdx.x] += sb[threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = sa[0];
-    part[kDotBlocks + blockIdx.x] = sb[0];
-  }
+  block_sums2(x.value(), w.value(), part);
 }
 
 // Preconditioned CG (Jacobi when dinv is given) on A d = rhs from d = 0, until
@@ -354,10 +392,10 @@ gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* 
   T* zz = dinv ? z : r;
   SYS_CUDA(cudaMemsetAsync(d, 0, n * sizeof(T), s->st));
   SYS_CUDA(cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
-  if (dinv) scale_k<T><<<kVecBlocks, kThreads, 0, s->st>>>(z, dinv, r, n);
+  if (dinv) scale_k<T><<<s->nvec, kThreads, 0, s->st>>>(z, dinv, r, n);
   SYS_CUDA(cudaMemcpyAsync(p, zz, n * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
-  dot2_partial<T><<<kDotBlocks, kThreads, 0, s->st>>>(r, r, r, zz, n, s->part);
-  cg_init_final<<<1, kThreads, 0, s->st>>>(s->part, sc, tol, maxit);
+  dot2_partial<T><<<s->nblk, kThreads, 0, s->st>>>(r, r, r, zz, n, s->part);
+  cg_init_final<<<1, kThreads, 0, s->st>>>(s->part, s->nblk, sc, tol, maxit);
   SYS_CUDA(cudaGetLastError());
   // one block of iterations, captured once and replayed
   cudaGraph_t graph = nullptr;
@@ -368,9 +406,9 @@ gp_status cg(gp_system* s, gp_ctx* c, gp::CellsFn cells, const T* rhs, T* d, T* 
     g = sys_apply(s, c, cells, p, q, s->st, p);   // q = A p and the partial sums of p . q
     if (g != GP_OK) break;
     cg_alpha<<<1, kThreads, 0, s->st>>>(s->part, s->nparts, sc);
-    cg_update<T><<<kDotBlocks, kThreads, 0, s->st>>>(d, r, p, q, z, dinv, sc, n, s->part);
-    cg_beta<<<1, kThreads, 0, s->st>>>(s->part, sc);
-    cg_direction<T><<<kVecBlocks, kThreads, 0, s->st>>>(p, zz, sc, n);
+    cg_update<T><<<s->nblk, kThreads, 0, s->st>>>(d, r, p, q, z, dinv, sc, n, s->part);
+    cg_beta<<<1, kThreads, 0, s->st>>>(s->part, s->nblk, sc);
+    cg_direction<T><<<s->nvec, kThreads, 0, s->st>>>(p, zz, sc, n);
   }
   const cudaError_t ec = cudaStreamEndCapture(s->st, &graph);
   if (g != GP_OK) {
@@ -436,6 +474,10 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
     return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
   };
   cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  s->nblk = kDotPerSm * std::max(sms, 1);
+  s->nvec = kVecPerSm * std::max(sms, 1);
   auto upload = [](int32_t** dst, const std::vector<int32_t>& v) -> cudaError_t {
     if (v.empty()) return cudaSuccess;
     cudaError_t r = cudaMalloc((void**)dst, v.size() * sizeof(int32_t));
@@ -484,9 +526,9 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->ri32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->p32, n4);
   if (e == cudaSuccess && lo) e = cudaMalloc(&s->q32, n4);
-  s->nparts = (int)(((int64_t)p.ncown * gp::ipow_host(p.k, p.dim - 1) + gp::GATHER_THREADS - 1) / gp::GATHER_THREADS);
+  s->nparts = (int)gp::gather_ctas(p.dim, p.k, p.ncown);
   if (e == cudaSuccess)
-    e = cudaMalloc(&s->part, (size_t)std::max<int64_t>(2 * kDotBlocks + 1, s->nparts) * sizeof(double));
+    e = cudaMalloc(&s->part, (size_t)std::max<int64_t>(2 * s->nblk + 1, s->nparts) * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_cg, sizeof(CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_cg, sizeof(CgScalars));
@@ -547,25 +589,25 @@ gp_status gp_system_solve(gp_system* s, const double* b, double* u, const gp_sol
     if (rn <= o->rtol * nb || rr == 0.0) break;
     int it = 0, applies = 0;
     if (o->mode == 0) {
-      to32_k<<<kVecBlocks, kThreads, 0, s->st>>>(s->r32, s->r, n);
+      to32_k<<<s->nvec, kThreads, 0, s->st>>>(s->r32, s->r, n);
       g = cg<float>(s, s->lo, s->cells_lo, s->r32, s->d32, s->ri32, s->p32, s->q32, s->z32,
                     jac ? s->dinv32 : nullptr, o->inner_rtol, o->max_inner, &it, &applies);
       if (g != GP_OK) return g;
       stats->lo_applies += applies;
-      add32_k<<<kVecBlocks, kThreads, 0, s->st>>>(u, s->d32, n);
+      add32_k<<<s->nvec, kThreads, 0, s->st>>>(u, s->d32, n);
     } else {
       const double tol = std::max(0.5 * o->rtol * nb / rn, 1e-15);
       g = cg<double>(s, s->hi, s->cells_hi, s->r, s->dd, s->ri, s->p, s->q, s->z, jac ? s->dinv : nullptr, tol,
                      o->max_inner, &it, &applies);
       if (g != GP_OK) return g;
       stats->hi_applies += applies;
-      add64_k<<<kVecBlocks, kThreads, 0, s->st>>>(u, s->dd, n);
+      add64_k<<<s->nvec, kThreads, 0, s->st>>>(u, s->dd, n);
     }
     stats->inner += it;
     g = sys_apply(s, s->hi, s->cells_hi, u, s->q, s->st);
     if (g != GP_OK) return g;
     stats->hi_applies++;
-    resid_k<<<kVecBlocks, kThreads, 0, s->st>>>(s->r, b, s->q, n);
+    resid_k<<<s->nvec, kThreads, 0, s->st>>>(s->r, b, s->q, n);
     ++outer;
   }
   double rr = 0.0;
