@@ -137,6 +137,44 @@ __device__ __forceinline__ ff64 dot_value(const Dot<ff64>& d) {
   return ff64{hi, __fsub_rn(d.c, __fsub_rn(hi, d.s))};
 }
 
+// (a + b) and (a - b) for inputs of the compensated dot products: for float-float
+// the two-sum of the high parts with the low parts added to its error, left
+// unnormalised (the products of the dot product split both parts exactly or carry
+// their rounding into the error sum, so the absolute error stays 2^-48 |a|, |b|).
+__device__ __forceinline__ float vadd_loose(float a, float b) { return a + b; }
+__device__ __forceinline__ double vadd_loose(double a, double b) { return a + b; }
+__device__ __forceinline__ ff64 vadd_loose(ff64 a, ff64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ff64{s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+__device__ __forceinline__ float vsub_loose(float a, float b) { return a - b; }
+__device__ __forceinline__ double vsub_loose(double a, double b) { return a - b; }
+__device__ __forceinline__ ff64 vsub_loose(ff64 a, ff64 b) { return vadd_loose(a, ff64{-b.hi, -b.lo}); }
+
+// value of the sum (NEG = false) or difference (NEG = true) of two dot-product
+// accumulators: one two-sum of the running sums, the error sums added, one
+// renormalisation
+template <bool NEG>
+__device__ __forceinline__ float dot_merge(const Dot<float>& a, const Dot<float>& b) {
+  return NEG ? a.v - b.v : a.v + b.v;
+}
+template <bool NEG>
+__device__ __forceinline__ double dot_merge(const Dot<double>& a, const Dot<double>& b) {
+  return NEG ? a.v - b.v : a.v + b.v;
+}
+template <bool NEG>
+__device__ __forceinline__ ff64 dot_merge(const Dot<ff64>& a, const Dot<ff64>& b) {
+  const float bs = NEG ? -b.s : b.s, bc = NEG ? -b.c : b.c;
+  const float s = __fadd_rn(a.s, bs);
+  const float bb = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(bs, bb));
+  const float c = __fadd_rn(__fadd_rn(a.c, bc), err);
+  const float hi = __fadd_rn(s, c);
+  return ff64{hi, __fsub_rn(c, __fsub_rn(hi, s))};
+}
+
 template <typename V> __device__ __forceinline__ Sum<V> sum_zero() { return Sum<V>{vzero<V>()}; }
 template <> __device__ __forceinline__ Sum<ff64> sum_zero<ff64>() { return Sum<ff64>{0.f, 0.f}; }
 __device__ __forceinline__ void sum_add(Sum<float>& d, float v) { d.v += v; }

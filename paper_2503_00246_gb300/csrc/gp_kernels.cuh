@@ -159,8 +159,8 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     V vp[K], vm[K];
 #pragma unroll
     for (int b = 0; b < K; ++b) {
-      vp[b] = vadd(v[b], v[NN - 1 - b]);
-      vm[b] = vsub(v[b], v[NN - 1 - b]);
+      vp[b] = vadd_loose(v[b], v[NN - 1 - b]);
+      vm[b] = vsub_loose(v[b], v[NN - 1 - b]);
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -238,19 +238,16 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
       Dot<V> ev = dot_first(c.g[0][b], sj[0]);
 #pragma unroll
       for (int j = 2; j < K; j += 2) dot_fma(ev, c.g[j][b], sj[j]);
-      const V e = dot_value(ev);
-      if (b == K) {
+      if (b == K || K == 1) {
+        const V e = dot_value(ev);
         dst[pos0 + pstride * b] = e;
-      } else if constexpr (K == 1) {
-        dst[pos0 + pstride * b] = e;
-        dst[pos0 + pstride * (NN - 1 - b)] = e;
+        if (b < K) dst[pos0 + pstride * (NN - 1 - b)] = e;
       } else {
-        Dot<V> ov = dot_first(c.g[1][b], sj[1]);
+        Dot<V> ov = dot_first(c.g[K > 1 ? 1 : 0][b], sj[K > 1 ? 1 : 0]);
 #pragma unroll
         for (int j = 3; j < K; j += 2) dot_fma(ov, c.g[j][b], sj[j]);
-        const V o = dot_value(ov);
-        dst[pos0 + pstride * b] = vadd(e, o);
-        dst[pos0 + pstride * (NN - 1 - b)] = vsub(e, o);
+        dst[pos0 + pstride * b] = dot_merge<false>(ev, ov);
+        dst[pos0 + pstride * (NN - 1 - b)] = dot_merge<true>(ev, ov);
       }
     }
   }

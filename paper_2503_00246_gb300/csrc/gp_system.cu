@@ -130,8 +130,8 @@ cudaError_t dot(gp_system* s, const T* a, const T* b, double* out) {
 // y = A x with the operator of context c in three launches: the ghost-penalty face
 // kernel (face outputs only), the cell kernel (cell outputs; it overlaps the face kernel
 // as its programmatic dependent), and one gather that adds, per node, the face outputs
-// and then the cell outputs and writes y once.  With dotp, the gather also leaves the partial sums of dotp . y (one per gather
-// CTA, s->nparts of them) in s->part.
+// and then the cell outputs and writes y once.  With dotp, the gather also leaves the
+// partial sums of dotp . y (one per gather CTA, s->nparts of them) in s->part.
 gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, void* y, cudaStream_t st,
                     const void* dotp = nullptr) {
   gp_status g = gpi::launch(c, x, y, 1, st, nullptr, false, nullptr, 1);   // face kernel alone
