@@ -300,8 +300,10 @@ void gp_batch_destroy(gp_batch* batch);
 typedef struct gp_system gp_system;
 gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out);
 
-/* y = A x with the hi (which = 0; x, y double) or lo (which = 1; float) operator.
- * Deterministic: G first, then the cells of each parity colour in a fixed order. */
+/* y = A x with the hi (which = 0; x, y double) or lo (which = 1; float) operator,
+ * y overwritten.  Three launches on `stream`: the ghost-penalty face kernel, the cell
+ * kernel, and one gather that adds per node the ghost-face outputs and then the cell
+ * outputs in a fixed order (no atomics: bitwise reproducible) and writes y once. */
 gp_status gp_system_apply(gp_system* sys, int which, const void* x, void* y, void* stream);
 
 /* y = (mass_weight M_active + stiff_weight K_active) x with the hi (which = 0) or lo
@@ -313,7 +315,9 @@ gp_status gp_system_cells(gp_system* sys, int which, double mass_weight, double 
 
 /* Solvers (the paper leaves the solver open, Sec. 1).  mode 0, defect correction:
  * r = b - A_hi u and all updates in FP64; each correction A_lo d = r solved by CG
- * with the FP32 operator and FP64 inner products to relative residual inner_rtol
+ * with the FP32 operator to relative residual inner_rtol; its inner products sum
+ * the exact products of the FP32 entries with compensated float-float sums and
+ * combine the per-thread sums in FP64 (about FP64 accuracy, no FP64 work per element)
  * (at most max_inner iterations); at most max_outer corrections; stops when
  * ||b - A_hi u|| <= rtol ||b||.  mode 1: the same outer loop with FP64 CG on the hi
  * operator as the inner solver (tolerance chosen to reach rtol), i.e. plain FP64 CG

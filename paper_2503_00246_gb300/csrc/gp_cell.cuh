@@ -15,9 +15,11 @@
 // Two launches, like the face operator: cell_kernel stores every cell's (k+1)^d
 // outputs, and cell_gather adds, for every node, the outputs of the (up to 2^d) active
 // cells that hold it, in a fixed order: no atomics, no colour phases, bitwise
-// reproducible.  Both are programmatic dependents of the kernel before them: cell_kernel
-// reads only x and the tables, so it runs while the ghost-penalty lift drains and waits
-// for it only before it exits; cell_gather waits for cell_kernel before it touches y.
+// reproducible.  In the model system's apply the gather first adds the ghost-face
+// outputs of the node (the lift's row code) and so writes y = (M + K + G) x once.  Both
+// are programmatic dependents of the kernel before them: cell_kernel reads only x and
+// the tables, so it runs while the ghost-penalty face kernel drains and waits for it
+// only before it exits; cell_gather waits for cell_kernel before it touches y.
 #pragma once
 
 #include <cstdint>
