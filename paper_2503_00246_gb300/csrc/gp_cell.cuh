@@ -9,7 +9,8 @@
 // is applied by sum factorisation: a = M^ x, b = S^ x along x; c = M^ a, d = S^ a,
 // e = M^ b along y; y_K = M^ (h^3 c + h (d + e)) + S^ (h c) along z (3D), or
 // y_K = M^ (h^2 a + b) + S^ a along y (2D).  One thread per x-line of a cell; the y
-// and z passes go through shared memory.  The float-float form renormalises after every
+// and z passes go through shared memory.  Every 1D application uses the even / odd
+// halves of the centrosymmetric M^ and S^ (about half the multiply-adds; CellConsts).  The float-float form renormalises after every
 // operation here (the model system's outer residual needs the full accuracy).
 //
 // Two launches, like the face operator: cell_kernel stores every cell's (k+1)^d
@@ -41,13 +42,53 @@ struct CellShape {
   static constexpr int KR = (D == 3) ? K * K : K;           // x-rows per owner cell
 };
 
+// Even / odd halves of a centrosymmetric (N x N) matrix A (A[N-1-p][N-1-q] = A[p][q]; the 1D
+// reference mass and stiffness on the Gauss-Lobatto nodes, which are symmetric about the
+// cell centre).  With the folded input e[i] = x[i] + x[N-1-i], o[i] = x[i] - x[N-1-i]
+// (i < N/2) and e[N/2] = x[N/2] for odd N,
+//   y[p] = E_p + O_p,  y[N-1-p] = E_p - O_p  (p < N/2),  y[N/2] = E_{N/2}  (odd N),
+//   E_p = sum_i ae[p][i] e[i],  O_p = sum_i ao[p][i] o[i],
+// with ae[p][i] = (A[p][i] + A[p][N-1-i]) / 2, ae[p][N/2] = A[p][N/2] and
+// ao[p][i] = (A[p][i] - A[p][N-1-i]) / 2: (N/2 + 1)(N+1)/2 + (N/2)^2 multiply-adds instead
+// of N^2.
 template <typename V, int K>
 struct CellConsts {
-  V m[K + 1][K + 1];  // reference mass
-  V s[K + 1][K + 1];  // reference stiffness
-  V hm;               // wm h^d
-  V hs;               // ws h^(d-2)
+  static constexpr int N = K + 1, H = N / 2, NE = (N + 1) / 2;
+  V me[NE][NE];  // reference mass, even half
+  V mo[H][H];    // reference mass, odd half
+  V se[NE][NE];  // reference stiffness, even half
+  V so[H][H];    // reference stiffness, odd half
+  V hm;          // wm h^d
+  V hs;          // ws h^(d-2)
 };
+
+template <int N, class V>
+__device__ __forceinline__ void eo_fold(const V (&x)[N], V (&e)[(N + 1) / 2], V (&o)[N / 2]) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    e[i] = vadd(x[i], x[N - 1 - i]);
+    o[i] = vsub(x[i], x[N - 1 - i]);
+  }
+  if constexpr (N % 2 == 1) e[N / 2] = x[N / 2];
+}
+
+// the even (E) or odd (O) partial sum of output p: sum_i a[p][i] v[i]
+template <int M, class V>
+__device__ __forceinline__ V eo_row(const V (&a)[M], const V (&v)[M]) {
+  V acc = vmul(a[0], v[0]);
+#pragma unroll
+  for (int i = 1; i < M; ++i) acc = vfma(a[i], v[i], acc);
+  return acc;
+}
+template <int M, class V>
+__device__ __forceinline__ V eo_row2(const V (&a)[M], const V (&v)[M], const V (&b)[M], const V (&w)[M]) {
+  V acc = vmul(a[0], v[0]);
+#pragma unroll
+  for (int i = 1; i < M; ++i) acc = vfma(a[i], v[i], acc);
+#pragma unroll
+  for (int i = 0; i < M; ++i) acc = vfma(b[i], w[i], acc);
+  return acc;
+}
 
 // Device tables of the cell operator (see Plan::crow, cwin, corow).
 struct CellTabs {
@@ -79,6 +120,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
   using S = CellShape<D, K>;
   using V = typename A::V;
   constexpr int K1 = S::K1, R = S::R, NODES = S::NODES, CB = S::CB;
+  constexpr int H = K1 / 2, NE = (K1 + 1) / 2;
   __shared__ V sa[CB][NODES];
   __shared__ V sb[CB][NODES];
   const int t = threadIdx.x;
@@ -89,19 +131,25 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
   asm volatile("griddepcontrol.launch_dependents;");
 
   // ---- x pass: a = M^ x, b = S^ x on this thread's x-line
-  V xl[K1];
+  {
+    V xl[K1], e[NE], o[H];
 #pragma unroll
-  for (int i = 0; i < K1; ++i) xl[i] = valid ? from_io(__ldg(x + row + i), (V*)nullptr) : vzero<V>();
+    for (int i = 0; i < K1; ++i) xl[i] = valid ? from_io(__ldg(x + row + i), (V*)nullptr) : vzero<V>();
+    eo_fold<K1>(xl, e, o);
 #pragma unroll
-  for (int p = 0; p < K1; ++p) {
-    V a = vzero<V>(), b = vzero<V>();
-#pragma unroll
-    for (int q = 0; q < K1; ++q) {
-      a = vfma(c.m[p][q], xl[q], a);
-      b = vfma(c.s[p][q], xl[q], b);
+    for (int p = 0; p < NE; ++p) {
+      const V ae = eo_row<NE>(c.me[p], e), be = eo_row<NE>(c.se[p], e);
+      if (p < H) {
+        const V ao = eo_row<H>(c.mo[p], o), bo = eo_row<H>(c.so[p], o);
+        sa[cl][p + K1 * line] = vadd(ae, ao);
+        sa[cl][K1 - 1 - p + K1 * line] = vsub(ae, ao);
+        sb[cl][p + K1 * line] = vadd(be, bo);
+        sb[cl][K1 - 1 - p + K1 * line] = vsub(be, bo);
+      } else {
+        sa[cl][p + K1 * line] = ae;
+        sb[cl][p + K1 * line] = be;
+      }
     }
-    sa[cl][p + K1 * line] = a;
-    sb[cl][p + K1 * line] = b;
   }
   __syncthreads();
 
@@ -110,41 +158,52 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
     // ---- y pass on the line (i1, i3): f = h^3 M^ a + h (S^ a + M^ b), g = h M^ a
     {
       const int i1 = line % K1, i3 = line / K1;
-      V ay[K1], by[K1];
+      V ay[K1], by[K1], ae[NE], ao[H], be[NE], bo[H];
 #pragma unroll
       for (int q = 0; q < K1; ++q) {
         ay[q] = sa[cl][i1 + K1 * (q + K1 * i3)];
         by[q] = sb[cl][i1 + K1 * (q + K1 * i3)];
       }
+      eo_fold<K1>(ay, ae, ao);
+      eo_fold<K1>(by, be, bo);
 #pragma unroll
-      for (int p = 0; p < K1; ++p) {
-        V cc = vzero<V>(), dd = vzero<V>(), ee = vzero<V>();
-#pragma unroll
-        for (int q = 0; q < K1; ++q) {
-          cc = vfma(c.m[p][q], ay[q], cc);
-          dd = vfma(c.s[p][q], ay[q], dd);
-          ee = vfma(c.m[p][q], by[q], ee);
+      for (int p = 0; p < NE; ++p) {
+        const V cE = eo_row<NE>(c.me[p], ae), tE = eo_row2<NE>(c.se[p], ae, c.me[p], be);
+        if (p < H) {
+          const V cO = eo_row<H>(c.mo[p], ao), tO = eo_row2<H>(c.so[p], ao, c.mo[p], bo);
+          const V c0 = vadd(cE, cO), c1 = vsub(cE, cO), t0 = vadd(tE, tO), t1 = vsub(tE, tO);
+          sa[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hm, c0, vmul(c.hs, t0));
+          sb[cl][i1 + K1 * (p + K1 * i3)] = vmul(c.hs, c0);
+          sa[cl][i1 + K1 * (K1 - 1 - p + K1 * i3)] = vfma(c.hm, c1, vmul(c.hs, t1));
+          sb[cl][i1 + K1 * (K1 - 1 - p + K1 * i3)] = vmul(c.hs, c1);
+        } else {
+          sa[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hm, cE, vmul(c.hs, tE));
+          sb[cl][i1 + K1 * (p + K1 * i3)] = vmul(c.hs, cE);
         }
-        sa[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hm, cc, vfma(c.hs, vadd(dd, ee), vzero<V>()));
-        sb[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hs, cc, vzero<V>());
       }
     }
     __syncthreads();
     // ---- z pass on the line (i1, i2): y = M^ f + S^ g, stored along z
     {
       const int i1 = line % K1, i2 = line / K1;
-      V fz[K1], gz[K1];
+      V fz[K1], gz[K1], fe[NE], fo[H], ge[NE], go[H];
 #pragma unroll
       for (int q = 0; q < K1; ++q) {
         fz[q] = sa[cl][i1 + K1 * (i2 + K1 * q)];
         gz[q] = sb[cl][i1 + K1 * (i2 + K1 * q)];
       }
+      eo_fold<K1>(fz, fe, fo);
+      eo_fold<K1>(gz, ge, go);
 #pragma unroll
-      for (int p = 0; p < K1; ++p) {
-        V yv = vzero<V>();
-#pragma unroll
-        for (int q = 0; q < K1; ++q) yv = vfma(c.s[p][q], gz[q], vfma(c.m[p][q], fz[q], yv));
-        yout[p] = yv;
+      for (int p = 0; p < NE; ++p) {
+        const V yE = eo_row2<NE>(c.me[p], fe, c.se[p], ge);
+        if (p < H) {
+          const V yO = eo_row2<H>(c.mo[p], fo, c.so[p], go);
+          yout[p] = vadd(yE, yO);
+          yout[K1 - 1 - p] = vsub(yE, yO);
+        } else {
+          yout[p] = yE;
+        }
       }
       if (valid) {
         V* dst = wc + (size_t)cell * NODES;
@@ -156,22 +215,25 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
     asm volatile("griddepcontrol.wait;" ::: "memory");
   } else {
     // ---- y pass on the line i1: y = M^ (h^2 a + b) + S^ a
-    V ay[K1], by[K1];
+    V f[K1], g[K1], fe[NE], fo[H], ge[NE], go[H];
 #pragma unroll
     for (int q = 0; q < K1; ++q) {
-      ay[q] = sa[cl][line + K1 * q];
-      by[q] = sb[cl][line + K1 * q];
+      const V ay = sa[cl][line + K1 * q], by = sb[cl][line + K1 * q];
+      f[q] = vfma(c.hm, ay, vmul(c.hs, by));
+      g[q] = vmul(c.hs, ay);
     }
+    eo_fold<K1>(f, fe, fo);
+    eo_fold<K1>(g, ge, go);
 #pragma unroll
-    for (int p = 0; p < K1; ++p) {
-      V yv = vzero<V>();
-#pragma unroll
-      for (int q = 0; q < K1; ++q) {
-        const V f = vfma(c.hm, ay[q], vfma(c.hs, by[q], vzero<V>()));
-        yv = vfma(c.m[p][q], f, yv);
-        yv = vfma(c.s[p][q], vfma(c.hs, ay[q], vzero<V>()), yv);
+    for (int p = 0; p < NE; ++p) {
+      const V yE = eo_row2<NE>(c.me[p], fe, c.se[p], ge);
+      if (p < H) {
+        const V yO = eo_row2<H>(c.mo[p], fo, c.so[p], go);
+        yout[p] = vadd(yE, yO);
+        yout[K1 - 1 - p] = vsub(yE, yO);
+      } else {
+        yout[p] = yE;
       }
-      yout[p] = yv;
     }
     if (valid) {
       V* dst = wc + (size_t)cell * NODES;
@@ -367,11 +429,20 @@ cudaError_t run_cells(const void* x, void* y, const CellTabs& ct, const double* 
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
-  CellConsts<V, K> c;
-  for (int p = 0; p < K + 1; ++p)
-    for (int q = 0; q < K + 1; ++q) {
-      c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
-      c.s[p][q] = from_host<V>(s[p * (K + 1) + q]);
+  using C = CellConsts<V, K>;
+  constexpr int N = C::N, H = C::H, NE = C::NE;
+  C c;
+  // even / odd halves of the centrosymmetric reference matrices (see CellConsts)
+  for (int p = 0; p < NE; ++p)
+    for (int i = 0; i < NE; ++i) {
+      const bool mid = 2 * i == N - 1;
+      c.me[p][i] = from_host<V>(mid ? m[p * N + i] : 0.5 * (m[p * N + i] + m[p * N + N - 1 - i]));
+      c.se[p][i] = from_host<V>(mid ? s[p * N + i] : 0.5 * (s[p * N + i] + s[p * N + N - 1 - i]));
+    }
+  for (int p = 0; p < H; ++p)
+    for (int i = 0; i < H; ++i) {
+      c.mo[p][i] = from_host<V>(0.5 * (m[p * N + i] - m[p * N + N - 1 - i]));
+      c.so[p][i] = from_host<V>(0.5 * (s[p * N + i] - s[p * N + N - 1 - i]));
     }
   c.hm = from_host<V>(wm * (D == 3 ? h * h * h : h * h));
   c.hs = from_host<V>(ws * (D == 3 ? h : 1.0));

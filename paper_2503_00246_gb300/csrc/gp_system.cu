@@ -9,6 +9,7 @@
 //
 // Every reduction has a fixed order (fixed grid, fixed tree), so a solve is
 // bitwise reproducible.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -464,6 +465,22 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (!gp::check_cell_table(p)) {
     delete s;
     return fail(nullptr, GP_EINVAL, "internal: cell table outside the active DoFs");
+  }
+  // the cell kernel applies M^ and S^ through their even / odd halves, which needs
+  // A[k-p][k-q] = A[p][q] (Gauss-Lobatto nodes symmetric about the cell centre)
+  {
+    const int N = p.k + 1;
+    double dev = 0.0, mx = 0.0;
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < N; ++b)
+        for (const std::vector<double>* A : {&p.mass, &p.stiff}) {
+          dev = std::max(dev, std::fabs((*A)[a * N + b] - (*A)[(N - 1 - a) * N + N - 1 - b]));
+          mx = std::max(mx, std::fabs((*A)[a * N + b]));
+        }
+    if (!(dev <= 1e-13 * mx)) {
+      delete s;
+      return fail(nullptr, GP_EINVAL, "internal: reference mass / stiffness not centrosymmetric");
+    }
   }
   s->cells_hi = cells_for(p);
   if (lo) s->cells_lo = cells_for(lo->plan);

@@ -201,6 +201,18 @@ def test_jump_vectors_mirror_symmetry(gplib, k):
             assert abs(row[k]) <= 1e-14 * scale
 
 
+@pytest.mark.parametrize("k", range(1, 9))
+def test_reference_mass_centrosymmetric(gplib, k):
+    # The Gauss-Lobatto nodes are symmetric about the cell centre, so reversing the node
+    # order maps M^ to itself: M^[k-a][k-b] = M^[a][b].  The cell kernel of the model system
+    # applies M^ (and S^, which the library checks when a system is created) through its
+    # even and odd halves and relies on this.
+    ctx = gplib.setup_problem(W.small_ball(3, 6, k), device=-1)
+    m, _, _ = gplib.gp_reference_1d(ctx)
+    m = np.asarray(m)
+    assert np.abs(m[::-1, ::-1] - m).max() <= 1e-15 * np.abs(m).max()
+
+
 @pytest.mark.parametrize("dim,k", [(2, 1), (2, 4), (2, 8), (3, 2), (3, 3), (3, 5)])
 def test_macro_patch_1d_data_matches_oracle(gplib, dim, k):
     # the host's rank-k form gamma h^d sum_j lambda_j (M^ x ... x v_j v_j^T) against the oracle's
