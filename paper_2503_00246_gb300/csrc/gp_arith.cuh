@@ -196,10 +196,17 @@ __device__ __forceinline__ void sum_add(Sum<ff64>& d, ff64 v) {
 // the (sum, error) pair to double once.
 template <typename T>
 struct IoDot;
+// merge() adds another partial sum (same scheme), shfl_down() reads lane + o's.
 template <>
 struct IoDot<double> {
   double v = 0.0;
   __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void merge(const IoDot& o) { v += o.v; }
+  __device__ __forceinline__ IoDot shfl_down(int o) const {
+    IoDot r;
+    r.v = __shfl_down_sync(0xffffffffu, v, o);
+    return r;
+  }
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
@@ -213,6 +220,19 @@ struct IoDot<float> {
     const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
     s = t;
     c = __fadd_rn(__fadd_rn(c, e), err);
+  }
+  __device__ __forceinline__ void merge(const IoDot& o) {
+    const float t = __fadd_rn(s, o.s);                     // two-sum of s + o.s
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o.s, bb));
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, o.c), err);
+  }
+  __device__ __forceinline__ IoDot shfl_down(int o) const {
+    IoDot r;
+    r.s = __shfl_down_sync(0xffffffffu, s, o);
+    r.c = __shfl_down_sync(0xffffffffu, c, o);
+    return r;
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };

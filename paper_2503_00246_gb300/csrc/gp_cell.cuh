@@ -113,6 +113,13 @@ struct CellTabs {
 
 constexpr int GATHER_THREADS = 256;
 
+// the two fields of a pass kept side by side in shared memory, so that one access
+// moves both (half the shared-memory instructions)
+template <typename V>
+struct alignas(2 * sizeof(V)) VPair {
+  V a, b;
+};
+
 template <int D, int K, class A>
 __global__ void __launch_bounds__(CellShape<D, K>::NT)
 cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc, const int32_t* __restrict__ crow,
@@ -121,8 +128,7 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
   using V = typename A::V;
   constexpr int K1 = S::K1, R = S::R, NODES = S::NODES, CB = S::CB;
   constexpr int H = K1 / 2, NE = (K1 + 1) / 2;
-  __shared__ V sa[CB][NODES];
-  __shared__ V sb[CB][NODES];
+  __shared__ VPair<V> sab[CB][NODES];
   const int t = threadIdx.x;
   const int cl = t / R, line = t - cl * R;
   const int cell = blockIdx.x * CB + cl;
@@ -141,13 +147,10 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
       const V ae = eo_row<NE>(c.me[p], e), be = eo_row<NE>(c.se[p], e);
       if (p < H) {
         const V ao = eo_row<H>(c.mo[p], o), bo = eo_row<H>(c.so[p], o);
-        sa[cl][p + K1 * line] = vadd(ae, ao);
-        sa[cl][K1 - 1 - p + K1 * line] = vsub(ae, ao);
-        sb[cl][p + K1 * line] = vadd(be, bo);
-        sb[cl][K1 - 1 - p + K1 * line] = vsub(be, bo);
+        sab[cl][p + K1 * line] = VPair<V>{vadd(ae, ao), vadd(be, bo)};
+        sab[cl][K1 - 1 - p + K1 * line] = VPair<V>{vsub(ae, ao), vsub(be, bo)};
       } else {
-        sa[cl][p + K1 * line] = ae;
-        sb[cl][p + K1 * line] = be;
+        sab[cl][p + K1 * line] = VPair<V>{ae, be};
       }
     }
   }
@@ -161,8 +164,9 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
       V ay[K1], by[K1], ae[NE], ao[H], be[NE], bo[H];
 #pragma unroll
       for (int q = 0; q < K1; ++q) {
-        ay[q] = sa[cl][i1 + K1 * (q + K1 * i3)];
-        by[q] = sb[cl][i1 + K1 * (q + K1 * i3)];
+        const VPair<V> v = sab[cl][i1 + K1 * (q + K1 * i3)];
+        ay[q] = v.a;
+        by[q] = v.b;
       }
       eo_fold<K1>(ay, ae, ao);
       eo_fold<K1>(by, be, bo);
@@ -172,13 +176,10 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
         if (p < H) {
           const V cO = eo_row<H>(c.mo[p], ao), tO = eo_row2<H>(c.so[p], ao, c.mo[p], bo);
           const V c0 = vadd(cE, cO), c1 = vsub(cE, cO), t0 = vadd(tE, tO), t1 = vsub(tE, tO);
-          sa[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hm, c0, vmul(c.hs, t0));
-          sb[cl][i1 + K1 * (p + K1 * i3)] = vmul(c.hs, c0);
-          sa[cl][i1 + K1 * (K1 - 1 - p + K1 * i3)] = vfma(c.hm, c1, vmul(c.hs, t1));
-          sb[cl][i1 + K1 * (K1 - 1 - p + K1 * i3)] = vmul(c.hs, c1);
+          sab[cl][i1 + K1 * (p + K1 * i3)] = VPair<V>{vfma(c.hm, c0, vmul(c.hs, t0)), vmul(c.hs, c0)};
+          sab[cl][i1 + K1 * (K1 - 1 - p + K1 * i3)] = VPair<V>{vfma(c.hm, c1, vmul(c.hs, t1)), vmul(c.hs, c1)};
         } else {
-          sa[cl][i1 + K1 * (p + K1 * i3)] = vfma(c.hm, cE, vmul(c.hs, tE));
-          sb[cl][i1 + K1 * (p + K1 * i3)] = vmul(c.hs, cE);
+          sab[cl][i1 + K1 * (p + K1 * i3)] = VPair<V>{vfma(c.hm, cE, vmul(c.hs, tE)), vmul(c.hs, cE)};
         }
       }
     }
@@ -189,8 +190,9 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
       V fz[K1], gz[K1], fe[NE], fo[H], ge[NE], go[H];
 #pragma unroll
       for (int q = 0; q < K1; ++q) {
-        fz[q] = sa[cl][i1 + K1 * (i2 + K1 * q)];
-        gz[q] = sb[cl][i1 + K1 * (i2 + K1 * q)];
+        const VPair<V> v = sab[cl][i1 + K1 * (i2 + K1 * q)];
+        fz[q] = v.a;
+        gz[q] = v.b;
       }
       eo_fold<K1>(fz, fe, fo);
       eo_fold<K1>(gz, ge, go);
@@ -218,7 +220,8 @@ cell_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wc
     V f[K1], g[K1], fe[NE], fo[H], ge[NE], go[H];
 #pragma unroll
     for (int q = 0; q < K1; ++q) {
-      const V ay = sa[cl][line + K1 * q], by = sb[cl][line + K1 * q];
+      const VPair<V> v = sab[cl][line + K1 * q];
+      const V ay = v.a, by = v.b;
       f[q] = vfma(c.hm, ay, vmul(c.hs, by));
       g[q] = vmul(c.hs, ay);
     }
@@ -405,14 +408,18 @@ cell_gather(const typename A::V* __restrict__ wc, typename A::IO* __restrict__ y
   IoDot<typename A::IO> dot;
   if (base >= 0) gather_row<D, K, A>(wc, y, add, ct, own, t, base, dot);
   if (ct.dotpart) {
-    __shared__ double sh[GATHER_THREADS];
-    sh[threadIdx.x] = dot.value();
+    // the CTA's partial sum in a fixed order: a shuffle tree per warp, then the warps in
+    // order, in the accumulator's own arithmetic (no FP64 work for FP32 vectors)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot.merge(dot.shfl_down(o));
+    __shared__ IoDot<typename A::IO> wsum[GATHER_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = dot;
     __syncthreads();
-    for (int o = GATHER_THREADS / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
+    if (threadIdx.x == 0) {
+      IoDot<typename A::IO> tot = wsum[0];
+      for (int w = 1; w < GATHER_THREADS / 32; ++w) tot.merge(wsum[w]);
+      ct.dotpart[blockIdx.x] = tot.value();
     }
-    if (threadIdx.x == 0) ct.dotpart[blockIdx.x] = sh[0];
   }
 }
 
