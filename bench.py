@@ -561,6 +561,10 @@ def run_gpu(args):
             "clocks": ck,
             "n_active": ctx.n_active, "n_faces": nf, "n_touched": ctx.n_touched,
             "paper_flops_per_step": _flops_paper(d, k, nf),
+            "paper_flop_rate": {"tflops": _flops_paper(d, k, nf) / (jump_ms * 1e-3) / 1e12,
+                                "flops_per_face": _flops_paper(d, k, 1),
+                                "count": "the paper's per-face count 2[(k+1)^(d-1) (2k+1)^2 + (d-1) (k+1)^d (2k+1)] "
+                                         "over the face kernel's time"},
             "tiles": tiles,
         }
         ctx.close()
@@ -595,6 +599,7 @@ def run_gpu(args):
                       "peak_source": peak_src},
         "kernel_ms": r["kernel_ms"],
         "ghost_faces_per_s": r["ghost_faces_per_s"],
+        "paper_flop_rate": r["paper_flop_rate"],
         "tiles": r["tiles"],
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
     }
@@ -603,7 +608,7 @@ def run_gpu(args):
         f = results[p]
         line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
                                               "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value", "tiles",
-                                              "ghost_faces_per_s")}
+                                              "ghost_faces_per_s", "paper_flop_rate")}
     if not args.no_batched:
         line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2, args.tune_reps)
                            for p in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32)}
