@@ -5,7 +5,10 @@
 // evaluation).  The paper leaves the solver to future work (Sec. 1); this file
 // provides the defect-correction scheme of mixed-precision solvers: residuals,
 // updates and inner products in FP64, the inner correction solved by CG with the
-// FP32 operator, next to plain CG with the FP64 operator for comparison.
+// FP32 operator, next to plain CG with the FP64 operator for comparison.  The inner
+// CG's FP32 vectors have their inner products summed from exact float products in
+// compensated float-float arithmetic and combined in FP64 (IoDot), which keeps the
+// FP64 pipe (2 FMAs per clock per SM on GB300) out of the per-element work.
 //
 // Every reduction has a fixed order (fixed grid, fixed tree), so a solve is
 // bitwise reproducible.
