@@ -353,7 +353,7 @@ inline int64_t gather_ctas(int dim, int k, int64_t ncown) {
 }
 
 template <int D, int K>
-__device__ __forceinline__ bool gather_slot(const int u, int& o, int& q, int& r) {
+__host__ __device__ __forceinline__ bool gather_slot(const int u, int& o, int& q, int& r) {
   constexpr int OPC = gather_owners_per_cta(D, K);
   constexpr int C1 = K - 1;                 // rows per owner with exactly one of q, r zero (each)
   if (u >= OPC * CellShape<D, K>::KR) return false;
