@@ -25,7 +25,8 @@ def _oracle_system(pr):
 
 
 @pytest.mark.parametrize("hi", [0, 2])
-@pytest.mark.parametrize("dim,k,n", [(2, 2, 14), (2, 5, 8), (3, 1, 10), (3, 3, 8), (3, 4, 7)])
+@pytest.mark.parametrize("dim,k,n", [(2, 2, 14), (2, 5, 8), (2, 8, 6), (3, 1, 10), (3, 3, 8), (3, 4, 7), (3, 6, 4),
+                                     (3, 7, 4), (3, 8, 3)])
 def test_system_apply_matches_oracle(gplib, cuda, dim, k, n, hi):
     pr = W.small_ball(dim, n, k, radius=0.6, seed=80 + k)
     o, A = _oracle_system(pr)
