@@ -1,4 +1,4 @@
-"""Compiles the C parts of the test infrastructure (oracle/kron_cpu.c) into oracle/_lib.
+"""Compiles the C part of the paper-like CPU baseline (baselines/kron_cpu.c) into baselines/_lib.
 
 Plain gcc with OpenMP, portable flags only (the same source builds on x86-64 and aarch64).
 """

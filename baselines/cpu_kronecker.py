@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).  This module is not part of
 the oracle's definition: the oracle never uses the tensor-product factorisation.
 It is the paper-like CPU baseline that bench.py times beside the oracle, and
-tests/test_oracle_kronecker.py checks it against the oracle's explicit face
+tests/test_baseline_kronecker.py checks it against the oracle's explicit face
 matrices.
 
 Sec. 2.4: on a face with normal a the face matrix factorises as
@@ -21,7 +21,7 @@ import os
 
 import numpy as np
 
-from .basis import gauss_legendre, gauss_lobatto_nodes, lagrange_derivative_at, lagrange_value
+from oracle.basis import gauss_legendre, gauss_lobatto_nodes, lagrange_derivative_at, lagrange_value
 
 
 def reference_1d(k: int):
@@ -82,8 +82,8 @@ class KroneckerCPU:
 
 
 class KroneckerOpenMP(KroneckerCPU):
-    """The same factorised apply in C with OpenMP over faces (oracle/kron_cpu.c, built by
-    oracle/build_c.py): the paper-like CPU baseline that bench.py times."""
+    """The same factorised apply in C with OpenMP over faces (baselines/kron_cpu.c, built by
+    baselines/build_c.py): the paper-like CPU baseline that bench.py times."""
 
     def __init__(self, pr, oracle, nthreads: int | None = None):
         super().__init__(pr, oracle)

@@ -1,16 +1,19 @@
 """Benchmark of the matrix-free ghost-penalty apply y = G x on GB300.
 
-Workload: 3D ball of radius 0.7 (seeded centre offset) in a 64^3 Cartesian mesh
-on [-1,1]^3, FE_Q(3) on Gauss-Lobatto points, gamma = 0.5 for every order;
-x ~ U[-1,1] on the active DoFs.  One step = one y = G x over all ghost faces.
+Workload (the headline): gyroid sin x cos y + sin y cos z + sin z cos x = 0.3 on
+[-pi,pi]^3, 128^3 Cartesian cells, FE_Q(4) on Gauss-Lobatto points, gamma = 0.5 for
+every order (58.8M active DoFs, 335,664 ghost faces); x ~ U[-1,1] on the active DoFs.
+One step = one y = G x over all ghost faces, native FP64.  The FP32 and float-float
+forms run beside it on the same workload, each with its error against the FP64
+oracle on sampled rows.  Also in the line: the degree sweep k = 1..8 on the 96^3
+ball (bounded), and the batched workload (64 problems x 4 right-hand sides).
 
 Metric: GDoF/s = active DoFs / apply time (the paper's throughput convention,
-Sec. 3.1), whole job over all ranks.  The inputs (about 12 MB) fit in L2, so
-a 512 MB buffer is written between timed steps to flush it.
+Sec. 3.1), whole job over all ranks.  x and y of the headline (470 MB each in
+FP64) exceed the L2, and a 512 MB buffer is written between timed steps anyway.
 
 Arms
-  default            the CUDA path through the C ABI: FP64-accuracy headline (float-float
-                     arithmetic on FP64 data), native FP64 and FP32 beside it
+  default            the CUDA path through the C ABI
   --impl reference   the CPU FP64 oracle timed on the host cores (bounded sample)
 
 Multi-GPU: one independent replica per rank (the single-problem apply does not
@@ -33,7 +36,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ghost-penalty GDoF/s & %HBM roofline, FP64 vs FP32/batched at stated error"
-WORKLOAD = "ghost-penalty y=Gx, 3D ball r=0.7 in 64^3 cells on [-1,1]^3, FE_Q(3) Gauss-Lobatto, gamma=0.5"
+WORKLOAD = ("ghost-penalty y=Gx, 3D gyroid sin x cos y + sin y cos z + sin z cos x = 0.3 in 128^3 cells on "
+            "[-pi,pi]^3, FE_Q(4) Gauss-Lobatto, gamma=0.5, x ~ U[-1,1]")
+# kernel launches of one gp_apply (face kernel, lift kernel)
+KERNELS_PER_APPLY = 2
+
+
+def config_dict(ws=1):
+    """The config object of both arms' JSON lines (identical keys and values)."""
+    return {"workload": WORKLOAD, "n_cells": 128 ** 3, "degree": 4, "n_active_dofs": 58763303,
+            "ghost_faces": 335664, "touched_dofs": 10956390,
+            "l2": "inputs larger than L2 (x, y 470 MB each in FP64); a 512 MB buffer is also written "
+                  "between timed steps",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 / FP32 FMA issue rates of a GB300 SM (flop per clock, FMA = 2) at the 2070 MHz maximum SM clock
 FP64_FLOP_PER_CLK_SM = 4
@@ -54,26 +69,31 @@ def _dist():
 
 KERNEL_SOURCES = ["paper_2503_00246_gb300/csrc/gp_kernels.cuh", "paper_2503_00246_gb300/csrc/gp_arith.cuh",
                   "paper_2503_00246_gb300/csrc/gp_launch.h", "paper_2503_00246_gb300/csrc/gp_plan.cpp"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def _traffic(tag):
-    """DRAM bytes per face-kernel launch from the committed ncu summary, or None when the
-    kernel sources changed since those counters were taken."""
+def kernel_sources_hash():
     import hashlib
-    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key):
+    """DRAM bytes (read + write) per launch of kernel `key` from the committed ncu counters
+    (profiles/traffic.json), or None when they are absent or the kernel sources changed
+    since they were taken."""
     try:
-        txt = open(os.path.join(ROOT, "profiles", "face_kernel_ball64_k3.md")).read()
-    except OSError:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
         return None
-    m = re.search(r"kernel_sources_sha256_16 = (\w+)", txt)
-    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(tag) + r"\] = (\d+)", txt)
-    if not m or not t or m.group(1) != h.hexdigest()[:16]:
+    if t.get("kernel_sources_sha256_16") != kernel_sources_hash():
         return None
-    return int(t.group(1))
+    v = t.get("traffic_bytes_per_launch", {}).get(key)
+    return int(v) if v is not None else None
 
 
 def _peaks():
@@ -174,7 +194,7 @@ def run_profile(args):
     B.build()
     from paper_2503_00246_gb300 import gp, workloads as W
     pr = WORKLOADS[args.workload](W)
-    prec = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF, "both": gp.GP_FP64_FF}[args.precision]
+    prec = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF, "all": gp.GP_FP64_FF}[args.precision]
     ctx = gp.setup_problem(pr, precision=prec, device=0)
     tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     x = torch.tensor(W.x_vectors(pr, ctx.n_active)[0], dtype=tdt, device="cuda")
@@ -403,9 +423,10 @@ def run_micro(args):
 
 def run_cg(args):
     """The solver study: gyroid (iso 0.3) on [-pi,pi]^3, n^3 cells, k = 4, model system
-    (M_active + K_active + G) u = b, b ~ U[-1,1], per-order weights gamma / (j!)^2: FP32-inner
-    defect correction and FP64 PCG, both to relative residual 1e-10 (Jacobi), float-float as
-    the FP64-accuracy operator.  The full 128^3 mesh needs ~1e5 iterations; --cg-n picks n."""
+    (M_active + K_active + G) u = b, b ~ U[-1,1], per-order weights gamma / (j!)^2, all to
+    relative residual 1e-10 with Jacobi: defect correction (FP32 inner CG, outer residuals with
+    the float-float FP64-accuracy operator), FP64 PCG with the native FP64 operator, and FP64
+    PCG with the float-float operator.  The full 128^3 mesh needs ~1e5 iterations; --cg-n picks n."""
     import torch
 
     from paper_2503_00246_gb300 import build as B
@@ -414,23 +435,154 @@ def run_cg(args):
     t0 = time.perf_counter()
     pr = W.gyroid_3d(k=4, n=args.cg_n)
     pr.weights = W.paper_weights(0.5, 4)
-    hi = gp.setup_problem(pr, precision=gp.GP_FP64_FF, device=0)
+    ff = gp.setup_problem(pr, precision=gp.GP_FP64_FF, device=0)
+    f64 = gp.setup_problem(pr, precision=gp.GP_FP64, device=0)
     lo = gp.setup_problem(pr, precision=gp.GP_FP32, device=0)
-    sysm = gp.gp_system_create(hi, lo)
-    b = torch.tensor(W.rhs_vector(pr, hi.n_active), dtype=torch.float64, device="cuda")
+    sys_ff = gp.gp_system_create(ff, lo)
+    sys_64 = gp.gp_system_create(f64, None)
+    b = torch.tensor(W.rhs_vector(pr, ff.n_active), dtype=torch.float64, device="cuda")
     u = torch.zeros_like(b)
     setup = time.perf_counter() - t0
     out = {"workload": f"{args.cg_n}^3 gyroid sin x cos y + sin y cos z + sin z cos x = 0.3 on [-pi,pi]^3, "
                        "k=4, c_j = 0.5/(j!)^2, (M_active + K_active + G) u = b, b ~ U[-1,1]",
-           "n_active_dofs": hi.n_active, "ghost_faces": hi.n_faces, "setup_s": setup}
-    for name, mode in (("defect_correction_fp32_inner", 0), ("pcg_fp64", 1)):
+           "n_active_dofs": ff.n_active, "ghost_faces": ff.n_faces, "setup_s": setup}
+    runs = (("defect_correction_fp32_inner", sys_ff, 0), ("pcg_fp64_native", sys_64, 1), ("pcg_fp64", sys_ff, 1))
+    for name, sysm, mode in runs:
+        if args.cg_only and name not in args.cg_only.split(","):
+            continue
         torch.cuda.nvtx.range_push(name)        # ncu --nvtx --nvtx-include "<name>/" picks one solver
         st = gp.gp_system_solve(sysm, b, u, rtol=1e-10, inner_rtol=args.inner_rtol, mode=mode,
                                 max_outer=args.max_outer, max_inner=args.max_inner)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         out[name] = st
+        print(json.dumps({name: st}), file=sys.stderr, flush=True)
+    out["operators"] = {"defect_correction_fp32_inner": "FP32 inner CG; outer residual with the float-float operator",
+                        "pcg_fp64_native": "FP64 PCG, native FP64 operator (FP64 pipe)",
+                        "pcg_fp64": "FP64 PCG, float-float FP64-accuracy operator"}
     print(json.dumps(out), flush=True)
+
+
+def _sampled_error(o, x_np, y_dev, prec, nrows, seed=12):
+    """max |y - y_ref| / max |y_ref| on sampled rows (random rows plus the patches of random
+    faces of every axis), with the oracle's apply_rows: the check at sizes where a full oracle
+    apply is too slow."""
+    rng = np.random.default_rng(seed)
+    touched = [o.patch_index(a)[rng.integers(0, o.faces[a].shape[0], 40)].ravel()
+               for a in range(o.pr.dim) if o.faces[a].shape[0] > 0]
+    rows = np.unique(np.concatenate([rng.integers(0, o.n_active, nrows)] + touched))
+    xin = x_np if prec != 1 else x_np.astype(np.float32).astype(np.float64)
+    ref = o.apply_rows(xin, rows)
+    y = y_dev[rows].double().cpu().numpy()
+    return float(np.abs(y - ref).max() / np.abs(ref).max())
+
+
+def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tune=True, steps=None):
+    """One arithmetic form of y = G x on one workload: device time per apply (CUDA events on
+    the launching stream around each apply, L2 flushed between applies), the per-kernel split
+    (separate traced applies), end to end through gp_apply_host, and the error against the
+    oracle on sampled rows (when o is given)."""
+    stream = torch.cuda.current_stream()
+    steps = args.steps if steps is None else steps
+    ctx = gp.setup_problem(pr, precision=prec, device=dev.index or 0)
+    tiles = None
+    if tune and args.tune_reps > 0:          # tile shape picked on this GPU, before any timing
+        chosen, (tf, tl) = gp.gp_autotune(ctx, args.tune_reps)
+        tiles = {"chosen": chosen, "face_ms": tf, "lift_ms": tl}
+    tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
+    x_np = W.x_vectors(pr, ctx.n_active)[0]
+    x = torch.tensor(x_np, dtype=tdt, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        gp.gp_apply(ctx, x, y)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    t0 = time.perf_counter()
+    for i in range(steps):
+        flush.fill_(float(i))                 # evict x, y and the tables from L2
+        ev[i][0].record(stream)
+        gp.gp_apply(ctx, x, y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    t_step = sum(a.elapsed_time(b) for a, b in ev) / steps   # ms
+    # per-kernel split: the same flushed applies with the library's event tracing (an event
+    # between the two kernels gives up their overlap)
+    gp.gp_profile_enable(ctx, True)
+    for i in range(min(steps, 200)):
+        flush.fill_(float(i))
+        gp.gp_apply(ctx, x, y)
+    torch.cuda.synchronize()
+    ms_face, ms_lift, calls = gp.gp_profile_read(ctx)
+    gp.gp_profile_enable(ctx, False)
+    err = _sampled_error(o, x_np, y, prec, args.check_rows) if (o is not None and args.check) else None
+    rec = {"ctx_sizes": (ctx.n_active, ctx.n_faces, ctx.n_touched), "t_step": t_step,
+           "wall_ms_per_step": wall * 1e3 / steps, "face_ms": ms_face / calls, "lift_ms": ms_lift / calls,
+           "tiles": tiles, "rel_err_vs_oracle": err}
+    if e2e:
+        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+        xh = torch.tensor(x_np, dtype=tdt).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for _ in range(2):
+            gp.gp_apply_host(ctx, xh, yh, stream)
+        ne = max(3, min(10, steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ne):
+            gp.gp_apply_host(ctx, xh, yh, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rec["t_e2e"] = e0.elapsed_time(e1) / ne
+        rec["h2d"] = rec["d2h"] = xh.numel() * xh.element_size()
+        del xh, yh
+    ctx.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return rec
+
+
+def form_summary(rec, pr, prec, gp, hbm, peak_src, ws=1):
+    """GDoF/s, ghost faces/s, the apply's algorithmic HBM fraction and the face kernel's
+    roofline (ALU: executed flops over its traced time) of one measured form."""
+    n_active, nf, n_touched = rec["ctx_sizes"]
+    d, k = pr.dim, pr.degree
+    w = 4 if prec == gp.GP_FP32 else 8
+    t = rec["t_step"]
+    fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: fp32_peak / FF_OPS_PER_FMA}[prec]
+    kname = {gp.GP_FP64: "double", gp.GP_FP32: "float", gp.GP_FP64_FF: "ff64"}[prec]
+    flop_face = _flops_face(d, k, nf)
+    roof = {"bound": "alu", "kernel": f"face_kernel<{d},{k},{kname}>",
+            "achieved": flop_face / (rec["face_ms"] * 1e-3) / 1e12 if rec["face_ms"] > 0 else None,
+            "unit": "TFLOP/s", "peak": peak,
+            "peak_source": {gp.GP_FP64: "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz x 2 flop",
+                            gp.GP_FP32: "derived: 152 SM x 128 FP32 FMA/clk x 2070 MHz x 2 flop",
+                            gp.GP_FP64_FF: "derived: FP32 peak / 12 FP32 ops per compensated float-float "
+                                           "multiply-add"}[prec]}
+    roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
+    roof["traffic"] = _traffic(f"face_kernel_{kname}_d{d}k{k}")
+    alg = w * (n_touched + n_active)
+    out = {"value": ws * n_active / (t * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": t,
+           "wall_ms_per_step": rec["wall_ms_per_step"],
+           "ghost_faces_per_s": ws * nf / (t * 1e-3),
+           "kernel_ms": {"face": rec["face_ms"], "lift": rec["lift_ms"]},
+           "apply_hbm": {"achieved": alg / (t * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (t * 1e-3) / 1e9 / hbm, "peak_source": peak_src,
+                         "algorithmic_bytes": alg,
+                         "bytes": f"{w} B x (touched DoFs {n_touched} read + active DoFs {n_active} written)"},
+           "roofline": roof,
+           "paper_flop_rate": {"tflops": _flops_paper(d, k, nf) / (t * 1e-3) / 1e12,
+                               "count": "2[(k+1)^(d-1) (2k+1)^2 + (d-1) (k+1)^d (2k+1)] per face over the apply time"},
+           "rel_err_vs_oracle": rec["rel_err_vs_oracle"], "tiles": rec["tiles"],
+           "n_active": n_active, "n_faces": nf, "n_touched": n_touched}
+    if "t_e2e" in rec:
+        out["e2e"] = {"value": ws * n_active / (rec["t_e2e"] * 1e-3) / 1e9, "unit": "GDoF/s",
+                      "h2d_bytes_per_step": rec["h2d"], "d2h_bytes_per_step": rec["d2h"]}
+    return out
 
 
 def run_gpu(args):
@@ -446,132 +598,35 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pr = W.ball_3d()
-    forms = {}
+    pr = W.gyroid_3d()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
     peaks, peak_src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
-    fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
-    ff_peak = fp32_peak / FF_OPS_PER_FMA
     clocks = Clocks(local)
+    o = None
+    if args.check:
+        from oracle.ghost_penalty import Oracle
+        o = Oracle(pr)
 
-    results = {}
     names = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF}
-    precs = ([gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32] if args.precision == "both" else [names[args.precision]])
+    precs = [gp.GP_FP64, gp.GP_FP32, gp.GP_FP64_FF] if args.precision == "all" else [names[args.precision]]
+    head = precs[0]
+    recs = {}
     for prec in precs:
-        ctx = gp.setup_problem(pr, precision=prec, device=local)
-        tiles = None
-        if args.tune_reps > 0:          # tile shape picked on this GPU, before any timing
-            default = gp.gp_get_tiles(ctx)
-            chosen, (tf, tl) = gp.gp_autotune(ctx, args.tune_reps)
-            tiles = {"default": default, "chosen": chosen, "face_ms": tf, "lift_ms": tl}
-        w = 4 if prec == gp.GP_FP32 else 8
-        tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
-        x_np = W.x_vectors(pr, ctx.n_active)[0]
-        x = torch.tensor(x_np, dtype=tdt, device=dev)
-        y = torch.empty_like(x)
-        for _ in range(args.warmup):
-            gp.gp_apply(ctx, x, y)
-        torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        if prec == precs[0]:
+        if prec == head:
             clocks.start()
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))                 # evict x, y and the tables from L2
-            ev[i][0].record(stream)
-            gp.gp_apply(ctx, x, y)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        torch.cuda.nvtx.range_pop()
+        recs[prec] = measure_form(gp, W, torch, pr, prec, dev, args, flush, o=o)
+        if prec == head:
+            ck = clocks.stop()
         if ws > 1:
-            dist.barrier()
-        ck = clocks.stop() if prec == precs[0] else None
-        # per-kernel split: the same flushed steps with the library's event tracing, which puts
-        # an event between the face and lift kernels (and so gives up their overlap)
-        gp.gp_profile_enable(ctx, True)
-        for i in range(min(args.steps, 500)):
-            flush.fill_(float(i))
-            gp.gp_apply(ctx, x, y)
-        torch.cuda.synchronize()
-        ms_jump, ms_lift, calls = gp.gp_profile_read(ctx)
-        gp.gp_profile_enable(ctx, False)
-        t_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps   # ms
-        t_max = t_step
-        if ws > 1:
-            tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+            tt = torch.tensor([recs[prec]["t_step"]], device=dev, dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_max = float(tt.item())
-        d, k, nf = pr.dim, pr.degree, ctx.n_faces
-        jump_ms = ms_jump / calls
-        lift_ms = ms_lift / calls
-        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-        xh = torch.tensor(x_np, dtype=tdt).pin_memory()
-        yh = torch.empty_like(xh).pin_memory()
-        for _ in range(max(3, args.warmup // 4)):
-            gp.gp_apply_host(ctx, xh, yh, stream)
-        ne = max(10, args.steps // 10)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(ne):
-            gp.gp_apply_host(ctx, xh, yh, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_e2e = e0.elapsed_time(e1) / ne
-        # accuracy of this very output against the oracle (outside every timed region)
-        err = None
-        if args.check:
-            from oracle.ghost_penalty import Oracle
-            o = Oracle(pr)
-            ref = o.apply(x_np if prec != gp.GP_FP32 else x_np.astype(np.float32).astype(np.float64))
-            err = float(np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref))
-        flop_face = _flops_face(d, k, nf)
-        kname = {gp.GP_FP64: "double", gp.GP_FP32: "float", gp.GP_FP64_FF: "ff64"}[prec]
-        roof = {"bound": "alu", "kernel": f"face_kernel<3,3,{kname}>",
-                "achieved": flop_face / (jump_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                "peak": {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: ff_peak}[prec],
-                "peak_source": {gp.GP_FP64: "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz x 2 flop",
-                                gp.GP_FP32: "derived: 152 SM x 128 FP32 FMA/clk x 2070 MHz x 2 flop",
-                                gp.GP_FP64_FF: "derived: FP32 peak / 12 FP32 ops per compensated float-float multiply-add"}[prec]}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = _traffic({gp.GP_FP64: "f64", gp.GP_FP32: "f32", gp.GP_FP64_FF: "ff64"}[prec])
-        alg_bytes = w * (ctx.n_touched + ctx.n_active)
-        results[prec] = {
-            "value": ws * ctx.n_active / (t_max * 1e-3) / 1e9,
-            "ghost_faces_per_s": ws * ctx.n_faces / (t_max * 1e-3),
-            "ms_per_step": t_max,
-            "wall_ms_per_step": wall * 1e3 / args.steps,
-            "kernel_ms": {"jump": jump_ms, "lift": lift_ms},
-            "apply_hbm_gbs": alg_bytes / (t_step * 1e-3) / 1e9,
-            "apply_hbm_frac": alg_bytes / (t_step * 1e-3) / 1e9 / hbm,
-            "lift_hbm_gbs": w * ctx.n_active / (lift_ms * 1e-3) / 1e9,
-            "roofline": roof,
-            "e2e_ms": t_e2e,
-            "e2e_value": ws * ctx.n_active / (t_e2e * 1e-3) / 1e9,
-            "h2d": w * ctx.n_active, "d2h": w * ctx.n_active,
-            "rel_err_vs_oracle": err,
-            "clocks": ck,
-            "n_active": ctx.n_active, "n_faces": nf, "n_touched": ctx.n_touched,
-            "paper_flops_per_step": _flops_paper(d, k, nf),
-            "paper_flop_rate": {"tflops": _flops_paper(d, k, nf) / (jump_ms * 1e-3) / 1e12,
-                                "flops_per_face": _flops_paper(d, k, 1),
-                                "count": "the paper's per-face count 2[(k+1)^(d-1) (2k+1)^2 + (d-1) (k+1)^d (2k+1)] "
-                                         "over the face kernel's time"},
-            "tiles": tiles,
-        }
-        ctx.close()
-
-    order = [p for p in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32) if p in results]
-    head = order[0]
-    r = results[head]
+            recs[prec]["t_step"] = float(tt.item())
+    forms = {p: form_summary(recs[p], pr, p, gp, hbm, peak_src, ws) for p in precs}
+    r = forms[head]
+    tags = {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff64"}
     dtypes = {gp.GP_FP64: "f64", gp.GP_FP32: "f32", gp.GP_FP64_FF: "ff64 (float-float arithmetic on f64 data)"}
     line = {
         "metric": METRIC,
@@ -586,41 +641,60 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": dtypes[head],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_cells": 64 ** 3, "degree": 3, "n_active_dofs": r["n_active"],
-                   "ghost_faces": r["n_faces"], "touched_dofs": r["n_touched"],
-                   "l2": "512 MB buffer written between timed steps (inputs < L2)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "config": config_dict(ws),
         "roofline": r["roofline"],
-        "e2e": {"value": r["e2e_value"], "unit": "GDoF/s", "h2d_bytes_per_step": r["h2d"],
-                "d2h_bytes_per_step": r["d2h"]},
-        "gpu_launches": 2 * args.steps,
-        "clocks": r["clocks"],
-        "apply_hbm": {"achieved": r["apply_hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": r["apply_hbm_frac"],
-                      "peak_source": peak_src},
+        "e2e": r["e2e"],
+        "gpu_launches": KERNELS_PER_APPLY * args.steps,
+        "clocks": ck,
+        "apply_hbm": r["apply_hbm"],
         "kernel_ms": r["kernel_ms"],
         "ghost_faces_per_s": r["ghost_faces_per_s"],
         "paper_flop_rate": r["paper_flop_rate"],
-        "tiles": r["tiles"],
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
+        "tiles": r["tiles"],
+        "forms": {tags[p]: {k2: forms[p][k2] for k2 in ("value", "ms_per_step", "kernel_ms", "apply_hbm", "roofline",
+                                                      "rel_err_vs_oracle", "e2e", "ghost_faces_per_s", "tiles")}
+                  for p in precs},
+        "error_check": f"max |y - y_ref| / max |y_ref| over ~{args.check_rows} sampled rows plus the patches of "
+                       "sampled faces, FP64 oracle (explicit face matrices); FP32 against the oracle applied to x "
+                       "rounded to FP32; targets 1e-12 (FP64, float-float) and 1e-5 (FP32)",
     }
-    tags = {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff64"}
-    for p in order[1:]:
-        f = results[p]
-        line[tags[p]] = {k2: f[k2] for k2 in ("value", "ms_per_step", "kernel_ms", "roofline", "apply_hbm_gbs",
-                                              "apply_hbm_frac", "rel_err_vs_oracle", "e2e_value", "tiles",
-                                              "ghost_faces_per_s", "paper_flop_rate")}
+    if not args.no_sweep:
+        line["sweep_96"] = run_sweep_record(gp, W, torch, dev, args, flush, hbm, peak_src)
     if not args.no_batched:
         line["batched"] = {tags[p]: run_batched(gp, W, torch, dev, p, args.batched_steps, 2, args.tune_reps)
-                           for p in (gp.GP_FP64_FF, gp.GP_FP64, gp.GP_FP32)}
+                           for p in (gp.GP_FP64, gp.GP_FP32, gp.GP_FP64_FF)}
         line["batched"]["workload"] = ("64 independent 3D balls on [-1,1]^3, n ~ U{16..96}, k ~ U{2..6}, "
                                        "r ~ U[0.4,0.8], 4 right-hand sides, one CUDA graph per apply")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, o)
         line["cpu_paper_like"] = cpu_kronecker(args.cpu_seconds / 2)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_sweep_record(gp, W, torch, dev, args, flush, hbm, peak_src):
+    """The degree sweep at its stated size, bounded: 96^3 ball, k = 1..8, each form timed over
+    a few flushed applies (tiles tuned first), with sampled-row errors for k <= --sweep-check-kmax."""
+    from oracle.ghost_penalty import Oracle
+    out = {"workload": "96^3 cells on [-1,1]^3, ball r = 0.7 (seeded centre offset), gamma = 0.5, x ~ U[-1,1]",
+           "steps_per_form": args.sweep_steps, "k": {}}
+    tags = {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff64"}
+    for k in range(1, 9):
+        pr = W.ball_3d_sweep(k)
+        o = Oracle(pr) if (args.check and k <= args.sweep_check_kmax) else None
+        rec = {}
+        for prec in (gp.GP_FP64, gp.GP_FP32, gp.GP_FP64_FF):
+            m = measure_form(gp, W, torch, pr, prec, dev, args, flush, o=o, e2e=False, steps=args.sweep_steps)
+            f = form_summary(m, pr, prec, gp, hbm, peak_src)
+            rec[tags[prec]] = {"gdofs": f["value"], "ms": f["ms_per_step"], "apply_hbm_frac": f["apply_hbm"]["frac"],
+                               "face_alu_frac": f["roofline"]["frac"], "rel_err_vs_oracle": f["rel_err_vs_oracle"]}
+            rec["n_active"], rec["n_faces"] = f["n_active"], f["n_faces"]
+        out["k"][str(k)] = rec
+        print(json.dumps({"sweep_k": k, **rec}), file=sys.stderr, flush=True)
+    return out
 
 
 # ---------------------------------------------------------------- CPU arm --
@@ -632,97 +706,102 @@ def _cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(seconds: float):
-    """The oracle, as it stands, on the host cores: full applies for about `seconds`."""
+def _oracle_sample(o, frac):
+    """The first ceil(frac * n_a) faces of every axis, and one oracle step over them: the
+    explicit face matrices applied to the gathered patches, scattered with bincount."""
+    sub = {}
+    for a in range(o.pr.dim):
+        nfa = o.faces[a].shape[0]
+        if nfa:
+            sub[a] = o.patch_index(a)[: max(1, int(math.ceil(frac * nfa)))]
+    nsub = sum(v.shape[0] for v in sub.values())
+
+    def step(x):
+        y = np.zeros(o.n_active)
+        for a, idx in sub.items():
+            yf = x[idx] @ o.A(a).T
+            y += np.bincount(idx.ravel(), weights=yf.ravel(), minlength=o.n_active)
+        return y
+    return step, nsub
+
+
+def _headline_oracle(o=None):
     from oracle.ghost_penalty import Oracle
     from paper_2503_00246_gb300 import workloads as W
-    pr = W.ball_3d()
-    o = Oracle(pr)
+    pr = W.gyroid_3d()
+    if o is None:
+        o = Oracle(pr)
     x = W.x_vectors(pr, o.n_active)[0]
     for a in range(pr.dim):
         o.patch_index(a)
         o.A(a)
+    return o, x
+
+
+def cpu_baseline(seconds: float, o=None):
+    """The oracle, as it stands, on the host cores: full applies of the headline workload
+    for about `seconds` (at least one)."""
+    o, x = _headline_oracle(o)
     o.apply(x)
     reps, t0 = 0, time.perf_counter()
     while True:
         o.apply(x)
         reps += 1
         el = time.perf_counter() - t0
-        if el >= seconds and reps >= 3:
+        if el >= seconds and reps >= 1:
             break
     t = el / reps
+    P = 9 * 25
     return {"value": o.n_active / t / 1e9, "unit": "GDoF/s", "cores": _cores(), "kind": "oracle",
-            "sample": f"{reps} full applies of the 64^3 k=3 workload ({o.n_faces} faces, explicit "
-                      f"{(2 * 3 + 1) * 16}x{(2 * 3 + 1) * 16} face matrices, numpy FP64), {el:.1f} s"}
+            "sample": f"{reps} full applies of the 128^3 gyroid k=4 workload ({o.n_faces} faces, explicit "
+                      f"{P}x{P} face matrices, numpy FP64), {el:.1f} s"}
 
 
-def cpu_kronecker(seconds: float):
+def cpu_kronecker(seconds: float, o=None):
     """The paper-like CPU baseline: the factorised (Kronecker) face operator of the paper
-    in C with OpenMP over faces, FP64 (oracle/kron_cpu.c), full applies for about `seconds`."""
-    from oracle.cpu_kronecker import KroneckerOpenMP
-    from oracle.ghost_penalty import Oracle
-    from paper_2503_00246_gb300 import workloads as W
-    pr = W.ball_3d()
-    o = Oracle(pr)
-    kc = KroneckerOpenMP(pr, o)
-    x = W.x_vectors(pr, o.n_active)[0]
+    in C with OpenMP over faces, FP64 (baselines/kron_cpu.c), full applies of the headline
+    workload for about `seconds` (at least one)."""
+    from baselines.cpu_kronecker import KroneckerOpenMP
+    o, x = _headline_oracle(o)
+    kc = KroneckerOpenMP(o.pr, o)
     kc.apply(x)
     reps, t0 = 0, time.perf_counter()
     while True:
         kc.apply(x)
         reps += 1
         el = time.perf_counter() - t0
-        if el >= seconds and reps >= 3:
+        if el >= seconds and reps >= 1:
             break
     t = el / reps
     return {"value": o.n_active / t / 1e9, "unit": "GDoF/s", "cores": kc.nthreads,
             "kind": "paper-like CPU (Kronecker form of the face operator, C + OpenMP over faces, FP64)",
-            "sample": f"{reps} full applies of the 64^3 k=3 workload, {el:.1f} s"}
+            "sample": f"{reps} full applies of the 128^3 gyroid k=4 workload, {el:.1f} s"}
 
 
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    from oracle.ghost_penalty import Oracle
-    from paper_2503_00246_gb300 import workloads as W
-    pr = W.ball_3d()
-    o = Oracle(pr)
-    x = W.x_vectors(pr, o.n_active)[0]
-    for a in range(pr.dim):
-        o.patch_index(a)
-        o.A(a)
+    o, x = _headline_oracle()
     t0 = time.perf_counter()
     o.apply(x)
     t_full = time.perf_counter() - t0
     # each step is a bounded sample: a fixed fraction of the faces, so the whole run takes ~60 s
     budget = 60.0
     frac = min(1.0, budget / max(1, args.steps + args.warmup) / t_full)
-    sub = {}
-    for a in range(pr.dim):
-        nfa = o.faces[a].shape[0]
-        sub[a] = o.patch_index(a)[: max(1, int(math.ceil(frac * nfa)))]
-    nsub = sum(v.shape[0] for v in sub.values())
+    step, nsub = _oracle_sample(o, frac)
     frac_eff = nsub / o.n_faces
-
-    def step():
-        y = np.zeros(o.n_active)
-        for a, idx in sub.items():
-            yf = x[idx] @ o.A(a).T
-            y += np.bincount(idx.ravel(), weights=yf.ravel(), minlength=o.n_active)
-        return y
-
     for _ in range(args.warmup):
-        step()
+        step(x)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        step(x)
     t = (time.perf_counter() - t0) / args.steps
     value = frac_eff * o.n_active / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_fraction_of_faces": frac_eff},
+            "config": config_dict(ws),
             "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": _cores(), "kind": "oracle",
                              "sample": f"{nsub} of {o.n_faces} faces per step (explicit face matrices, numpy FP64); "
                                        f"DoF throughput scaled by that fraction"},
@@ -734,10 +813,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
-    ap.add_argument("--precision", default="both", choices=["fp64", "fp32", "ff", "both"])
+    ap.add_argument("--precision", default="all", choices=["fp64", "fp32", "ff", "all"])
+    ap.add_argument("--check-rows", type=int, default=2000, help="sampled rows of the oracle error check")
+    ap.add_argument("--no-sweep", action="store_true", help="leave out the bounded 96^3 degree sweep")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
@@ -745,12 +826,13 @@ def main():
     ap.add_argument("--micro-reps", type=int, default=200)
     ap.add_argument("--sweep-k", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--sweep-workloads", default="", help="comma-separated workload names instead of --sweep-k")
-    ap.add_argument("--sweep-steps", type=int, default=50)
-    ap.add_argument("--sweep-check-kmax", type=int, default=5)
+    ap.add_argument("--sweep-steps", type=int, default=10)
+    ap.add_argument("--sweep-check-kmax", type=int, default=4)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--max-inner", type=int, default=200000)
     ap.add_argument("--max-outer", type=int, default=50)
     ap.add_argument("--cg-n", type=int, default=32)
+    ap.add_argument("--cg-only", default="", help="comma-separated solver names of --mode cg to run")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--workload", default="ball64_k3", choices=sorted(WORKLOADS))

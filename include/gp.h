@@ -56,8 +56,17 @@ typedef enum {
 /* Arithmetic of the operator.  GP_FP64: x, y double, FP64 arithmetic.
  * GP_FP32: x, y float, FP32 arithmetic.  GP_FP64_FF: x, y double, computed in
  * float-float pairs (hi + lo, about 2^-48 relative per operation) on the FP32
- * pipes; entries of x must lie in the float exponent range (|x| below 2^-126
- * reads as 0, at or above 2^128 as infinity). */
+ * pipes.  The pairs have the exponent range of float, not of double:
+ *   - FP64-level accuracy (1e-12 relative to the largest output) holds when every
+ *     non-zero |x_i| lies in [2^-97, 2^127) and every output |y_i| stays below
+ *     2^127 (about 1.7e38);
+ *   - an entry with 2^-126 <= |x_i| < 2^-97 keeps only its leading 24 bits (the
+ *     low float would be subnormal), |x_i| < 2^-126 reads as 0, and |x_i| >= 2^128
+ *     reads as infinity (y is then not finite on the DoFs its faces reach);
+ *   - the operator is linear: scale x by a power of two into that range (and y
+ *     back) when the data lie outside it, or use GP_FP64.
+ * gp_setup refuses (GP_EINVAL) a GP_FP64_FF context whose per-order scale factors
+ * c_j h^(d-2) lie outside [2^-90, 2^90]. */
 enum { GP_FP64 = 0, GP_FP32 = 1, GP_FP64_FF = 2 };
 
 /* level-set kinds; phi > 0 inside the domain (Sec. 2) */
@@ -105,6 +114,9 @@ typedef struct {
                                partition of cell layers [part_lo, part_hi) along the last
                                axis (y in 2D, z in 3D); see gp_partition_info */
   int stabilization;        /* GP_STAB_GHOST (0, the ghost penalty) or GP_STAB_MACRO */
+  int no_scratch;           /* 1: allocate no face-output scratch; only gp_apply_noalloc can
+                               apply the context (the other applies, the autotuner, batches and
+                               the model system return GP_EINVAL) */
 } gp_opts;
 
 /* Stabilisations.  GP_STAB_MACRO is the macro-patch alternative the paper names next to the
@@ -246,7 +258,12 @@ gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream);
  *   - The scratch must hold n_faces * (2k+1) * (k+1)^(d-1) values (4 bytes for
  *     GP_FP32, 8 otherwise); larger problems get GP_EINVAL and a message.
  *   - The first call on a device looks the array's device address up with
- *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *     cudaGetSymbolAddress and keeps it for the life of the process; make that
+ *     first call before any stream capture.  A device reset (cudaDeviceReset)
+ *     invalidates the kept address: do not call gp_apply_noalloc after one.
+ *   - A context created with gp_opts.no_scratch = 1 holds no face-output buffer
+ *     of its own, so that a caller who only uses this entry point pays for no
+ *     device allocation beyond the plan's tables.
  *   - All calls share the array and it keeps the last call's contents (every
  *     value the operator reads is rewritten first, so nothing needs clearing);
  *     calls whose kernels overlap on the GPU race on it.
@@ -259,12 +276,19 @@ gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream);
  * for completion.  Uses device buffers owned by the context. */
 gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* stream);
 
-/* Several independent problems, nrhs right-hand sides each:
- * x[p] and y[p] point to nrhs contiguous vectors of n_active(p) elements
- * (layout [nrhs][n_active]).  All contexts must share one precision and
- * device.  y[p] is overwritten. */
+/* Several independent problems, nrhs right-hand sides each (the batched workload
+ * of many meshes of uneven n, k and geometry): x[p] and y[p] point to nrhs
+ * contiguous vectors of n_active(p) elements (layout [nrhs][n_active]).  All
+ * contexts must share one precision and device.  y[p] is overwritten.
+ * The first call with a given list of contexts and nrhs builds a gp_batch for it
+ * (gp_batch_create below: device allocations and a CUDA graph capture, so make
+ * that first call outside any stream capture) and keeps it until one of the
+ * contexts is destroyed; every call then replays that batch's graph once
+ * (gp_batch_apply).  gp_apply_batched_info returns the number of graph replays
+ * made so far for the list (GP_EINVAL if it was never applied). */
 gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs,
                            const void* const* x, void* const* y, void* stream);
+gp_status gp_apply_batched_info(gp_ctx* const* ctxs, int nprob, int nrhs, int64_t* graph_launches);
 
 /* Kernel tracing.  While enabled, every apply on ctx records CUDA events on
  * its stream before the jump kernel, between the two kernels and after the

@@ -1,6 +1,8 @@
 // C ABI of the ghost-penalty operator (declarations and contracts in gp.h).
+#include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <tuple>
@@ -70,6 +72,8 @@ void free_device(gp_ctx* c) {
 gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace,
                       const gp::Tiles* tiles, int which) {
   const gp::Plan& p = c->plan;
+  if (!scratch && !c->d_tp && p.num_faces() > 0)
+    return fail(c, GP_EINVAL, "the context was created with no_scratch = 1: only gp_apply_noalloc can apply it");
   gp::ApplyArgs a;
   a.dim = p.dim;
   a.k = p.k;
@@ -113,6 +117,15 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return GP_OK;
 }
+
+// gp_apply_batched's batches, one per (contexts, nrhs) list; gp_destroy drops those of a context
+struct BatchedKey {
+  std::vector<gp_ctx*> ctxs;
+  int nrhs;
+  bool operator<(const BatchedKey& o) const { return nrhs != o.nrhs ? nrhs < o.nrhs : ctxs < o.ctxs; }
+};
+std::mutex g_batched_mu;
+std::map<BatchedKey, gp_batch*> g_batched;
 
 namespace {
 using gpi::launch;
@@ -173,7 +186,7 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     // face outputs W_F: float, double, or a (hi, lo) float pair per value
     const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
     const size_t tp_bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
-    if (e == cudaSuccess && tp_bytes > 0) e = cudaMalloc(&c->d_tp, tp_bytes);
+    if (e == cudaSuccess && tp_bytes > 0 && !opts->no_scratch) e = cudaMalloc(&c->d_tp, tp_bytes);
     if (e != cudaSuccess) {
       std::string m = std::string("device setup: ") + cudaGetErrorString(e);
       free_device(c);
@@ -189,6 +202,18 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
 
 void gp_destroy(gp_ctx* ctx) {
   if (!ctx) return;
+  {
+    // release the cached gp_apply_batched batches that hold this context
+    std::lock_guard<std::mutex> lock(g_batched_mu);
+    for (auto it = g_batched.begin(); it != g_batched.end();) {
+      if (std::find(it->first.ctxs.begin(), it->first.ctxs.end(), ctx) != it->first.ctxs.end()) {
+        gp_batch_destroy(it->second);
+        it = g_batched.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
   if (ctx->on_device) {
     DeviceGuard g(ctx->device);
     free_device(ctx);
@@ -361,35 +386,6 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
   return GP_OK;
 }
 
-gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs, const void* const* x,
-                           void* const* y, void* stream) {
-  if (nprob < 0 || nrhs < 1 || (nprob > 0 && (!ctxs || !x || !y)))
-    return fail(nullptr, GP_EINVAL, "bad batched arguments");
-  if (nprob == 0) return GP_OK;
-  const int prec = ctxs[0] ? ctxs[0]->plan.precision : -1;
-  const int dev = ctxs[0] ? ctxs[0]->device : -1;
-  for (int p = 0; p < nprob; ++p) {
-    gp_status s = check_apply(ctxs[p], x[p], y[p]);
-    if (s != GP_OK) return fail(nullptr, s, std::string("problem ") + std::to_string(p) + ": " + ctxs[p]->err);
-    if (ctxs[p]->plan.precision != prec || ctxs[p]->device != dev)
-      return fail(nullptr, GP_EINVAL, "all contexts must share precision and device");
-  }
-  DeviceGuard g(dev);
-  if (!g.ok) return fail(nullptr, GP_ECUDA, "cudaSetDevice failed");
-  for (int p = 0; p < nprob; ++p) {
-    gp_ctx* c = ctxs[p];
-    const int64_t n = c->plan.n_active;
-    if (n == 0) continue;
-    for (int r = 0; r < nrhs; ++r) {
-      const char* xp = (const char*)x[p] + (size_t)r * n * c->elem;
-      char* yp = (char*)y[p] + (size_t)r * n * c->elem;
-      gp_status s = launch(c, xp, yp, 0, (cudaStream_t)stream);
-      if (s != GP_OK) return fail(nullptr, s, c->err);
-    }
-  }
-  return GP_OK;
-}
-
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches --
@@ -416,6 +412,7 @@ struct gp_batch {
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool pending[2] = {false, false};
   int slot = 0;
+  int64_t launches = 0;   // graph replays made through gp_apply_batched
   std::string err;
 };
 
@@ -608,6 +605,53 @@ void gp_batch_destroy(gp_batch* b) {
   DeviceGuard dg(b->device);
   batch_free(b);
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------- gp_apply_batched (cached batches) --
+extern "C" {
+
+gp_status gp_apply_batched(gp_ctx* const* ctxs, int nprob, int nrhs, const void* const* x,
+                           void* const* y, void* stream) {
+  if (nprob < 0 || nrhs < 1 || (nprob > 0 && (!ctxs || !x || !y)))
+    return fail(nullptr, GP_EINVAL, "bad batched arguments");
+  if (nprob == 0) return GP_OK;
+  const int prec = ctxs[0] ? ctxs[0]->plan.precision : -1;
+  const int dev = ctxs[0] ? ctxs[0]->device : -1;
+  for (int p = 0; p < nprob; ++p) {
+    gp_status s = check_apply(ctxs[p], x[p], y[p]);
+    if (s != GP_OK) return fail(nullptr, s, std::string("problem ") + std::to_string(p) + ": " +
+                                               (ctxs[p] ? ctxs[p]->err : std::string("null context")));
+    if (ctxs[p]->plan.precision != prec || ctxs[p]->device != dev)
+      return fail(nullptr, GP_EINVAL, "all contexts must share precision and device");
+  }
+  // the graph-replayed batch of this (contexts, nrhs) list: built on the first call, replayed after
+  gp_batch* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_batched_mu);
+    const BatchedKey key{std::vector<gp_ctx*>(ctxs, ctxs + nprob), nrhs};
+    auto it = g_batched.find(key);
+    if (it != g_batched.end()) {
+      b = it->second;
+    } else {
+      const gp_status s = gp_batch_create(ctxs, nprob, nrhs, &b);
+      if (s != GP_OK) return s;
+      g_batched[key] = b;
+    }
+  }
+  gp_status s = gp_batch_apply(b, x, y, stream);
+  if (s == GP_OK) b->launches++;
+  return s;
+}
+
+gp_status gp_apply_batched_info(gp_ctx* const* ctxs, int nprob, int nrhs, int64_t* graph_launches) {
+  if (!graph_launches || nprob < 1 || !ctxs) return fail(nullptr, GP_EINVAL, "bad arguments");
+  std::lock_guard<std::mutex> lock(g_batched_mu);
+  auto it = g_batched.find(BatchedKey{std::vector<gp_ctx*>(ctxs, ctxs + nprob), nrhs});
+  if (it == g_batched.end()) return fail(nullptr, GP_EINVAL, "no batch of these contexts has been applied");
+  *graph_launches = it->second->launches;
+  return GP_OK;
 }
 
 }  // extern "C"

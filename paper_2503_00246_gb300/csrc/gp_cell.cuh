@@ -432,7 +432,7 @@ inline int gather_blocks(const CellTabs& ct) {
 // y (+)= (wm M_active + ws K_active) x: the cell kernel, then the gather (add = 1: onto y).
 template <int D, int K, class A>
 cudaError_t run_cells(const void* x, void* y, const CellTabs& ct, const double* m, const double* s, double h,
-                      double wm, double ws, int add, cudaStream_t st) {
+                      double wm, double ws, int add, int first, cudaStream_t st) {
   using S = CellShape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
@@ -462,9 +462,12 @@ cudaError_t run_cells(const void* x, void* y, const CellTabs& ct, const double* 
   cfg.blockDim = dim3((unsigned)S::NT);
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  // the cell kernel loads x before its dependency wait: as the first kernel of a call it runs
+  // only after everything earlier on the stream has completed
+  cfg.numAttrs = first ? 0 : 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, cell_kernel<D, K, A>, (const IO*)x, (V*)ct.wc, ct.crow, ct.ncact, c);
   if (e != cudaSuccess) return e;
+  cfg.numAttrs = 1;
   const int64_t rows = (int64_t)ct.ncown * S::KR;
   if (rows > 0) {
     cfg.gridDim = dim3((unsigned)gather_blocks<D, K>(ct));

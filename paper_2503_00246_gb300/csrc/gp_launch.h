@@ -273,9 +273,12 @@ BatchOps batch_ops_ff_d3();
   return ops;
 
 // y (+)= (wm M_active + ws K_active) x over the active cells (cell kernel + gather; add = 1:
-// onto y, 0: overwrite the nodes of active cells).
+// onto y, 0: overwrite the nodes of active cells).  first = 1: the cell kernel is the first
+// kernel of the call and is launched normally (it reads x before any dependency wait, so it must
+// not start early under the previous kernel on the stream); 0: it follows the face kernel of
+// the same call and starts as that kernel's programmatic dependent.
 using CellsFn = cudaError_t (*)(int k, const void* x, void* y, const CellTabs& ct, const double* m, const double* s,
-                                double h, double wm, double ws, int add, cudaStream_t st);
+                                double h, double wm, double ws, int add, int first, cudaStream_t st);
 CellsFn cells_f64_d2();
 CellsFn cells_f64_d3();
 CellsFn cells_f32_d2();
@@ -284,10 +287,10 @@ CellsFn cells_ff_d2();
 CellsFn cells_ff_d3();
 
 #define GP_CELLS_CASE(D, A, K) \
-  case K: return run_cells<D, K, A>(x, y, ct, m, s, h, wm, ws, add, st);
+  case K: return run_cells<D, K, A>(x, y, ct, m, s, h, wm, ws, add, first, st);
 #define GP_CELLS_FN(D, A)                                                                                 \
   return [](int k, const void* x, void* y, const CellTabs& ct, const double* m, const double* s, double h, \
-            double wm, double ws, int add, cudaStream_t st) -> cudaError_t {                             \
+            double wm, double ws, int add, int first, cudaStream_t st) -> cudaError_t {                  \
     switch (k) {                                                                                          \
       GP_CELLS_CASE(D, A, 1) GP_CELLS_CASE(D, A, 2) GP_CELLS_CASE(D, A, 3) GP_CELLS_CASE(D, A, 4)         \
       GP_CELLS_CASE(D, A, 5) GP_CELLS_CASE(D, A, 6) GP_CELLS_CASE(D, A, 7) GP_CELLS_CASE(D, A, 8)         \

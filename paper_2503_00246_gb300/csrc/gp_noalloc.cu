@@ -9,11 +9,13 @@
 // threads) race on it.
 #include <mutex>
 
+#include "gp.h"
 #include "gp_launch.h"
 
 namespace {
 
-constexpr size_t kScratchBytes = (size_t)32 << 20;   // GP_NOALLOC_SCRATCH_BYTES in gp.h
+constexpr size_t kScratchBytes = (size_t)32 << 20;
+static_assert(kScratchBytes == GP_NOALLOC_SCRATCH_BYTES, "the scratch size must match the documented limit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -29,7 +31,10 @@ size_t noalloc_scratch_bytes() { return kScratchBytes; }
 
 // Device address of the scratch array on `device`, which must be the current
 // device.  The host-side symbol is only a stand-in, so the address is looked up
-// once per device with cudaGetSymbolAddress and cached.
+// once per device with cudaGetSymbolAddress and cached.  A device reset
+// (cudaDeviceReset, or a reset of the primary context) unloads the library's
+// device image and invalidates the cached address: the cache is not refreshed,
+// so gp_apply_noalloc must not be called after such a reset.
 cudaError_t noalloc_scratch(int device, void** out) {
   *out = nullptr;
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;

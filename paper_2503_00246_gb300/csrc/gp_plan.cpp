@@ -1019,7 +1019,14 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
     std::vector<double> lam;
     if (!macro_patch_1d(k, p.jumps, lam)) { err = "internal: macro-patch matrix not of rank k"; return GP_EINVAL; }
     const double hv = d == 3 ? h * h * h : h * h;
-    for (int j = 0; j < k; ++j) p.scale[j] = opts->gamma * lam[j] * hv;
+    for (int j = 0; j < k; ++j) {
+      p.scale[j] = opts->gamma * lam[j] * hv;
+      const double a = std::fabs(p.scale[j]);
+      if (opts->precision == GP_FP64_FF && a != 0.0 && !(a >= 0x1p-90 && a <= 0x1p90)) {
+        err = "GP_FP64_FF: a macro-patch scale factor lies outside [2^-90, 2^90]; use GP_FP64";
+        return GP_EINVAL;
+      }
+    }
     return GP_OK;
   }
   if (opts->stabilization != GP_STAB_GHOST) { err = "unknown stabilization"; return GP_EINVAL; }
@@ -1027,6 +1034,13 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
   for (int j = 0; j < k; ++j) {
     double c = opts->nweights == k ? opts->weights[j] : opts->gamma;
     p.scale[j] = c * hd;
+    // float-float keeps float's exponent range: the scale factors must stay well inside it
+    const double a = std::fabs(p.scale[j]);
+    if (opts->precision == GP_FP64_FF && a != 0.0 && !(a >= 0x1p-90 && a <= 0x1p90)) {
+      err = "GP_FP64_FF: the scale factor c_j h^(d-2) of order " + std::to_string(j + 1) +
+            " lies outside [2^-90, 2^90]; use GP_FP64";
+      return GP_EINVAL;
+    }
   }
   return GP_OK;
 }

@@ -147,7 +147,7 @@ gp_status sys_apply(gp_system* s, gp_ctx* c, gp::CellsFn cells, const void* x, v
   ct.wf = c->d_tp;
   ct.fwin = c->d_lwin;
   ct.own2lift = c == s->hi ? s->d_o2l_hi : s->d_o2l_lo;
-  const cudaError_t e = cells(p.k, x, y, ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 0, st);
+  const cudaError_t e = cells(p.k, x, y, ct, p.mass.data(), p.stiff.data(), p.h, 1.0, 1.0, 0, 0, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }
@@ -448,6 +448,8 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (hi->plan.precision == GP_FP32) return fail(nullptr, GP_EINVAL, "hi must be GP_FP64 or GP_FP64_FF");
   if (hi->plan.partitioned || (lo && lo->plan.partitioned))
     return fail(nullptr, GP_EUNSUPPORTED, "the model system is built for whole meshes only");
+  if ((!hi->d_tp && hi->plan.num_faces() > 0) || (lo && !lo->d_tp && lo->plan.num_faces() > 0))
+    return fail(nullptr, GP_EINVAL, "the model system needs contexts created with no_scratch = 0");
   if (lo) {
     if (!lo->on_device || lo->device != hi->device) return fail(nullptr, GP_EINVAL, "lo must be on hi's device");
     if (lo->plan.precision != GP_FP32) return fail(nullptr, GP_EINVAL, "lo must be GP_FP32");
@@ -579,7 +581,7 @@ gp_status gp_system_cells(gp_system* s, int which, double mass_weight, double st
   const cudaStream_t st = (cudaStream_t)stream;
   // the gather overwrites every active DoF (each is a node of an active cell)
   const cudaError_t e = (which == 0 ? s->cells_hi : s->cells_lo)(p.k, x, y, s->ct, p.mass.data(), p.stiff.data(),
-                                                                 p.h, mass_weight, stiff_weight, 0, st);
+                                                                 p.h, mass_weight, stiff_weight, 0, 1, st);
   if (e != cudaSuccess) return fail(c, GP_ECUDA, std::string("cell kernels: ") + cudaGetErrorString(e));
   return GP_OK;
 }

@@ -58,7 +58,8 @@ class gp_solve_stats(C.Structure):
 class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
-                ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int), ("stabilization", C.c_int)]
+                ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int), ("stabilization", C.c_int),
+                ("no_scratch", C.c_int)]
 
 
 class gp_tiles(C.Structure):
@@ -102,6 +103,7 @@ def _load():
         "gp_apply_noalloc": ([P, P, P, P], C.c_int),
         "gp_apply_host": ([P, P, P, P], C.c_int),
         "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
+        "gp_apply_batched_info": ([C.POINTER(P), C.c_int, C.c_int, i64p], C.c_int),
         "gp_batch_create": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P)], C.c_int),
         "gp_batch_apply": ([P, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_batch_info": ([P, i64p, i64p], C.c_int),
@@ -133,7 +135,8 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_version", "gp_apply_noalloc", "gp_batch_create", "gp_batch_apply", "gp_batch_info",
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
                "gp_system_destroy", "gp_partition_info", "gp_partition_slabs", "gp_get_tiles",
-               "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup", "gp_system_cells")
+               "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup", "gp_system_cells",
+               "gp_apply_batched_info")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -247,6 +250,8 @@ def gp_apply_host(ctx: Context, x: np.ndarray, y: np.ndarray | None = None, stre
 
 
 def gp_apply_batched(ctxs, nrhs, xs, ys, stream=None):
+    """y_p = G_p x_p for every problem and right-hand side: one graph replay of the batch the
+    library keeps for this list of contexts (built on the first call)."""
     n = len(ctxs)
     for c, x, y in zip(ctxs, xs, ys):
         _check_vec(c, x, nrhs)
@@ -255,6 +260,15 @@ def gp_apply_batched(ctxs, nrhs, xs, ys, stream=None):
     X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
     Y = (C.c_void_p * n)(*[_ptr(y) for y in ys])
     _check(lib.gp_apply_batched(H, n, nrhs, X, Y, _stream(stream)))
+
+
+def gp_apply_batched_info(ctxs, nrhs) -> int:
+    """Graph replays made by gp_apply_batched for this list of contexts."""
+    n = len(ctxs)
+    H = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    v = C.c_int64()
+    _check(lib.gp_apply_batched_info(H, n, nrhs, C.byref(v)))
+    return v.value
 
 
 class Batch:

@@ -265,3 +265,28 @@ def test_callback_level_set_and_non_finite_values(gplib):
     with pytest.raises(gplib.GpError) as e:
         gplib.gp_setup(mesh, ls, opts)
     assert e.value.status == gplib.GP_EINVAL and "finite" in str(e.value)
+
+
+def test_noalloc_limit_and_struct_layout_match_header(gplib):
+    """The binding's copy of GP_NOALLOC_SCRATCH_BYTES and of gp_opts' fields follow gp.h."""
+    src = open(HEADER).read()
+    m = re.search(r"#define GP_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", src)
+    assert m and int(m.group(1)) << int(m.group(2)) == gplib.NOALLOC_SCRATCH_BYTES
+    body = re.search(r"typedef struct \{([^{}]*?)\} gp_opts;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        if decl.strip():
+            names += [part.replace("*", " ").split()[-1] for part in decl.split(",")]
+    assert names == [f for f, _ in gplib.gp_opts._fields_]
+
+
+def test_ff_setup_refuses_extreme_scale_factors(gplib):
+    """GP_FP64_FF keeps float's exponent range: gp_setup refuses scale factors c_j h^(d-2)
+    outside [2^-90, 2^90] (native FP64 accepts them)."""
+    pr = W.small_ball(3, 8, 2, seed=62)
+    pr.weights = [1e30, 0.5]                               # c_1 h = 1e30 * 0.25 > 2^90
+    with pytest.raises(gplib.GpError) as e:
+        gplib.setup_problem(pr, precision=2, device=-1)
+    assert e.value.status == gplib.GP_EINVAL and "2^90" in str(e.value)
+    gplib.setup_problem(pr, precision=0, device=-1).close()    # native FP64 accepts it

@@ -1,10 +1,10 @@
-"""The paper-like CPU baseline (oracle/cpu_kronecker.py: the factorised face operator of
+"""The paper-like CPU baseline (baselines/cpu_kronecker.py: the factorised face operator of
 Sec. 2.4 applied in the three steps of Sec. 2.5.1 with numpy) against the oracle's
 explicit face matrices.  Agreement pins the baseline that bench.py times."""
 import numpy as np
 import pytest
 
-from oracle.cpu_kronecker import KroneckerCPU, KroneckerOpenMP
+from baselines.cpu_kronecker import KroneckerCPU, KroneckerOpenMP
 from oracle.ghost_penalty import Oracle
 from paper_2503_00246_gb300 import workloads as W
 

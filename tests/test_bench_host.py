@@ -1,8 +1,5 @@
 """Host-side pieces of bench.py: the flop counts behind the roofline figures and the
 lookup of the committed ncu traffic (no GPU)."""
-import os
-import re
-
 import bench
 
 
@@ -28,12 +25,23 @@ def test_executed_flop_count_below_paper_count():
     assert bench._flops_face(3, 3, 1) == 16 * 91
 
 
-def test_traffic_lookup_follows_the_committed_summary():
-    path = os.path.join(bench.ROOT, "profiles", "face_kernel_ball64_k3.md")
-    txt = open(path).read()
-    for tag in ("ff64", "f64", "f32"):
-        t = bench._traffic(tag)
-        m = re.search(r"traffic_bytes_per_launch\[" + tag + r"\] = (\d+)", txt)
-        assert m, tag
-        # either the sources still match the capture (the committed value) or they changed (None)
-        assert t is None or t == int(m.group(1))
+def test_traffic_lookup_follows_the_committed_counters(tmp_path, monkeypatch):
+    """bench.py reads DRAM traffic per launch from profiles/traffic.json, and only while the
+    kernel sources hash to the value recorded beside the counters."""
+    import json
+    f = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench._traffic("face_kernel_double_d3k4") is None            # no file
+    f.write_text(json.dumps({"kernel_sources_sha256_16": bench.kernel_sources_hash(),
+                             "traffic_bytes_per_launch": {"face_kernel_double_d3k4": 123456}}))
+    assert bench._traffic("face_kernel_double_d3k4") == 123456
+    assert bench._traffic("other") is None
+    f.write_text(json.dumps({"kernel_sources_sha256_16": "0" * 16,
+                             "traffic_bytes_per_launch": {"face_kernel_double_d3k4": 123456}}))
+    assert bench._traffic("face_kernel_double_d3k4") is None            # sources changed
+
+
+def test_both_arms_share_the_config_object():
+    assert bench.config_dict(1) == bench.config_dict(1)
+    c = bench.config_dict(1)
+    assert "gyroid" in c["workload"] and c["degree"] == 4 and c["n_cells"] == 128 ** 3

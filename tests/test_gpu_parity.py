@@ -163,22 +163,86 @@ def test_host_buffers_end_to_end(gplib, cuda):
     assert np.array_equal(y_host, y_dev)
 
 
+def _batched_c(gplib):
+    """gp_apply_batched as the exported C symbol (ctypes.CDLL on the library file)."""
+    import ctypes
+    fn = ctypes.CDLL(gplib.LIB_PATH).gp_apply_batched
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+
+    def call(ctxs, nrhs, xs, ys, stream):
+        import ctypes as C
+        n = len(ctxs)
+        H = (C.c_void_p * n)(*[c.handle for c in ctxs])
+        X = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        Y = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+        return fn(H, n, nrhs, X, Y, stream)
+    return call
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_batched(gplib, cuda, prec):
+    """gp_apply_batched through the C symbol: two calls with fresh inputs replay the cached
+    batch's graph once each, and match the oracle."""
     probs = [W.small_ball(3, 10, 2, seed=21), W.small_ball(3, 13, 4, seed=22),
-             W.small_ball(3, 8, 6, seed=23)]
+             W.small_ball(3, 8, 6, seed=23), W.small_ball(2, 18, 3, seed=24)]
     nrhs = 2
     ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
-    xs = [W.x_vectors(p, c.n_active, nrhs) for p, c in zip(probs, ctxs)]
-    xd = [_dev(cuda, x.ravel(), prec) for x in xs]
-    yd = [cuda.full_like(a, float("nan")) for a in xd]
-    gplib.gp_apply_batched(ctxs, nrhs, xd, yd)
+    call = _batched_c(gplib)
+    oracles = [Oracle(p) for p in probs]
+    stream = cuda.cuda.current_stream().cuda_stream
+    for rep in range(2):
+        xs = [W.x_vectors(p, c.n_active, nrhs + rep)[rep:] for p, c in zip(probs, ctxs)]
+        xd = [_dev(cuda, x.ravel(), prec) for x in xs]
+        yd = [cuda.full_like(a, float("nan")) for a in xd]
+        assert call(ctxs, nrhs, xd, yd, stream) == gplib.GP_OK, gplib.gp_last_error()
+        cuda.cuda.synchronize()
+        assert gplib.gp_apply_batched_info(ctxs, nrhs) == rep + 1     # one graph launch per call
+        for o, c, x, y in zip(oracles, ctxs, xs, yd):
+            yy = y.double().cpu().numpy().reshape(nrhs, -1)
+            for r in range(nrhs):
+                _close(yy[r], o.apply(_ref_input(x[r], prec)), prec)
+                assert np.array_equal(yy[r], _apply(gplib, cuda, c, x[r], prec))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_workload_full_size(gplib, cuda, prec):
+    """The batched workload at its stated size: 64 independent 3D balls (n ~ U{16..96},
+    k ~ U{2..6}), 4 right-hand sides, one gp_apply_batched call.  Every output vector equals a
+    single gp_apply bit for bit; the oracle checks sampled rows of 8 problems (the smallest,
+    the largest and one of every degree)."""
+    probs = W.batched_3d()
+    nrhs = 4
+    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    dt = cuda.float32 if prec == 1 else cuda.float64
+    gen = cuda.Generator(device="cuda")
+    gen.manual_seed(W.BASE_SEED + 5000)
+    xs = [cuda.rand(nrhs * c.n_active, generator=gen, dtype=dt, device="cuda") * 2 - 1 for c in ctxs]
+    ys = [cuda.full_like(x, float("nan")) for x in xs]
+    call = _batched_c(gplib)
+    assert call(ctxs, nrhs, xs, ys, cuda.cuda.current_stream().cuda_stream) == gplib.GP_OK, gplib.gp_last_error()
     cuda.cuda.synchronize()
-    for p, c, x, y in zip(probs, ctxs, xs, yd):
-        o = Oracle(p)
-        yy = y.double().cpu().numpy().reshape(nrhs, -1)
+    for c, x, y in zip(ctxs, xs, ys):
+        n = c.n_active
+        one = cuda.empty(n, dtype=dt, device="cuda")
         for r in range(nrhs):
-            _close(yy[r], o.apply(_ref_input(x[r], prec)), prec)
+            gplib.gp_apply(c, x[r * n:(r + 1) * n], one)
+            assert cuda.equal(y[r * n:(r + 1) * n], one)
+    pick = {int(np.argmin([c.n_active for c in ctxs])), int(np.argmax([c.n_active for c in ctxs]))}
+    for k in sorted({p.degree for p in probs}):
+        pick.add(next(i for i, p in enumerate(probs) if p.degree == k))
+    rng = np.random.default_rng(31)
+    for i in sorted(pick):
+        o = Oracle(probs[i])
+        n = ctxs[i].n_active
+        assert (n, ctxs[i].n_faces) == (o.n_active, o.n_faces)
+        r = int(rng.integers(0, nrhs))
+        x = xs[i][r * n:(r + 1) * n].double().cpu().numpy()
+        y = ys[i][r * n:(r + 1) * n].double().cpu().numpy()
+        touched = np.unique(o.patch_index(0)[rng.integers(0, o.faces[0].shape[0], 100)].ravel())
+        rows = np.unique(np.concatenate([rng.integers(0, n, 1500), touched]))
+        ref = o.apply_rows(x, rows)
+        assert np.abs(y[rows] - ref).max() <= TOL[prec] * np.abs(ref).max(), i
 
 
 def test_argument_errors(gplib, cuda):
@@ -209,8 +273,33 @@ def _sampled(gplib, cuda, pr, prec, nsample=3000):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_ball_96_k4_sampled(gplib, cuda, prec):
-    _sampled(gplib, cuda, W.ball_3d_sweep(4), prec)
+@pytest.mark.parametrize("k", range(1, 9))
+def test_ball_96_sampled_every_degree(gplib, cuda, k, prec):
+    """The degree sweep at its stated size: 96^3 ball, k = 1..8, every arithmetic form."""
+    _sampled(gplib, cuda, W.ball_3d_sweep(k), prec)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("k", [5, 6])
+def test_ball_96_annihilation(gplib, cuda, k, prec):
+    """Consistency of the penalty (Sec. 2.2): G annihilates the interpolant of a seeded global
+    polynomial of degree <= k, here on the 96^3 mesh at k = 5, 6 (||G|| by 30 power iterations)."""
+    pr = W.ball_3d_sweep(k)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    ex, co = W.poly_coeffs(pr, k)
+    xp = W.poly_eval(ex, co, gplib.gp_active_dof_coords(ctx))
+    xd = _dev(cuda, xp, prec)
+    yd = cuda.empty_like(xd)
+    v = cuda.tensor(np.random.default_rng(0).standard_normal(ctx.n_active), dtype=cuda.float64, device="cuda")
+    w = cuda.empty_like(v)
+    for _ in range(30):
+        gplib.gp_apply(ctx, v, w)
+        gn = float(cuda.linalg.norm(w))
+        v = w / gn
+    gplib.gp_apply(ctx, xd, yd)
+    r = float(cuda.linalg.norm(yd))
+    bound = 1e-10 * gn * float(cuda.linalg.norm(xd))
+    assert np.isfinite(r) and r <= bound, r / (gn * float(cuda.linalg.norm(xd)))
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -127,3 +127,34 @@ def test_gyroid_k4_defect_correction_vs_fp64_pcg(gplib, cuda):
     assert st_dc["hi_applies"] < 20 < st_cg["hi_applies"]
     assert cuda.linalg.norm(u_dc - u_cg) <= 1e-6 * cuda.linalg.norm(u_cg)
     sysm.close()
+
+
+@pytest.mark.parametrize("hi", [0, 2])
+def test_cells_after_apply_on_one_stream(gplib, cuda, hi):
+    """gp_apply(x -> t) and then gp_system_cells(t -> y) on one stream with no host sync:
+    the cell kernel, the first kernel of gp_system_cells, must not read t before the
+    ghost-penalty lift has written it.  t is filled with NaN on the same stream before
+    every apply, so an early read shows up as NaN in y."""
+    from oracle.cell_operator import CellOperator
+    pr = W.small_ball(3, 20, 3, radius=0.6, seed=140)
+    o = Oracle(pr)
+    co = CellOperator(pr, o.num, o.cls)
+    chi = gplib.setup_problem(pr, precision=hi)
+    sysm = gplib.gp_system_create(chi, None)
+    x = W.x_vectors(pr, chi.n_active)[0]
+    xd = cuda.tensor(x, dtype=cuda.float64, device="cuda")
+    t = cuda.empty_like(xd)
+    ys = []
+    for _ in range(20):
+        t.fill_(float("nan"))
+        yd = cuda.empty_like(xd)
+        gplib.gp_apply(chi, xd, t)
+        gplib.gp_system_cells(sysm, 0, t, yd, 1.0, 1.0)
+        ys.append(yd)
+    cuda.cuda.synchronize()
+    ref = co.apply(o.apply(x))
+    for yd in ys:
+        y = yd.cpu().numpy()
+        assert np.all(np.isfinite(y))
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    sysm.close()
