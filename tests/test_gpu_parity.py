@@ -255,8 +255,19 @@ def test_argument_errors(gplib, cuda):
         gplib.gp_apply(ctx, xd.float(), xd)
 
 
-def _sampled(gplib, cuda, pr, prec, nsample=3000):
-    o = Oracle(pr)
+_ORACLE = {}
+
+
+def _oracle_once(key, pr):
+    """The oracle of the last large workload (built once for the three arithmetic forms)."""
+    if key not in _ORACLE:
+        _ORACLE.clear()
+        _ORACLE[key] = Oracle(pr)
+    return _ORACLE[key]
+
+
+def _sampled(gplib, cuda, pr, prec, nsample=3000, key=None):
+    o = _oracle_once(key, pr) if key is not None else Oracle(pr)
     ctx = gplib.setup_problem(pr, precision=prec)
     assert (ctx.n_active, ctx.n_faces) == (o.n_active, o.n_faces)
     x = W.x_vectors(pr, ctx.n_active)[0]
@@ -276,7 +287,7 @@ def _sampled(gplib, cuda, pr, prec, nsample=3000):
 @pytest.mark.parametrize("k", range(1, 9))
 def test_ball_96_sampled_every_degree(gplib, cuda, k, prec):
     """The degree sweep at its stated size: 96^3 ball, k = 1..8, every arithmetic form."""
-    _sampled(gplib, cuda, W.ball_3d_sweep(k), prec)
+    _sampled(gplib, cuda, W.ball_3d_sweep(k), prec, key=("ball96", k))
 
 
 @pytest.mark.parametrize("prec", [0, 2])
@@ -304,7 +315,7 @@ def test_ball_96_annihilation(gplib, cuda, k, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_gyroid_128_k4_sampled(gplib, cuda, prec):
-    _sampled(gplib, cuda, W.gyroid_3d(), prec)
+    _sampled(gplib, cuda, W.gyroid_3d(), prec, key="gyroid128")
 
 
 @pytest.mark.parametrize("prec", PRECS)
