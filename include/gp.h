@@ -59,7 +59,9 @@ typedef enum {
  * pipes.  The pairs have the exponent range of float, not of double:
  *   - FP64-level accuracy (1e-12 relative to the largest output) holds when every
  *     non-zero |x_i| lies in [2^-97, 2^127) and every output |y_i| stays below
- *     2^127 (about 1.7e38);
+ *     2^127 (about 1.7e38); besides that relative error, every value carries an
+ *     absolute error of up to a few 2^-126 (about 1e-38: float cannot hold the low
+ *     part of a smaller value), which matters only for outputs below about 2^-80;
  *   - an entry with 2^-126 <= |x_i| < 2^-97 keeps only its leading 24 bits (the
  *     low float would be subnormal), |x_i| < 2^-126 reads as 0, and |x_i| >= 2^128
  *     reads as infinity (y is then not finite on the DoFs its faces reach);
@@ -117,7 +119,23 @@ typedef struct {
   int no_scratch;           /* 1: allocate no face-output scratch; only gp_apply_noalloc can
                                apply the context (the other applies, the autotuner, batches and
                                the model system return GP_EINVAL) */
+  int kernel_path;          /* GP_PATH_AUTO (0), GP_PATH_FACE_LIFT or GP_PATH_BRICK */
+  int brick_smem;           /* brick path: shared-memory budget in bytes that picks the brick
+                               shape (0: 100 KB) */
 } gp_opts;
+
+/* Kernel paths of gp_apply / gp_apply_add (same operator, same accuracy, rounding may differ):
+ *   GP_PATH_FACE_LIFT  a face kernel writes every face output W_F to a buffer of
+ *                      n_faces (2k+1)(k+1)^(d-1) values and a lift kernel gathers them per DoF;
+ *   GP_PATH_BRICK      the mesh is cut into bricks of cells; one CTA per brick stages the x
+ *                      blocks of its involved cells in shared memory, evaluates the faces of
+ *                      its cells, sums the outputs per DoF in shared memory and writes y once
+ *                      (DoFs on the boundary planes between bricks go through a small buffer of
+ *                      partial sums and a second kernel); GP_EUNSUPPORTED from gp_setup when no
+ *                      brick shape fits the shared-memory budget;
+ *   GP_PATH_AUTO       the brick path when a brick shape fits, else face + lift.
+ * Both are deterministic: repeated applies are bitwise identical. */
+enum { GP_PATH_AUTO = 0, GP_PATH_FACE_LIFT = 1, GP_PATH_BRICK = 2 };
 
 /* Stabilisations.  GP_STAB_MACRO is the macro-patch alternative the paper names next to the
  * ghost penalty (Sec. 2.2): per ghost face, gamma times the integral over each of its two

@@ -29,6 +29,30 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m) {
   return s;
 }
 
+size_t brick_scratch_bytes(const gp_ctx* c) {
+  const gp::Plan& p = c->plan;
+  return (size_t)p.num_bricks() * (size_t)p.pgrid * (p.precision == GP_FP32 ? 4 : 8);
+}
+
+int brick_default_fb(int dim, int k) {
+  const int L = dim == 3 ? (k + 1) * (k + 1) : k + 1;
+  const int fb = 256 / L;
+  return fb > 0 ? fb : 1;
+}
+
+gp_status ensure_face_outputs(gp_ctx* c) {
+  if (c->d_tp || c->plan.num_faces() == 0) return GP_OK;
+  if (c->no_scratch) return fail(c, GP_EINVAL, "the context was created with no_scratch = 1");
+  const gp::Plan& p = c->plan;
+  const size_t bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * (p.precision == GP_FP32 ? 4 : 8);
+  DeviceGuard g(c->device);
+  const cudaError_t e = cudaMalloc(&c->d_tp, bytes);
+  if (e != cudaSuccess)
+    return fail(c, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA,
+                std::string("face outputs: ") + cudaGetErrorString(e));
+  return GP_OK;
+}
+
 }  // namespace gpi
 
 using gpi::DeviceGuard;
@@ -48,13 +72,19 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_device(gp_ctx* c) {
-  void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow,
-                  c->d_zruns, c->d_tp, c->d_xh, c->d_yh};
+  void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow, c->d_zruns, c->d_tp, c->d_xh, c->d_yh,
+                  c->d_bdesc, c->d_bcell, c->d_bccoord, c->d_bface, c->d_rowtab, c->d_bslot,
+                  c->d_pnode, c->d_invmask, c->d_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_frows = c->d_lwin = c->d_lrow = nullptr;
   c->d_zruns = nullptr;
   c->d_tp = c->d_xh = c->d_yh = nullptr;
+  c->d_bdesc = c->d_bcell = c->d_bccoord = c->d_rowtab = c->d_bslot = nullptr;
+  c->d_bface = nullptr;
+  c->d_pnode = nullptr;
+  c->d_invmask = nullptr;
+  c->d_part = nullptr;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
 }
@@ -72,8 +102,11 @@ void free_device(gp_ctx* c) {
 gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace,
                       const gp::Tiles* tiles, int which) {
   const gp::Plan& p = c->plan;
-  if (!scratch && !c->d_tp && p.num_faces() > 0)
-    return fail(c, GP_EINVAL, "the context was created with no_scratch = 1: only gp_apply_noalloc can apply it");
+  const bool brick = c->use_brick && which == 3;
+  if (!scratch && p.num_faces() > 0 && (brick ? (!c->d_part && p.num_plane_nodes() > 0) : !c->d_tp))
+    return fail(c, GP_EINVAL,
+                c->no_scratch ? "the context was created with no_scratch = 1: only gp_apply_noalloc can apply it"
+                              : "internal: the context has no face-output buffer");
   gp::ApplyArgs a;
   a.dim = p.dim;
   a.k = p.k;
@@ -107,6 +140,44 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
   a.ev = ev;
   a.tiles = tiles ? *tiles : c->tiles;
   a.which = which;
+  if (brick) {
+    a.brick = true;
+    gp::BrickArgs& ba = a.ba;
+    ba.bdesc = c->d_bdesc;
+    ba.bcell = c->d_bcell;
+    ba.bccoord = c->d_bccoord;
+    ba.bface = c->d_bface;
+    ba.rowtab = c->d_rowtab;
+    ba.part = scratch ? scratch : c->d_part;
+    ba.nbricks = (int32_t)p.num_bricks();
+    ba.n = p.n;
+    ba.pgrid = p.pgrid;
+    ba.maxcell = p.bmax_cell;
+    ba.maxown = p.bmax_own;
+    gp::PlaneArgs& pa = a.pa;
+    pa.pnode = c->d_pnode;
+    pa.nplane = (int32_t)p.num_plane_nodes();
+    pa.part = ba.part;
+    pa.bslot = c->d_bslot;
+    pa.invmask = c->d_invmask;
+    pa.n = p.n;
+    pa.pgrid = p.pgrid;
+    // box-face grids of a brick: axis a, side 0 (lower) and 1 (upper); rows along the first
+    // other axis u0, (bdim[u0] k + 1) entries each
+    int32_t off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      ba.bdim[ax] = pa.bdim[ax] = p.bdim[ax];
+      pa.nbx[ax] = p.nbx[ax];
+      const int u0 = ax == 0 ? 1 : 0, u1 = ax == 2 ? 1 : 2;
+      ba.gstride[ax] = pa.gstride[ax] = p.bdim[u0] * p.k + 1;
+      const int32_t e2 = ax < p.dim ? (p.bdim[u0] * p.k + 1) * (p.dim == 3 ? p.bdim[u1] * p.k + 1 : 1) : 0;
+      for (int side = 0; side < 2; ++side) {
+        ba.goff[ax][side] = pa.goff[ax][side] = off;
+        off += e2;
+      }
+    }
+    if (off != p.pgrid) return fail(c, GP_EINVAL, "internal: brick partial grid size");
+  }
   cudaError_t e;
   if (p.precision == GP_FP64)
     e = p.dim == 2 ? gp::apply_f64_d2(a, st) : gp::apply_f64_d3(a, st);
@@ -183,10 +254,37 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     if (e == cudaSuccess) e = upload(&c->d_lwin, p.lwin);
     if (e == cudaSuccess) e = upload(&c->d_lrow, p.lrow);
     if (e == cudaSuccess) e = upload(&c->d_zruns, zruns);
-    // face outputs W_F: float, double, or a (hi, lo) float pair per value
+    c->no_scratch = opts->no_scratch != 0;
+    // kernel path: the brick path when a brick shape fits the shared-memory budget
     const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
+    if (opts->kernel_path != GP_PATH_FACE_LIFT && p.num_faces() > 0 && !p.partitioned) {
+      const size_t budget = opts->brick_smem > 0 ? (size_t)opts->brick_smem : (size_t)100 * 1024;
+      const int fb = gpi::brick_default_fb(p.dim, p.k);
+      const size_t extra = (size_t)(p.dim == 3 ? 2 : 1) * fb * p.k * p.L * vbytes;
+      c->use_brick = gp::build_bricks(c->plan, (int)vbytes, (int)vbytes, extra, std::min(budget, gp::BRICK_MAX_SMEM));
+    }
+    if (opts->kernel_path == GP_PATH_BRICK && !c->use_brick && p.num_faces() > 0) {
+      free_device(c);
+      delete c;
+      return fail(nullptr, GP_EUNSUPPORTED, "no brick shape fits the shared-memory budget (use GP_PATH_AUTO)");
+    }
+    if (c->use_brick) {
+      std::vector<int4> pn(p.num_plane_nodes());
+      std::memcpy(pn.data(), p.pnode.data(), pn.size() * sizeof(int4));
+      if (e == cudaSuccess) e = upload(&c->d_bdesc, p.bdesc);
+      if (e == cudaSuccess) e = upload(&c->d_bcell, p.bcell);
+      if (e == cudaSuccess) e = upload(&c->d_bccoord, p.bccoord);
+      if (e == cudaSuccess) e = upload(&c->d_bface, p.bface);
+      if (e == cudaSuccess) e = upload(&c->d_rowtab, p.rowtab);
+      if (e == cudaSuccess) e = upload(&c->d_bslot, p.bslot);
+      if (e == cudaSuccess) e = upload(&c->d_pnode, pn);
+      if (e == cudaSuccess) e = upload(&c->d_invmask, p.invmask);
+      const size_t part_bytes = gpi::brick_scratch_bytes(c);
+      if (e == cudaSuccess && part_bytes > 0 && !opts->no_scratch) e = cudaMalloc(&c->d_part, part_bytes);
+    }
+    // face outputs W_F of the face + lift path: float, double, or a (hi, lo) float pair per value
     const size_t tp_bytes = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
-    if (e == cudaSuccess && tp_bytes > 0 && !opts->no_scratch) e = cudaMalloc(&c->d_tp, tp_bytes);
+    if (e == cudaSuccess && tp_bytes > 0 && !opts->no_scratch && !c->use_brick) e = cudaMalloc(&c->d_tp, tp_bytes);
     if (e != cudaSuccess) {
       std::string m = std::string("device setup: ") + cudaGetErrorString(e);
       free_device(c);
@@ -194,7 +292,8 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
       return fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA, m);
     }
     c->on_device = true;
-    gpi::tiles_lookup(c->device, c->plan.dim, c->plan.k, c->plan.precision, &c->tiles);
+    if (c->use_brick) gpi::brick_tiles_lookup(c->device, c->plan.dim, c->plan.k, c->plan.precision, &c->tiles);
+    else gpi::tiles_lookup(c->device, c->plan.dim, c->plan.k, c->plan.precision, &c->tiles);
   }
   *out = c;
   return GP_OK;
@@ -341,12 +440,14 @@ gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream) {
   if (s != GP_OK) return s;
   const gp::Plan& p = ctx->plan;
   const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
-  const size_t need = (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
+  // the scratch of the context's kernel path: partial grids (brick) or face outputs (face + lift)
+  const size_t need = ctx->use_brick ? gpi::brick_scratch_bytes(ctx)
+                                     : (size_t)p.num_faces() * p.L * (2 * p.k + 1) * vbytes;
   if (need > gp::noalloc_scratch_bytes())
     return fail(ctx, GP_EINVAL,
-                "gp_apply_noalloc: the face outputs need " + std::to_string(need) +
-                    " bytes, more than the fixed scratch of " + std::to_string(gp::noalloc_scratch_bytes()) +
-                    " bytes; use gp_apply");
+                std::string("gp_apply_noalloc: the ") + (ctx->use_brick ? "plane partial sums" : "face outputs") +
+                    " need " + std::to_string(need) + " bytes, more than the fixed scratch of " +
+                    std::to_string(gp::noalloc_scratch_bytes()) + " bytes; use gp_apply");
   if (p.n_active == 0) return GP_OK;
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");

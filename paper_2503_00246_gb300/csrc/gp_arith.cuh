@@ -187,6 +187,17 @@ __device__ __forceinline__ void sum_add(Sum<ff64>& d, ff64 v) {
   d.c = __fadd_rn(__fadd_rn(d.c, v.lo), err);
 }
 
+// d += o for two partial sums (the same compensated scheme for float-float)
+__device__ __forceinline__ void sum_merge(Sum<float>& d, const Sum<float>& o) { d.v += o.v; }
+__device__ __forceinline__ void sum_merge(Sum<double>& d, const Sum<double>& o) { d.v += o.v; }
+__device__ __forceinline__ void sum_merge(Sum<ff64>& d, const Sum<ff64>& o) {
+  const float s = __fadd_rn(d.s, o.s);                     // two-sum of d.s + o.s
+  const float bb = __fsub_rn(s, d.s);
+  const float err = __fadd_rn(__fsub_rn(d.s, __fsub_rn(s, bb)), __fsub_rn(o.s, bb));
+  d.s = s;
+  d.c = __fadd_rn(__fadd_rn(d.c, o.c), err);
+}
+
 // ------------------------------------------------ solver inner products --
 // IoDot<T> accumulates an inner product of two solver vectors of element type T.
 // FP64 vectors use FP64 fused multiply-adds.  FP32 vectors use the compensated

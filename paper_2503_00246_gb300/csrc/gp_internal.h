@@ -17,7 +17,19 @@ struct gp_ctx {
   int32_t* d_lwin = nullptr;
   int32_t* d_lrow = nullptr;
   int2* d_zruns = nullptr;
-  void* d_tp = nullptr;          // per-face outputs W_F (scratch)
+  void* d_tp = nullptr;          // per-face outputs W_F (scratch of the face + lift path)
+  // brick path (gp_brick.cuh): tables and the partial grids of the plane nodes (scratch)
+  bool use_brick = false;
+  int32_t* d_bdesc = nullptr;
+  int32_t* d_bcell = nullptr;
+  int32_t* d_bccoord = nullptr;
+  uint32_t* d_bface = nullptr;
+  int32_t* d_rowtab = nullptr;
+  int32_t* d_bslot = nullptr;
+  int4* d_pnode = nullptr;
+  int8_t* d_invmask = nullptr;
+  void* d_part = nullptr;
+  bool no_scratch = false;
   void* d_xh = nullptr;          // gp_apply_host staging
   void* d_yh = nullptr;
   gp::Tiles tiles{};             // tile shape of the face and lift launches (0: defaults)
@@ -54,6 +66,14 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m);
 gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
                  bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3);
 
+// Default faces per chunk of the brick kernel (about 256 threads).
+int brick_default_fb(int dim, int k);
+// Bytes of the brick path's partial grids (its scratch) for context c.
+size_t brick_scratch_bytes(const gp_ctx* c);
+// Allocates the face-output buffer W of the face + lift path if the context has none (the
+// model system and the autotuner's face + lift timings need it).
+gp_status ensure_face_outputs(gp_ctx* c);
+
 // Tile-shape helpers for the context's (dimension, arithmetic).
 gp::TileOps tile_ops(int dim, int precision);
 
@@ -61,5 +81,7 @@ gp::TileOps tile_ops(int dim, int precision);
 // gp_setup starts every context from the entry of its key, if there is one.
 bool tiles_lookup(int device, int dim, int k, int precision, gp::Tiles* out);
 void tiles_record(int device, int dim, int k, int precision, const gp::Tiles& t);
+// The same for brick-path contexts (faces per chunk), filled by gp_autotune.
+bool brick_tiles_lookup(int device, int dim, int k, int precision, gp::Tiles* out);
 
 }  // namespace gpi

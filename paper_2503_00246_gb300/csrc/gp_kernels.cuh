@@ -79,6 +79,103 @@ struct LiftArgs {
   int32_t n_active;
 };
 
+// ------------------------------------------------- one normal line's steps --
+// The three one-dimensional steps of the face apply for one normal line, shared by the
+// face kernel and the brick kernel (gp_brick.cuh).
+
+// Jump values t_j = g_j . v of the line (j = 1..k; row j - 1 of c.g).  Mirroring the patch
+// about the face maps basis b to 2k - b, K- to K+ and d/dn to -d/dn, so
+// g_j[2k - b] = (-1)^(j+1) g_j[b]: odd orders see v[b] + v[2k-b], even orders
+// v[b] - v[2k-b], and only odd orders see the shared node b = k.
+template <int K, typename V>
+__device__ __forceinline__ void line_jumps(const V (&v)[2 * K + 1], const Consts<V, K>& c, V (&t)[K]) {
+  constexpr int NN = 2 * K + 1;
+  V vp[K], vm[K];
+#pragma unroll
+  for (int b = 0; b < K; ++b) {
+    vp[b] = vadd_loose(v[b], v[NN - 1 - b]);
+    vm[b] = vsub_loose(v[b], v[NN - 1 - b]);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const bool odd = (j % 2) == 0;   // order j + 1
+    Dot<V> acc = dot_first(c.g[j][0], odd ? vp[0] : vm[0]);
+#pragma unroll
+    for (int b = 1; b < K; ++b) dot_fma(acc, c.g[j][b], odd ? vp[b] : vm[b]);
+    if (odd) dot_fma(acc, c.g[j][K], v[K]);
+    t[j] = dot_value(acc);
+  }
+}
+
+// Tangential reference masses of one face: plane[j][tau] holds the jump values of the face's
+// lines (written by every line, then a barrier); each thread returns out[j] for its line
+// tau = t1 + (k+1) t2.  3D: two passes through plane2 with a barrier between them.  Every
+// thread of the CTA must call it (it synchronises).
+template <int D, int K, typename V, int L>
+__device__ __forceinline__ void line_tangential(V (*plane)[L], V (*plane2)[L], const V (*sm)[K + 1], const int tau,
+                                                V (&out)[K]) {
+  constexpr int K1 = K + 1;
+  if constexpr (D == 3) {
+    const int t1 = tau % K1, t2 = tau / K1;
+    V m1[K1];
+#pragma unroll
+    for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      Dot<V> acc = dot_first(m1[0], plane[j][K1 * t2]);
+#pragma unroll
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane[j][q + K1 * t2]);
+      plane2[j][tau] = dot_value(acc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      Dot<V> acc = dot_first(m1[0], plane2[j][t1]);
+#pragma unroll
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane2[j][t1 + K1 * q]);
+      out[j] = dot_value(acc);
+    }
+  } else {
+    V m1[K1];
+#pragma unroll
+    for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      Dot<V> acc = dot_first(m1[0], plane[j][0]);
+#pragma unroll
+      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane[j][q]);
+      out[j] = dot_value(acc);
+    }
+  }
+}
+
+// Normal expansion w[b] = sum_j g_j[b] sj[j] (sj = s_j times the tangential result):
+// w[b] = E_b + O_b and w[2k-b] = E_b - O_b, with E_b (O_b) the sum over odd (even) orders of
+// g_j[b] sj[j]; w[k] = E_k.
+template <int K, typename V>
+__device__ __forceinline__ void line_expand(const Consts<V, K>& c, const V (&sj)[K], V (&w)[2 * K + 1]) {
+  constexpr int NN = 2 * K + 1;
+#pragma unroll
+  for (int b = 0; b <= K; ++b) {
+    Dot<V> ev = dot_first(c.g[0][b], sj[0]);
+#pragma unroll
+    for (int j = 2; j < K; j += 2) dot_fma(ev, c.g[j][b], sj[j]);
+    if (b == K || K == 1) {
+      const V e = dot_value(ev);
+      w[b] = e;
+      if (b < K) w[NN - 1 - b] = e;
+    } else {
+      Dot<V> ov = dot_first(c.g[K > 1 ? 1 : 0][b], sj[K > 1 ? 1 : 0]);
+#pragma unroll
+      for (int j = 3; j < K; j += 2) dot_fma(ov, c.g[j][b], sj[j]);
+      w[b] = dot_merge<false>(ev, ov);
+      w[NN - 1 - b] = dot_merge<true>(ev, ov);
+    }
+  }
+}
+
 // ----------------------------------------------------------------- face --
 // One thread per (face, normal line tau); fb faces per CTA (blockDim.x = fb L).
 // `blk` is the CTA's index within its problem; `sc` points to the k scale
@@ -151,65 +248,16 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
 #pragma unroll
     for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
   }
-  // ---- contract with the k jump vectors.  Mirroring the patch about the face maps
-  // basis b to 2k - b, K- to K+ and d/dn to -d/dn, so g_j[2k - b] = (-1)^(j+1) g_j[b]
-  // (j = 1..k; row j - 1 of c.g): odd orders see v[b] + v[2k-b], even orders
-  // v[b] - v[2k-b], and only odd orders see the shared node b = k.
+  // ---- contract with the k jump vectors, then the tangential reference masses
   {
-    V vp[K], vm[K];
+    V t[K];
+    line_jumps<K, V>(v, c, t);
 #pragma unroll
-    for (int b = 0; b < K; ++b) {
-      vp[b] = vadd_loose(v[b], v[NN - 1 - b]);
-      vm[b] = vsub_loose(v[b], v[NN - 1 - b]);
-    }
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const bool odd = (j % 2) == 0;   // order j + 1
-      Dot<V> acc = dot_first(c.g[j][0], odd ? vp[0] : vm[0]);
-#pragma unroll
-      for (int b = 1; b < K; ++b) dot_fma(acc, c.g[j][b], odd ? vp[b] : vm[b]);
-      if (odd) dot_fma(acc, c.g[j][K], v[K]);
-      buf[fl][j][tau] = dot_value(acc);
-    }
+    for (int j = 0; j < K; ++j) buf[fl][j][tau] = t[j];
   }
   __syncthreads();
-
-  // ---- tangential reference masses: tau = t1 + (k+1) t2, each thread keeps its rows of M^
   V out[K];
-  if constexpr (D == 3) {
-    const int t1 = tau % K1, t2 = tau / K1;
-    V m1[K1];
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], buf[fl][j][K1 * t2]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], buf[fl][j][q + K1 * t2]);
-      sb2[fl][j][tau] = dot_value(acc);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], sb2[fl][j][t1]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], sb2[fl][j][t1 + K1 * q]);
-      out[j] = dot_value(acc);
-    }
-  } else {
-    V m1[K1];
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], buf[fl][j][0]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], buf[fl][j][q]);
-      out[j] = dot_value(acc);
-    }
-  }
+  line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
   // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored in patch order
   if (valid) {
@@ -231,25 +279,10 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
       pos0 = tau;
       pstride = K1 * K1;
     }
-    // W[b] = E_b + O_b and W[2k-b] = E_b - O_b, with E_b (O_b) the sum over odd
-    // (even) orders of g_j[b] s_j out_j; W[k] = E_k
+    V w[NN];
+    line_expand<K, V>(c, sj, w);
 #pragma unroll
-    for (int b = 0; b <= K; ++b) {
-      Dot<V> ev = dot_first(c.g[0][b], sj[0]);
-#pragma unroll
-      for (int j = 2; j < K; j += 2) dot_fma(ev, c.g[j][b], sj[j]);
-      if (b == K || K == 1) {
-        const V e = dot_value(ev);
-        dst[pos0 + pstride * b] = e;
-        if (b < K) dst[pos0 + pstride * (NN - 1 - b)] = e;
-      } else {
-        Dot<V> ov = dot_first(c.g[K > 1 ? 1 : 0][b], sj[K > 1 ? 1 : 0]);
-#pragma unroll
-        for (int j = 3; j < K; j += 2) dot_fma(ov, c.g[j][b], sj[j]);
-        dst[pos0 + pstride * b] = dot_merge<false>(ev, ov);
-        dst[pos0 + pstride * (NN - 1 - b)] = dot_merge<true>(ev, ov);
-      }
-    }
+    for (int bb = 0; bb < NN; ++bb) dst[pos0 + pstride * bb] = w[bb];
   }
 }
 

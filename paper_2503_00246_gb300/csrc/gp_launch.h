@@ -6,6 +6,7 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+#include "gp_brick.cuh"
 #include "gp_cell.cuh"
 #include "gp_kernels.cuh"
 
@@ -29,6 +30,9 @@ struct ApplyArgs {
   cudaEvent_t* ev = nullptr;  // optional: 3 events recorded around the two kernels
   Tiles tiles{};              // 0 fields: the defaults of default_tiles
   int which = 3;              // bit 0: face kernel, bit 1: lift kernel (the autotuner times them apart)
+  bool brick = false;         // the brick path (brick kernel + plane fixup) instead of face + lift
+  BrickArgs ba{};             // brick tables (zero-run fields are filled by the launcher)
+  PlaneArgs pa{};             // plane-fixup tables
 };
 
 // Default tile shape: about 256 threads per CTA, one item per thread.
@@ -101,6 +105,64 @@ cudaError_t apply_f32_d3(const ApplyArgs& a, cudaStream_t st);
 cudaError_t apply_ff_d2(const ApplyArgs& a, cudaStream_t st);
 cudaError_t apply_ff_d3(const ApplyArgs& a, cudaStream_t st);
 
+// Faces per chunk of the brick kernel: the tile's fb, else about 256 threads.
+template <int D, int K>
+inline int brick_fb(const Tiles& t) {
+  constexpr int L = Shape<D, K>::L;
+  const int fb = t.fb > 0 ? t.fb : Shape<D, K>::FB;
+  return fb * L <= MAX_CTA_THREADS ? fb : MAX_CTA_THREADS / L;
+}
+
+constexpr size_t BRICK_MAX_SMEM = 200 * 1024;   // dynamic shared memory the brick kernel may ask for
+
+// The brick path: brick kernel (zero-fill CTAs first), then the plane fixup as its
+// programmatic dependent.  Ar.ev (3 events) brackets the two kernels when given.
+template <int D, int K, class A>
+cudaError_t run_brick(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, cudaStream_t st) {
+  using V = typename A::V;
+  using IO = typename A::IO;
+  constexpr int L = Shape<D, K>::L;
+  const int fb = brick_fb<D, K>(Ar.tiles);
+  BrickArgs ba = Ar.ba;
+  ba.zruns = Ar.zruns;
+  ba.nzruns = Ar.nzruns;
+  ba.nzblocks = (Ar.nzruns + ZGROUP - 1) / ZGROUP;
+  const size_t smem = brick_smem<D, K, V>(ba.maxown, ba.maxcell, fb);
+  if (smem > BRICK_MAX_SMEM) return cudaErrorInvalidConfiguration;
+  static bool smem_raised[64] = {};              // per instantiation and device, raised once
+  int dev = 0;
+  if (smem > 48 * 1024 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !smem_raised[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(brick_kernel<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)BRICK_MAX_SMEM);
+    if (e != cudaSuccess) return e;
+    smem_raised[dev] = true;
+  }
+  const int grid = ba.nzblocks + ba.nbricks;
+  if (Ar.ev) cudaEventRecord(Ar.ev[0], st);
+  if (grid > 0) brick_kernel<D, K, A><<<grid, fb * L, smem, st>>>((const IO*)Ar.x, (IO*)Ar.y, Ar.add, ba, fb, c);
+  if (Ar.ev) cudaEventRecord(Ar.ev[1], st);
+  if (Ar.pa.nplane > 0 && ba.nbricks > 0) {
+    const int nb = (Ar.pa.nplane + 255) / 256;
+    if (Ar.ev) {
+      plane_fixup_kernel<D, A><<<nb, 256, 0, st>>>((IO*)Ar.y, Ar.add, Ar.pa, Ar.k);
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nb);
+      cfg.blockDim = dim3(256u);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, plane_fixup_kernel<D, A>, (IO*)Ar.y, Ar.add, Ar.pa, Ar.k);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (Ar.ev) cudaEventRecord(Ar.ev[2], st);
+  return cudaGetLastError();
+}
+
 template <int D, int K, class A>
 cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   using S = Shape<D, K>;
@@ -112,6 +174,7 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   for (int p = 0; p < K + 1; ++p)
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(Ar.m[p * (K + 1) + q]);
   for (int j = 0; j < K; ++j) c.s[j] = from_host<V>(Ar.s[j]);
+  if (Ar.brick) return run_brick<D, K, A>(Ar, c, st);
   Tiles t = Ar.tiles;
   if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
   FaceArgs fa;

@@ -12,6 +12,9 @@ namespace gp {
 
 constexpr int KMAX = 8;
 constexpr int ZRUN_MAX = 256;       // elements per zero run (one CTA pass)
+// ints per brick descriptor: first local cell, own cells, local cells, first face, faces,
+// brick coordinates bx, by, bz
+constexpr int BDESC = 8;
 
 enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
 
@@ -78,6 +81,23 @@ struct Plan {
   int part_lo = 0, part_hi = 0;
   int64_t n_global = 0, g_offset = 0, n_owned = 0, n_lower = 0;
 
+  // brick path (build_bricks): the mesh cut into bricks of bdim cells; one CTA per non-empty
+  // brick stages the cell blocks of its involved cells, evaluates every ghost face with a cell
+  // in the brick, accumulates per-cell outputs and writes its nodes (see gp_brick.cuh)
+  int bdim[3] = {0, 0, 0};        // cells per brick along each axis; bdim[0] == 0: no brick path
+  int nbx[3] = {1, 1, 1};         // bricks per axis
+  std::vector<int32_t> bdesc;     // BDESC ints per non-empty brick (see gp_brick.cuh)
+  std::vector<int32_t> bcell;     // per brick: involved-cell indices, own cells first, then halo cells
+  std::vector<int32_t> bccoord;   // parallel to bcell: packed local coords cx | cy << 8 | cz << 16 (own)
+  std::vector<uint32_t> bface;    // per brick: packed faces (axis, local K-, local K+, own flags)
+  std::vector<int32_t> bslot;     // dense brick index -> non-empty brick slot, or -1
+  std::vector<int32_t> pnode;     // 4 per plane node: compact index, lattice X, Y, Z
+  std::vector<int8_t> invmask;    // per cell: 1 if the cell is involved (K- or K+ of a ghost face)
+  int64_t pgrid = 0;              // partial-grid entries per brick slot
+  int bmax_own = 0, bmax_cell = 0, bmax_face = 0;
+  int64_t num_bricks() const { return bdim[0] == 0 ? 0 : (int64_t)bdesc.size() / BDESC; }
+  int64_t num_plane_nodes() const { return (int64_t)pnode.size() / 4; }
+
   // FP64 1D reference data
   std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
   std::vector<double> stiff;      // (k+1)^2: int_0^1 l_a' l_b' 
@@ -112,6 +132,14 @@ void reference_stiffness(int k, std::vector<double>& stiff);
 // Macro-patch 1D data: k mirror-(anti)symmetric vectors (k x (2k+1)) and weights lambda_j;
 // false if the matrix is not of rank k with the expected parities.
 bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda);
+// Brick tables for the fused face + lift kernel: picks the brick shape (largest first) whose
+// staged cell blocks and per-cell outputs fit smem_budget bytes of shared memory with values
+// of vbytes and accumulators of sbytes bytes (plus extra bytes that do not scale with the
+// brick), and fills bdim, nbx, bdesc, bcell, bccoord, bface, bslot, pnode, invmask, pgrid.
+// Returns false (bdim[0] = 0) when no shape fits; the two-kernel path is used then.
+bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_budget);
+// Dynamic shared memory of the brick kernel for the plan's brick tables.
+size_t brick_smem_bytes(const Plan& p, int vbytes, int sbytes, size_t extra);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`

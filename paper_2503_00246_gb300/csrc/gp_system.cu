@@ -448,8 +448,11 @@ gp_status gp_system_create(gp_ctx* hi, gp_ctx* lo, gp_system** out) {
   if (hi->plan.precision == GP_FP32) return fail(nullptr, GP_EINVAL, "hi must be GP_FP64 or GP_FP64_FF");
   if (hi->plan.partitioned || (lo && lo->plan.partitioned))
     return fail(nullptr, GP_EUNSUPPORTED, "the model system is built for whole meshes only");
-  if ((!hi->d_tp && hi->plan.num_faces() > 0) || (lo && !lo->d_tp && lo->plan.num_faces() > 0))
+  if (hi->no_scratch || (lo && lo->no_scratch))
     return fail(nullptr, GP_EINVAL, "the model system needs contexts created with no_scratch = 0");
+  // the system's fused gather reads the face kernel's outputs W_F: give brick-path contexts one
+  if (gpi::ensure_face_outputs(hi) != GP_OK) return fail(nullptr, GP_ENOMEM, hi->err);
+  if (lo && gpi::ensure_face_outputs(lo) != GP_OK) return fail(nullptr, GP_ENOMEM, lo->err);
   if (lo) {
     if (!lo->on_device || lo->device != hi->device) return fail(nullptr, GP_EINVAL, "lo must be on hi's device");
     if (lo->plan.precision != GP_FP32) return fail(nullptr, GP_EINVAL, "lo must be GP_FP32");

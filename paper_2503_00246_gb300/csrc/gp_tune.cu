@@ -1,6 +1,8 @@
 // Tile shapes of the face and lift launches and their autotuner.
 //
-// The tile shape is (faces per face CTA, owner cells per lift CTA, lift threads).
+// The tile shape is (faces per face CTA, owner cells per lift CTA, lift threads); on the
+// brick path only the first field counts (faces per chunk of the brick kernel), and the
+// autotuner times whole applies for it.
 // gp_autotune times each candidate on the context's own tables with CUDA events,
 // with the L2 flushed before every timed launch (the operator's operands are
 // read from HBM in a real solve), and keeps the fastest face and lift shapes.
@@ -18,7 +20,8 @@
 namespace {
 
 std::mutex g_tiles_mu;
-std::map<std::tuple<int, int, int, int>, gp::Tiles> g_tiles;
+std::map<std::tuple<int, int, int, int>, gp::Tiles> g_tiles;        // face + lift path
+std::map<std::tuple<int, int, int, int>, gp::Tiles> g_brick_tiles;  // brick path (fb only)
 
 }  // namespace
 
@@ -41,6 +44,14 @@ bool tiles_lookup(int device, int dim, int k, int precision, gp::Tiles* out) {
 void tiles_record(int device, int dim, int k, int precision, const gp::Tiles& t) {
   std::lock_guard<std::mutex> lk(g_tiles_mu);
   g_tiles[std::make_tuple(device, dim, k, precision)] = t;
+}
+
+bool brick_tiles_lookup(int device, int dim, int k, int precision, gp::Tiles* out) {
+  std::lock_guard<std::mutex> lk(g_tiles_mu);
+  auto it = g_brick_tiles.find(std::make_tuple(device, dim, k, precision));
+  if (it == g_brick_tiles.end()) return false;
+  *out = it->second;
+  return true;
 }
 
 }  // namespace gpi
@@ -190,16 +201,27 @@ gp_status gp_autotune(gp_ctx* ctx, int reps, gp_tiles* best, double* ms) {
   };
   gp::Tiles bf = cur, bl = cur;
   double tf = 1e30, tl = 1e30;
+  if (ctx->use_brick) {
+    // brick path: faces per chunk of the brick kernel, timed over whole applies
+    for (const gp::Tiles& t : face) {
+      double m;
+      if (!time_one(t, 3, m)) break;
+      if (m < tf) { tf = m; bf = t; }
+    }
+    tl = 0.0;
+  }
   for (const gp::Tiles& t : face) {
+    if (ctx->use_brick) break;
     double m;
     if (!time_one(t, 1, m)) break;
     if (m < tf) { tf = m; bf = t; }
   }
   // the lift reads the face outputs of the best face shape
-  if (e == cudaSuccess && status == GP_OK && gpi::launch(ctx, x, y, 0, st, nullptr, false, &bf, 1) != GP_OK)
+  if (!ctx->use_brick && e == cudaSuccess && status == GP_OK &&
+      gpi::launch(ctx, x, y, 0, st, nullptr, false, &bf, 1) != GP_OK)
     status = GP_ECUDA;
   for (const gp::Tiles& t : lift) {
-    if (e != cudaSuccess || status != GP_OK) break;
+    if (ctx->use_brick || e != cudaSuccess || status != GP_OK) break;
     double m;
     if (!time_one(t, 2, m)) break;
     if (m < tl) { tl = m; bl = t; }
@@ -220,7 +242,12 @@ gp_status gp_autotune(gp_ctx* ctx, int reps, gp_tiles* best, double* ms) {
   chosen.lcb = bl.lcb;
   chosen.lnt = bl.lnt;
   ctx->tiles = chosen;
-  gpi::tiles_record(ctx->device, p.dim, p.k, p.precision, chosen);
+  if (ctx->use_brick) {
+    std::lock_guard<std::mutex> lk(g_tiles_mu);
+    g_brick_tiles[std::make_tuple(ctx->device, p.dim, p.k, p.precision)] = chosen;
+  } else {
+    gpi::tiles_record(ctx->device, p.dim, p.k, p.precision, chosen);
+  }
   if (best) *best = to_abi(chosen);
   if (ms) {
     ms[0] = tf;

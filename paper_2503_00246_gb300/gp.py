@@ -21,6 +21,7 @@ GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_EDEVICE, GP_EUNSUPPORTED = range(6)
 GP_FP64, GP_FP32, GP_FP64_FF = 0, 1, 2
 GP_LS_BALLS, GP_LS_GYROID, GP_LS_CALLBACK, GP_LS_CONST = 1, 2, 3, 4
 GP_STAB_GHOST, GP_STAB_MACRO = 0, 1
+GP_PATH_AUTO, GP_PATH_FACE_LIFT, GP_PATH_BRICK = 0, 1, 2
 _STATUS = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ECUDA", 4: "GP_EDEVICE",
            5: "GP_EUNSUPPORTED"}
 
@@ -59,7 +60,7 @@ class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
                 ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int), ("stabilization", C.c_int),
-                ("no_scratch", C.c_int)]
+                ("no_scratch", C.c_int), ("kernel_path", C.c_int), ("brick_smem", C.c_int)]
 
 
 class gp_tiles(C.Structure):
