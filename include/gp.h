@@ -289,6 +289,12 @@ gp_status gp_apply_add(gp_ctx* ctx, const void* x, void* y, void* stream);
 #define GP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream);
 
+/* Kernel path of a context: *path receives GP_PATH_BRICK or GP_PATH_FACE_LIFT; on the brick
+ * path bdim (3 ints, may be NULL) receives the brick shape in cells and counts (3 int64, may
+ * be NULL) the bricks that hold faces, the plane nodes shared by several bricks and the bytes
+ * of the partial sums (the path's scratch). */
+gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* counts);
+
 /* End-to-end form with HOST buffers: copies x (n_active elements of the
  * context's precision) to the device, applies G, copies y back and waits
  * for completion.  Uses device buffers owned by the context. */

@@ -235,6 +235,27 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
   }
   c->elem = c->plan.precision == GP_FP32 ? 4 : 8;   // element size of x and y
   c->device = opts->device;
+  c->no_scratch = opts->no_scratch != 0;
+  {
+    // kernel path: the brick path when a brick shape fits the shared-memory budget
+    gp::Plan& p = c->plan;
+    const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
+    if (opts->kernel_path != GP_PATH_FACE_LIFT && p.num_faces() > 0 && !p.partitioned) {
+      const size_t budget = opts->brick_smem > 0 ? (size_t)opts->brick_smem : (size_t)100 * 1024;
+      const int fb = gpi::brick_default_fb(p.dim, p.k);
+      const size_t extra = (size_t)(p.dim == 3 ? 2 : 1) * fb * p.k * p.L * vbytes;
+      try {
+        c->use_brick = gp::build_bricks(p, (int)vbytes, (int)vbytes, extra, std::min(budget, gp::BRICK_MAX_SMEM));
+      } catch (const std::bad_alloc&) {
+        delete c;
+        return fail(nullptr, GP_ENOMEM, "host allocation failed while building the brick tables");
+      }
+    }
+    if (opts->kernel_path == GP_PATH_BRICK && !c->use_brick && p.num_faces() > 0) {
+      delete c;
+      return fail(nullptr, GP_EUNSUPPORTED, "no brick shape fits the shared-memory budget (use GP_PATH_AUTO)");
+    }
+  }
   if (opts->device >= 0) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -254,20 +275,7 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     if (e == cudaSuccess) e = upload(&c->d_lwin, p.lwin);
     if (e == cudaSuccess) e = upload(&c->d_lrow, p.lrow);
     if (e == cudaSuccess) e = upload(&c->d_zruns, zruns);
-    c->no_scratch = opts->no_scratch != 0;
-    // kernel path: the brick path when a brick shape fits the shared-memory budget
     const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
-    if (opts->kernel_path != GP_PATH_FACE_LIFT && p.num_faces() > 0 && !p.partitioned) {
-      const size_t budget = opts->brick_smem > 0 ? (size_t)opts->brick_smem : (size_t)100 * 1024;
-      const int fb = gpi::brick_default_fb(p.dim, p.k);
-      const size_t extra = (size_t)(p.dim == 3 ? 2 : 1) * fb * p.k * p.L * vbytes;
-      c->use_brick = gp::build_bricks(c->plan, (int)vbytes, (int)vbytes, extra, std::min(budget, gp::BRICK_MAX_SMEM));
-    }
-    if (opts->kernel_path == GP_PATH_BRICK && !c->use_brick && p.num_faces() > 0) {
-      free_device(c);
-      delete c;
-      return fail(nullptr, GP_EUNSUPPORTED, "no brick shape fits the shared-memory budget (use GP_PATH_AUTO)");
-    }
     if (c->use_brick) {
       std::vector<int4> pn(p.num_plane_nodes());
       std::memcpy(pn.data(), p.pnode.data(), pn.size() * sizeof(int4));
@@ -390,6 +398,20 @@ gp_status gp_partition_slabs(const gp_mesh* mesh, const gp_levelset* ls, const g
   } catch (const std::exception& e) {
     return fail(nullptr, GP_ENOMEM, e.what());
   }
+}
+
+gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* counts) {
+  if (!ctx || !path) return fail(ctx, GP_EINVAL, "null argument");
+  const gp::Plan& p = ctx->plan;
+  *path = ctx->use_brick ? GP_PATH_BRICK : GP_PATH_FACE_LIFT;
+  if (bdim)
+    for (int a = 0; a < 3; ++a) bdim[a] = ctx->use_brick ? p.bdim[a] : 0;
+  if (counts) {
+    counts[0] = ctx->use_brick ? p.num_bricks() : 0;
+    counts[1] = ctx->use_brick ? p.num_plane_nodes() : 0;
+    counts[2] = ctx->use_brick ? (int64_t)gpi::brick_scratch_bytes(ctx) : 0;
+  }
+  return GP_OK;
 }
 
 gp_status gp_reference_1d(const gp_ctx* ctx, double* mass, double* jumps, double* scale) {

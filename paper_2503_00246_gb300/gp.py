@@ -105,6 +105,7 @@ def _load():
         "gp_apply_host": ([P, P, P, P], C.c_int),
         "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_apply_batched_info": ([C.POINTER(P), C.c_int, C.c_int, i64p], C.c_int),
+        "gp_kernel_path": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int32), i64p], C.c_int),
         "gp_batch_create": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P)], C.c_int),
         "gp_batch_apply": ([P, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_batch_info": ([P, i64p, i64p], C.c_int),
@@ -137,7 +138,7 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
                "gp_system_destroy", "gp_partition_info", "gp_partition_slabs", "gp_get_tiles",
                "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup", "gp_system_cells",
-               "gp_apply_batched_info")
+               "gp_apply_batched_info", "gp_kernel_path")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -461,13 +462,14 @@ def tiles_cache_path() -> str:
 
 
 def autotune_cached(ctx: Context, reps: int = 10, path: str | None = None) -> dict:
-    """Tile shapes for ctx from the cache file, keyed by (GPU name, d, k, precision); on a miss
+    """Tile shapes for ctx from the cache file, keyed by (GPU name, d, k, precision, path); on a miss
     gp_autotune times the candidates and the result is written back.  Either way the shape is
     set on ctx and recorded in the library's table for new contexts."""
     import json
     import torch
     path = path or tiles_cache_path()
-    key = f"{torch.cuda.get_device_name(ctx.device)}|d{ctx.dim}|k{ctx.degree}|p{ctx.precision}"
+    path = gp_kernel_path(ctx)["path"]
+    key = f"{torch.cuda.get_device_name(ctx.device)}|d{ctx.dim}|k{ctx.degree}|p{ctx.precision}|path{path}"
     cache = {}
     if os.path.exists(path):
         with open(path) as fh:
@@ -475,7 +477,8 @@ def autotune_cached(ctx: Context, reps: int = 10, path: str | None = None) -> di
     if key in cache:
         tiles = cache[key]
         gp_set_tiles(ctx, tiles)
-        gp_tiles_record(ctx.device, ctx.dim, ctx.degree, ctx.precision, tiles)
+        if path == GP_PATH_FACE_LIFT:
+            gp_tiles_record(ctx.device, ctx.dim, ctx.degree, ctx.precision, tiles)
         return tiles
     tiles, _ = gp_autotune(ctx, reps)
     cache[key] = tiles
@@ -500,6 +503,15 @@ def gp_partition_slabs(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts, npar
     _check(lib.gp_partition_slabs(C.byref(mesh), C.byref(levelset), C.byref(opts), int(nparts),
                                   b.ctypes.data_as(C.POINTER(C.c_int32))))
     return b
+
+
+def gp_kernel_path(ctx: Context) -> dict:
+    """{"path": GP_PATH_*, "bdim": brick shape, "bricks", "plane_nodes", "scratch_bytes"}."""
+    path = C.c_int()
+    bd = (C.c_int32 * 3)()
+    cn = (C.c_int64 * 3)()
+    _check(lib.gp_kernel_path(ctx.handle, C.byref(path), bd, cn), ctx)
+    return {"path": path.value, "bdim": list(bd), "bricks": cn[0], "plane_nodes": cn[1], "scratch_bytes": cn[2]}
 
 
 def gp_reference_1d(ctx: Context):
@@ -535,8 +547,9 @@ def gp_version() -> str:
 
 # ------------------------------------------------------------ marshalling --
 
-def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None):
-    """gp_mesh / gp_levelset / gp_opts for a workloads.Problem (kept alive in the tuple)."""
+def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None, path: int = GP_PATH_AUTO):
+    """gp_mesh / gp_levelset / gp_opts for a workloads.Problem (kept alive in the tuple);
+    path is the kernel path (GP_PATH_*)."""
     mesh = gp_mesh()
     mesh.dim = pr.dim
     for a in range(3):
@@ -570,12 +583,15 @@ def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=N
     opts.stabilization = int(getattr(pr, "stabilization", 0))
     if part is not None:
         opts.part_lo, opts.part_hi = int(part[0]), int(part[1])
+    opts.kernel_path = int(path)
     return mesh, ls, opts, keep
 
 
-def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None) -> Context:
-    """Context for a workloads.Problem; part = (layer_lo, layer_hi) selects a slab partition."""
-    mesh, ls, opts, keep = structs_for(pr, precision, device, part)
+def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None,
+                  path: int = GP_PATH_AUTO) -> Context:
+    """Context for a workloads.Problem; part = (layer_lo, layer_hi) selects a slab partition,
+    path the kernel path (GP_PATH_AUTO, GP_PATH_FACE_LIFT, GP_PATH_BRICK)."""
+    mesh, ls, opts, keep = structs_for(pr, precision, device, part, path)
     return gp_setup(mesh, ls, opts)
 
 

@@ -187,7 +187,8 @@ def test_batched(gplib, cuda, prec):
     probs = [W.small_ball(3, 10, 2, seed=21), W.small_ball(3, 13, 4, seed=22),
              W.small_ball(3, 8, 6, seed=23), W.small_ball(2, 18, 3, seed=24)]
     nrhs = 2
-    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    # the batch runs the face + lift kernels: its outputs equal those of face + lift contexts
+    ctxs = [gplib.setup_problem(p, precision=prec, path=gplib.GP_PATH_FACE_LIFT) for p in probs]
     call = _batched_c(gplib)
     oracles = [Oracle(p) for p in probs]
     stream = cuda.cuda.current_stream().cuda_stream
@@ -213,7 +214,7 @@ def test_batched_workload_full_size(gplib, cuda, prec):
     the largest and one of every degree)."""
     probs = W.batched_3d()
     nrhs = 4
-    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    ctxs = [gplib.setup_problem(p, precision=prec, path=gplib.GP_PATH_FACE_LIFT) for p in probs]
     dt = cuda.float32 if prec == 1 else cuda.float64
     gen = cuda.Generator(device="cuda")
     gen.manual_seed(W.BASE_SEED + 5000)
@@ -321,11 +322,12 @@ def test_gyroid_128_k4_sampled(gplib, cuda, prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_batch_graph_replays(gplib, cuda, prec):
     """gp_batch_*: problems of mixed k and dimension, 3 right-hand sides, three graph replays
-    with fresh inputs; every vector equals gp_apply's bitwise and the oracle within tolerance."""
+    with fresh inputs; every vector equals gp_apply's bitwise (face + lift contexts: the batch
+    runs the same kernels) and the oracle within tolerance."""
     probs = [W.small_ball(3, 10, 2, seed=31), W.small_ball(3, 12, 3, seed=32), W.small_ball(3, 8, 5, seed=33),
              W.small_ball(2, 16, 4, seed=34), W.small_ball(3, 11, 3, seed=35), W.small_ball(3, 9, 2, seed=36)]
     nrhs = 3
-    ctxs = [gplib.setup_problem(p, precision=prec) for p in probs]
+    ctxs = [gplib.setup_problem(p, precision=prec, path=gplib.GP_PATH_FACE_LIFT) for p in probs]
     batch = gplib.gp_batch_create(ctxs, nrhs)
     ngroups, scratch = gplib.gp_batch_info(batch)
     assert ngroups == 4 and scratch > 0     # (3D,k2) x2, (3D,k3) x2, (3D,k5), (2D,k4)

@@ -1,6 +1,7 @@
 """Tile shapes and the autotuner on the GPU: the shape changes the speed, never the
 result (every DoF sums its face contributions in one fixed order), so every shape
-must give a bitwise-equal y, and so must a batch built from tuned contexts."""
+must give a bitwise-equal y on both kernel paths (face + lift, brick), and so must a
+batch built from tuned contexts."""
 import numpy as np
 import pytest
 
@@ -27,11 +28,16 @@ def _run(gp, torch, ctx, x, prec, add=False):
     return yd.cpu().numpy()
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("dim,n,k", [(3, 14, 3), (2, 40, 4), (3, 10, 1), (3, 8, 6)])
-def test_every_shape_is_bitwise_equal(gplib, cuda, prec, dim, n, k):
+def test_every_shape_is_bitwise_equal(gplib, cuda, prec, dim, n, k, path):
     pr = W.small_ball(dim, n, k, seed=40 + k)
-    ctx = gplib.setup_problem(pr, precision=prec)
+    try:
+        ctx = gplib.setup_problem(pr, precision=prec, path=path)
+    except gplib.GpError as e:          # the brick path does not fit every (k, precision)
+        assert path == gplib.GP_PATH_BRICK and e.status == gplib.GP_EUNSUPPORTED
+        pytest.skip("no brick shape fits")
     x = W.x_vectors(pr, ctx.n_active)[0]
     ref = _run(gplib, cuda, ctx, x, prec)
     ref_add = _run(gplib, cuda, ctx, x, prec, add=True)
@@ -54,7 +60,7 @@ def test_every_shape_is_bitwise_equal(gplib, cuda, prec, dim, n, k):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_autotune_records_and_keeps_result(gplib, cuda, prec):
     pr = W.small_ball(3, 24, 3, seed=5)
-    ctx = gplib.setup_problem(pr, precision=prec)
+    ctx = gplib.setup_problem(pr, precision=prec, path=gplib.GP_PATH_FACE_LIFT)
     x = W.x_vectors(pr, ctx.n_active)[0]
     ref = _run(gplib, cuda, ctx, x, prec)
     tiles, (tf, tl) = gplib.gp_autotune(ctx, reps=3)
@@ -63,13 +69,21 @@ def test_autotune_records_and_keeps_result(gplib, cuda, prec):
     assert gplib.gp_tiles_lookup(0, 3, 3, prec) == tiles
     assert np.array_equal(_run(gplib, cuda, ctx, x, prec), ref)
     # a new context of the same (d, k, precision) starts from the table
-    ctx2 = gplib.setup_problem(W.small_ball(3, 16, 3, seed=6), precision=prec)
+    ctx2 = gplib.setup_problem(W.small_ball(3, 16, 3, seed=6), precision=prec, path=gplib.GP_PATH_FACE_LIFT)
     assert gplib.gp_get_tiles(ctx2) == tiles
+    # brick path: the autotuner picks the faces per chunk over whole applies; the result stays
+    cb = gplib.setup_problem(pr, precision=prec, path=gplib.GP_PATH_BRICK)
+    yb = _run(gplib, cuda, cb, x, prec)
+    tb, (tbf, tbl) = gplib.gp_autotune(cb, reps=3)
+    assert tbf > 0 and tbl == 0.0 and gplib.gp_get_tiles(cb) == tb
+    assert np.array_equal(_run(gplib, cuda, cb, x, prec), yb)
+    cb2 = gplib.setup_problem(W.small_ball(3, 16, 3, seed=6), precision=prec, path=gplib.GP_PATH_BRICK)
+    assert gplib.gp_get_tiles(cb2)["faces_per_cta"] == tb["faces_per_cta"]
 
 
 def test_batch_with_tuned_groups_equals_single_applies(gplib, cuda):
     probs = [W.small_ball(3, 12 + 2 * i, 2 + i % 3, seed=60 + i) for i in range(6)]
-    ctxs = [gplib.setup_problem(pr, precision=1) for pr in probs]
+    ctxs = [gplib.setup_problem(pr, precision=1, path=gplib.GP_PATH_FACE_LIFT) for pr in probs]
     gplib.gp_set_tiles(ctxs[0], {"faces_per_cta": 3, "lift_cells_per_cta": 5, "lift_threads": 64})
     gplib.gp_set_tiles(ctxs[1], {"faces_per_cta": 20, "lift_cells_per_cta": 60, "lift_threads": 512})
     nrhs = 2
@@ -93,13 +107,13 @@ def test_autotune_cache_file(gplib, cuda, tmp_path):
     import json
     path = str(tmp_path / "tiles.json")
     pr = W.small_ball(3, 16, 2, seed=12)
-    ctx = gplib.setup_problem(pr, precision=1)
+    ctx = gplib.setup_problem(pr, precision=1, path=gplib.GP_PATH_FACE_LIFT)
     t1 = gplib.autotune_cached(ctx, reps=2, path=path)
     data = json.load(open(path))
-    assert len(data) == 1 and list(data.values())[0] == t1 and "|d3|k2|p1" in list(data)[0]
+    assert len(data) == 1 and list(data.values())[0] == t1 and "|d3|k2|p1|path1" in list(data)[0]
     # a hit sets the stored shape without timing
     data[list(data)[0]] = {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
     json.dump(data, open(path, "w"))
-    ctx2 = gplib.setup_problem(pr, precision=1)
+    ctx2 = gplib.setup_problem(pr, precision=1, path=gplib.GP_PATH_FACE_LIFT)
     assert gplib.autotune_cached(ctx2, path=path) == {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
     assert gplib.gp_get_tiles(ctx2) == {"faces_per_cta": 5, "lift_cells_per_cta": 7, "lift_threads": 96}
