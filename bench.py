@@ -484,7 +484,9 @@ def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tun
     oracle on sampled rows (when o is given)."""
     stream = torch.cuda.current_stream()
     steps = args.steps if steps is None else steps
-    ctx = gp.setup_problem(pr, precision=prec, device=dev.index or 0)
+    path = {"auto": gp.GP_PATH_AUTO, "face_lift": gp.GP_PATH_FACE_LIFT, "brick": gp.GP_PATH_BRICK}[args.path]
+    ctx = gp.setup_problem(pr, precision=prec, device=dev.index or 0, path=path)
+    kp = gp.gp_kernel_path(ctx)
     tiles = None
     if tune and args.tune_reps > 0:          # tile shape picked on this GPU, before any timing
         chosen, (tf, tl) = gp.gp_autotune(ctx, args.tune_reps)
@@ -519,7 +521,7 @@ def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tun
     ms_face, ms_lift, calls = gp.gp_profile_read(ctx)
     gp.gp_profile_enable(ctx, False)
     err = _sampled_error(o, x_np, y, prec, args.check_rows) if (o is not None and args.check) else None
-    rec = {"ctx_sizes": (ctx.n_active, ctx.n_faces, ctx.n_touched), "t_step": t_step,
+    rec = {"ctx_sizes": (ctx.n_active, ctx.n_faces, ctx.n_touched), "t_step": t_step, "kernel_path": kp,
            "wall_ms_per_step": wall * 1e3 / steps, "face_ms": ms_face / calls, "lift_ms": ms_lift / calls,
            "tiles": tiles, "rel_err_vs_oracle": err}
     if e2e:
@@ -556,7 +558,9 @@ def form_summary(rec, pr, prec, gp, hbm, peak_src, ws=1):
     peak = {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: fp32_peak / FF_OPS_PER_FMA}[prec]
     kname = {gp.GP_FP64: "double", gp.GP_FP32: "float", gp.GP_FP64_FF: "ff64"}[prec]
     flop_face = _flops_face(d, k, nf)
-    roof = {"bound": "alu", "kernel": f"face_kernel<{d},{k},{kname}>",
+    brick = rec["kernel_path"]["path"] == gp.GP_PATH_BRICK
+    kernels = ("brick_kernel", "plane_fixup_kernel") if brick else ("face_kernel", "lift_kernel")
+    roof = {"bound": "alu", "kernel": f"{kernels[0]}<{d},{k},{kname}>",
             "achieved": flop_face / (rec["face_ms"] * 1e-3) / 1e12 if rec["face_ms"] > 0 else None,
             "unit": "TFLOP/s", "peak": peak,
             "peak_source": {gp.GP_FP64: "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz x 2 flop",
@@ -569,7 +573,8 @@ def form_summary(rec, pr, prec, gp, hbm, peak_src, ws=1):
     out = {"value": ws * n_active / (t * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": t,
            "wall_ms_per_step": rec["wall_ms_per_step"],
            "ghost_faces_per_s": ws * nf / (t * 1e-3),
-           "kernel_ms": {"face": rec["face_ms"], "lift": rec["lift_ms"]},
+           "kernel_ms": {kernels[0]: rec["face_ms"], kernels[1]: rec["lift_ms"]},
+           "kernel_path": rec["kernel_path"],
            "apply_hbm": {"achieved": alg / (t * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg / (t * 1e-3) / 1e9 / hbm, "peak_source": peak_src,
                          "algorithmic_bytes": alg,
@@ -653,7 +658,8 @@ def run_gpu(args):
         "rel_err_vs_oracle": r["rel_err_vs_oracle"],
         "tiles": r["tiles"],
         "forms": {tags[p]: {k2: forms[p][k2] for k2 in ("value", "ms_per_step", "kernel_ms", "apply_hbm", "roofline",
-                                                      "rel_err_vs_oracle", "e2e", "ghost_faces_per_s", "tiles")}
+                                                      "rel_err_vs_oracle", "e2e", "ghost_faces_per_s", "tiles",
+                                                      "kernel_path")}
                   for p in precs},
         "error_check": f"max |y - y_ref| / max |y_ref| over ~{args.check_rows} sampled rows plus the patches of "
                        "sampled faces, FP64 oracle (explicit face matrices); FP32 against the oracle applied to x "
@@ -819,6 +825,8 @@ def main():
     ap.add_argument("--precision", default="all", choices=["fp64", "fp32", "ff", "all"])
     ap.add_argument("--check-rows", type=int, default=2000, help="sampled rows of the oracle error check")
     ap.add_argument("--no-sweep", action="store_true", help="leave out the bounded 96^3 degree sweep")
+    ap.add_argument("--path", default="auto", choices=["auto", "face_lift", "brick"],
+                    help="kernel path of the single-problem applies (gp_opts.kernel_path)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", dest="check", action="store_false")
