@@ -195,7 +195,8 @@ def run_profile(args):
     from paper_2503_00246_gb300 import gp, workloads as W
     pr = WORKLOADS[args.workload](W)
     prec = {"fp64": gp.GP_FP64, "fp32": gp.GP_FP32, "ff": gp.GP_FP64_FF, "all": gp.GP_FP64_FF}[args.precision]
-    ctx = gp.setup_problem(pr, precision=prec, device=0)
+    path = {"auto": gp.GP_PATH_AUTO, "face_lift": gp.GP_PATH_FACE_LIFT, "brick": gp.GP_PATH_BRICK}[args.path]
+    ctx = gp.setup_problem(pr, precision=prec, device=0, path=path)
     tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     x = torch.tensor(W.x_vectors(pr, ctx.n_active)[0], dtype=tdt, device="cuda")
     y = torch.empty_like(x)
@@ -208,7 +209,7 @@ def run_profile(args):
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"workload": args.workload, "precision": args.precision, "n_active": ctx.n_active,
                       "n_faces": ctx.n_faces, "n_touched": ctx.n_touched, "applies": args.reps,
-                      "tiles": tiles}))
+                      "tiles": tiles, "kernel_path": gp.gp_kernel_path(ctx)}))
 
 
 def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):

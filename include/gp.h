@@ -133,7 +133,8 @@ typedef struct {
  *                      (DoFs on the boundary planes between bricks go through a small buffer of
  *                      partial sums and a second kernel); GP_EUNSUPPORTED from gp_setup when no
  *                      brick shape fits the shared-memory budget;
- *   GP_PATH_AUTO       the brick path when a brick shape fits, else face + lift.
+ *   GP_PATH_AUTO       the path this build measured fastest on the benchmark workloads:
+ *                      face + lift.
  * Both are deterministic: repeated applies are bitwise identical. */
 enum { GP_PATH_AUTO = 0, GP_PATH_FACE_LIFT = 1, GP_PATH_BRICK = 2 };
 

@@ -73,17 +73,16 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 
 void free_device(gp_ctx* c) {
   void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow, c->d_zruns, c->d_tp, c->d_xh, c->d_yh,
-                  c->d_bdesc, c->d_bcell, c->d_bccoord, c->d_bface, c->d_rowtab, c->d_bslot,
-                  c->d_pnode, c->d_invmask, c->d_part};
+                  c->d_bdesc, c->d_bcell, c->d_bccoord, c->d_bface, c->d_rowtab,
+                  c->d_pnode, c->d_poff, c->d_pslot, c->d_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_frows = c->d_lwin = c->d_lrow = nullptr;
   c->d_zruns = nullptr;
   c->d_tp = c->d_xh = c->d_yh = nullptr;
-  c->d_bdesc = c->d_bcell = c->d_bccoord = c->d_rowtab = c->d_bslot = nullptr;
+  c->d_bdesc = c->d_bcell = c->d_bccoord = c->d_rowtab = nullptr;
+  c->d_pnode = c->d_poff = c->d_pslot = nullptr;
   c->d_bface = nullptr;
-  c->d_pnode = nullptr;
-  c->d_invmask = nullptr;
   c->d_part = nullptr;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
@@ -154,29 +153,17 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
     ba.pgrid = p.pgrid;
     ba.maxcell = p.bmax_cell;
     ba.maxown = p.bmax_own;
+    for (int ax = 0; ax < 3; ++ax) {
+      ba.bdim[ax] = p.bdim[ax];
+      ba.gstride[ax] = p.gstride[ax];
+      for (int side = 0; side < 2; ++side) ba.goff[ax][side] = p.goff[ax][side];
+    }
     gp::PlaneArgs& pa = a.pa;
     pa.pnode = c->d_pnode;
+    pa.poff = c->d_poff;
+    pa.pslot = c->d_pslot;
     pa.nplane = (int32_t)p.num_plane_nodes();
     pa.part = ba.part;
-    pa.bslot = c->d_bslot;
-    pa.invmask = c->d_invmask;
-    pa.n = p.n;
-    pa.pgrid = p.pgrid;
-    // box-face grids of a brick: axis a, side 0 (lower) and 1 (upper); rows along the first
-    // other axis u0, (bdim[u0] k + 1) entries each
-    int32_t off = 0;
-    for (int ax = 0; ax < 3; ++ax) {
-      ba.bdim[ax] = pa.bdim[ax] = p.bdim[ax];
-      pa.nbx[ax] = p.nbx[ax];
-      const int u0 = ax == 0 ? 1 : 0, u1 = ax == 2 ? 1 : 2;
-      ba.gstride[ax] = pa.gstride[ax] = p.bdim[u0] * p.k + 1;
-      const int32_t e2 = ax < p.dim ? (p.bdim[u0] * p.k + 1) * (p.dim == 3 ? p.bdim[u1] * p.k + 1 : 1) : 0;
-      for (int side = 0; side < 2; ++side) {
-        ba.goff[ax][side] = pa.goff[ax][side] = off;
-        off += e2;
-      }
-    }
-    if (off != p.pgrid) return fail(c, GP_EINVAL, "internal: brick partial grid size");
   }
   cudaError_t e;
   if (p.precision == GP_FP64)
@@ -240,10 +227,10 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     // kernel path: the brick path when a brick shape fits the shared-memory budget
     gp::Plan& p = c->plan;
     const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
-    if (opts->kernel_path != GP_PATH_FACE_LIFT && p.num_faces() > 0 && !p.partitioned) {
+    if (opts->kernel_path == GP_PATH_BRICK && p.num_faces() > 0 && !p.partitioned) {
       const size_t budget = opts->brick_smem > 0 ? (size_t)opts->brick_smem : (size_t)100 * 1024;
       const int fb = gpi::brick_default_fb(p.dim, p.k);
-      const size_t extra = (size_t)(p.dim == 3 ? 2 : 1) * fb * p.k * p.L * vbytes;
+      const size_t extra = (size_t)(p.dim == 3 ? 2 : 1) * fb * p.k * p.L * vbytes;   // jump planes
       try {
         c->use_brick = gp::build_bricks(p, (int)vbytes, (int)vbytes, extra, std::min(budget, gp::BRICK_MAX_SMEM));
       } catch (const std::bad_alloc&) {
@@ -277,16 +264,14 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     if (e == cudaSuccess) e = upload(&c->d_zruns, zruns);
     const size_t vbytes = p.precision == GP_FP32 ? 4 : 8;
     if (c->use_brick) {
-      std::vector<int4> pn(p.num_plane_nodes());
-      std::memcpy(pn.data(), p.pnode.data(), pn.size() * sizeof(int4));
       if (e == cudaSuccess) e = upload(&c->d_bdesc, p.bdesc);
       if (e == cudaSuccess) e = upload(&c->d_bcell, p.bcell);
       if (e == cudaSuccess) e = upload(&c->d_bccoord, p.bccoord);
       if (e == cudaSuccess) e = upload(&c->d_bface, p.bface);
       if (e == cudaSuccess) e = upload(&c->d_rowtab, p.rowtab);
-      if (e == cudaSuccess) e = upload(&c->d_bslot, p.bslot);
-      if (e == cudaSuccess) e = upload(&c->d_pnode, pn);
-      if (e == cudaSuccess) e = upload(&c->d_invmask, p.invmask);
+      if (e == cudaSuccess) e = upload(&c->d_pnode, p.pnode);
+      if (e == cudaSuccess) e = upload(&c->d_poff, p.poff);
+      if (e == cudaSuccess) e = upload(&c->d_pslot, p.pslot);
       const size_t part_bytes = gpi::brick_scratch_bytes(c);
       if (e == cudaSuccess && part_bytes > 0 && !opts->no_scratch) e = cudaMalloc(&c->d_part, part_bytes);
     }

@@ -22,8 +22,9 @@
 //      values, box face (a, side) at goff[a][side]; a node on several box faces uses the one
 //      of the lowest axis).
 // plane_fixup_kernel then adds, for every plane node, the partials of the bricks holding
-// involved cells that contain it, in increasing brick index, and writes y.  No atomics:
-// bitwise reproducible, and independent of the faces per chunk.
+// involved cells that contain it, in increasing brick index (the host lists their grid
+// entries per node), and writes y.  No atomics: bitwise reproducible, and independent of the
+// faces per chunk.
 // Extra CTAs at the front of the brick grid zero-fill the active DoFs no face touches.
 #pragma once
 
@@ -56,27 +57,52 @@ struct BrickArgs {
 };
 
 struct PlaneArgs {
-  const int4* pnode;       // plane nodes: compact index, lattice X, Y, Z
+  const int32_t* pnode;    // per plane node: compact index of the DoF
+  const int32_t* poff;     // plane nodes + 1: offsets into pslot
+  const int32_t* pslot;    // partial-grid entries to add, per node in increasing brick index
   int32_t nplane;
   const void* part;        // partial grids, V values
-  const int32_t* bslot;    // dense brick index -> slot (-1: empty)
-  const int8_t* invmask;   // per cell: involved
-  int32_t n;
-  int32_t bdim[3], nbx[3];
-  int64_t pgrid;
-  int32_t goff[3][2];
-  int32_t gstride[3];
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
 // dynamic shared memory of the brick kernel: per-cell output accumulators of the own cells,
-// the staged x blocks of all local cells, and the jump planes of fb faces
+// the staged x blocks of all local cells, the own cells' coordinates, and one region that
+// holds first the local cells' row starts (staging), then the jump planes of fb faces (face
+// loop), then the own cells' row starts (output)
+template <int D, int K, typename V>
+__host__ __device__ constexpr size_t brick_smem_region(int maxcell, int fb) {
+  const size_t planes = (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
+  const size_t rows = (size_t)maxcell * Shape<D, K>::L * sizeof(int32_t);
+  return planes > rows ? planes : rows;
+}
 template <int D, int K, typename V>
 __host__ __device__ constexpr size_t brick_smem(int maxown, int maxcell, int fb) {
   constexpr int NB = (D == 3) ? (K + 1) * (K + 1) * (K + 1) : (K + 1) * (K + 1);
   return align16((size_t)maxown * NB * sizeof(Sum<V>)) + align16((size_t)maxcell * NB * sizeof(V)) +
-         (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
+         align16((size_t)maxown * sizeof(int32_t)) + brick_smem_region<D, K, V>(maxcell, fb);
+}
+
+// Row starts of `count` local cells (from local cell `first`): rows[i] = rowtab of the cell's
+// involved index, i < count * L; four independent loads in flight per thread.
+template <int L>
+__device__ __forceinline__ void load_rows(int32_t* rows, const int32_t* __restrict__ bcell,
+                                          const int32_t* __restrict__ rowtab, const int count, const int t,
+                                          const int nt) {
+  const int total = count * L;
+  for (int base = t; base < total; base += 4 * nt) {
+    int32_t inv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * nt;
+      inv[u] = i < total ? __ldg(bcell + i / L) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * nt;
+      if (i < total) rows[i] = __ldg(rowtab + (size_t)inv[u] * L + (i % L));
+    }
+  }
 }
 
 // position of node (normal index bn, tangential index tau) of a face with normal `axis` in a
@@ -120,30 +146,51 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
   __shared__ int sd[BRICK_DESC];
   __shared__ V sm[K1][K1];
   __shared__ short cmap[BRICK_CMAP];
-  if (t < BRICK_DESC) sd[t] = __ldg(ba.bdesc + (size_t)brick * BRICK_DESC + t);
+  for (int i = t; i < BRICK_DESC; i += nt) sd[i] = __ldg(ba.bdesc + (size_t)brick * BRICK_DESC + i);
   for (int i = t; i < K1 * K1; i += nt) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
   for (int i = t; i < BRICK_CMAP; i += nt) cmap[i] = -1;
   __syncthreads();
   const int cell_off = sd[0], nown = sd[1], ncell = sd[2], face_off = sd[3], nface = sd[4];
   const int BX = ba.bdim[0], BY = ba.bdim[1], BZ = ba.bdim[2];
   extern __shared__ __align__(16) unsigned char gp_dyn_smem[];
-  Sum<V>* ys = reinterpret_cast<Sum<V>*>(gp_dyn_smem);
-  V* xs = reinterpret_cast<V*>(gp_dyn_smem + align16((size_t)ba.maxown * NB * sizeof(Sum<V>)));
-  Plane* buf = reinterpret_cast<Plane*>(reinterpret_cast<unsigned char*>(xs) +
-                                        align16((size_t)ba.maxcell * NB * sizeof(V)));
+  unsigned char* p0 = gp_dyn_smem;
+  Sum<V>* ys = reinterpret_cast<Sum<V>*>(p0);
+  p0 += align16((size_t)ba.maxown * NB * sizeof(Sum<V>));
+  V* xs = reinterpret_cast<V*>(p0);
+  p0 += align16((size_t)ba.maxcell * NB * sizeof(V));
+  int32_t* scc = reinterpret_cast<int32_t*>(p0);
+  p0 += align16((size_t)ba.maxown * sizeof(int32_t));
+  int32_t* srow = reinterpret_cast<int32_t*>(p0);          // region: row starts ...
+  Plane* buf = reinterpret_cast<Plane*>(p0);               // ... or jump planes
   Plane* sb2 = buf + fb;
 
-  // ---- own-cell map, zero accumulators, staged x blocks
+  // ---- own-cell map and coordinates, zero accumulators, row starts, staged x blocks
   for (int i = t; i < nown; i += nt) {
     const int cc = __ldg(ba.bccoord + cell_off + i);
+    scc[i] = cc;
     cmap[(cc & 255) + BX * (((cc >> 8) & 255) + BY * (cc >> 16))] = (short)i;
   }
   for (int i = t; i < nown * NB; i += nt) ys[i] = sum_zero<V>();
-  for (int i = t; i < ncell * NB; i += nt) {
-    const int lc = i / NB, e = i - lc * NB;
-    const int p = e % K1, row = e / K1;
-    const int32_t start = __ldg(ba.rowtab + (size_t)__ldg(ba.bcell + cell_off + lc) * L + row);
-    xs[i] = from_io(__ldg(x + start + p), (V*)nullptr);
+  load_rows<L>(srow, ba.bcell + cell_off, ba.rowtab, ncell, t, nt);
+  __syncthreads();
+  {
+    const int total = ncell * NB;
+    for (int base = t; base < total; base += 8 * nt) {
+      IO v8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = base + u * nt;
+        if (i < total) {
+          const int lc = i / NB, e = i - lc * NB;
+          v8[u] = __ldg(x + srow[lc * L + e / K1] + (e % K1));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = base + u * nt;
+        if (i < total) xs[i] = from_io(v8[u], (V*)nullptr);
+      }
+    }
   }
   __syncthreads();
 
@@ -204,12 +251,14 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
   }
 
   // ---- nodes of the own cells: sum of the blocks of the own cells that contain the node
+  load_rows<L>(srow, ba.bcell + cell_off, ba.rowtab, nown, t, nt);   // the face loop has ended
+  __syncthreads();
   const int bc[3] = {sd[5] * BX, sd[6] * BY, sd[7] * BZ};   // first cell of the brick
   const int bd[3] = {BX, BY, BZ};
   for (int i = t; i < nown * NB; i += nt) {
     const int lc = i / NB, e = i - lc * NB;
     const int pc[3] = {e % K1, (e / K1) % K1, (D == 3) ? e / (K1 * K1) : 0};
-    const int cc = __ldg(ba.bccoord + cell_off + lc);
+    const int cc = scc[lc];
     const int cl[3] = {cc & 255, (cc >> 8) & 255, cc >> 16};
     // local cells that contain the node: per axis cl - 1 (p = 0), cl, cl + 1 (p = k)
     int lo3[3], hi3[3];
@@ -244,7 +293,7 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
     }
     if (pa < 0) {
       const int row = (D == 3) ? pc[1] + K1 * pc[2] : pc[1];
-      const int32_t dst = __ldg(ba.rowtab + (size_t)__ldg(ba.bcell + cell_off + lc) * L + row) + pc[0];
+      const int32_t dst = srow[lc * L + row] + pc[0];
       y[dst] = to_io(add ? vadd(from_io(y[dst], (V*)nullptr), val) : val, (IO*)nullptr);
     } else {
       const int side = X[pa] == bc[pa] * K ? 0 : 1;
@@ -257,57 +306,24 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
 
 // One thread per plane node: the partials of the bricks holding involved cells that contain
 // the node, summed in increasing brick index, into y.
-template <int D, class A>
+template <class A>
 __global__ void __launch_bounds__(256)
-plane_fixup_kernel(typename A::IO* __restrict__ y, const int add, const PlaneArgs pa, const int k) {
+plane_fixup_kernel(typename A::IO* __restrict__ y, const int add, const PlaneArgs pa) {
   using V = typename A::V;
   using IO = typename A::IO;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int4 rec = make_int4(0, 0, 0, 0);
-  if (i < pa.nplane) rec = __ldg(pa.pnode + i);
+  int ci = 0, s0 = 0, s1 = 0;
+  if (i < pa.nplane) {
+    ci = __ldg(pa.pnode + i);
+    s0 = __ldg(pa.poff + i);
+    s1 = __ldg(pa.poff + i + 1);
+  }
   // the brick kernel's partials and y writes are complete after this wait
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (i >= pa.nplane) return;
-  const int X[3] = {rec.y, rec.z, rec.w};
-  int c0[3], c1[3], b0[3], b1[3], axis = -1;
-#pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    if (u < D) {
-      const bool on = X[u] % k == 0;
-      c0[u] = on ? max(X[u] / k - 1, 0) : X[u] / k;
-      c1[u] = on ? min(X[u] / k, pa.n - 1) : X[u] / k;
-      if (axis < 0 && X[u] % (pa.bdim[u] * k) == 0 && X[u] > 0 && X[u] < pa.n * k) axis = u;
-    } else {
-      c0[u] = c1[u] = 0;
-    }
-    b0[u] = c0[u] / pa.bdim[u];
-    b1[u] = c1[u] / pa.bdim[u];
-  }
-  const int u0 = axis == 0 ? 1 : 0, u1 = axis == 2 ? 1 : 2;
   const V* part = reinterpret_cast<const V*>(pa.part);
-  V s = vzero<V>();
-  bool first = true;
-  for (int bz = b0[2]; bz <= b1[2]; ++bz)
-    for (int by = b0[1]; by <= b1[1]; ++by)
-      for (int bx = b0[0]; bx <= b1[0]; ++bx) {
-        const int bb[3] = {bx, by, bz};
-        bool found = false;
-        for (int cz = c0[2]; cz <= c1[2]; ++cz)
-          for (int cy = c0[1]; cy <= c1[1]; ++cy)
-            for (int cx = c0[0]; cx <= c1[0]; ++cx)
-              if (cx / pa.bdim[0] == bx && cy / pa.bdim[1] == by && cz / pa.bdim[2] == bz &&
-                  __ldg(pa.invmask + cx + (size_t)pa.n * (cy + (size_t)(D == 3 ? pa.n : 0) * cz)))
-                found = true;
-        if (!found) continue;
-        const int slot = __ldg(pa.bslot + bx + (size_t)pa.nbx[0] * (by + (size_t)pa.nbx[1] * bz));
-        const int side = X[axis] == bb[axis] * pa.bdim[axis] * k ? 0 : 1;
-        const int g = (X[u0] - bb[u0] * pa.bdim[u0] * k) +
-                      ((D == 3) ? pa.gstride[axis] * (X[u1] - bb[u1] * pa.bdim[u1] * k) : 0);
-        const V v = part[(size_t)slot * pa.pgrid + pa.goff[axis][side] + g];
-        s = first ? v : vadd(s, v);
-        first = false;
-      }
-  const int ci = rec.x;
+  V s = part[__ldg(pa.pslot + s0)];
+  for (int j = s0 + 1; j < s1; ++j) s = vadd(s, part[__ldg(pa.pslot + j)]);
   y[ci] = to_io(add ? vadd(from_io(y[ci], (V*)nullptr), s) : s, (IO*)nullptr);
 }
 

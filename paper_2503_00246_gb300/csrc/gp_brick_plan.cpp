@@ -34,11 +34,6 @@ int64_t grid_entries(int d, const int b[3], int k) {
 
 }  // namespace
 
-size_t brick_smem_bytes(const Plan& p, int vbytes, int sbytes, size_t extra) {
-  const int64_t nb = ipow_host(p.k + 1, p.dim);
-  return (size_t)p.bmax_cell * nb * vbytes + (size_t)p.bmax_own * nb * sbytes + extra;
-}
-
 bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_budget) {
   const int d = p.dim, n = p.n, k = p.k, L = p.L;
   p.bdim[0] = p.bdim[1] = p.bdim[2] = 0;
@@ -48,7 +43,8 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
   p.bface.clear();
   p.bslot.clear();
   p.pnode.clear();
-  p.invmask.clear();
+  p.poff.clear();
+  p.pslot.clear();
   const int64_t nf = p.num_faces();
   if (nf == 0 || p.partitioned) return false;
   std::vector<BrickShape> shapes;
@@ -103,7 +99,10 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
       max_cell = std::max(max_cell, (int)(own[b].size() + halo[b].size()));
       max_face = std::max(max_face, (int)faces_of[b].size());
     }
-    const size_t need = (size_t)max_cell * nbl * vbytes + (size_t)max_own * nbl * sbytes + extra;
+    // the kernel's layout: accumulators, x blocks, own coordinates, then one region for either
+    // the local row starts or the jump planes (extra bytes), each rounded up to 16 bytes
+    const size_t need = (size_t)max_cell * nbl * vbytes + (size_t)max_own * nbl * sbytes + (size_t)max_own * 4 +
+                        std::max(extra, (size_t)max_cell * L * 4) + 48;
     const bool last = si + 1 == shapes.size();
     if (max_cell >= 1024 || (need > smem_budget && !last)) continue;
     if (need > smem_budget) return false;
@@ -162,9 +161,23 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
     break;
   }
   if (p.bdim[0] == 0) return false;
-  // ---- involved cells and the plane nodes (touched nodes on a brick boundary inside the mesh)
-  p.invmask.assign(p.ncell, 0);
-  for (int64_t c : p.inv_cells) p.invmask[c] = 1;
+  // ---- partial grids of a brick: for axis a and side (0 lower, 1 upper) one entry per node of
+  // the box face, rows along the first other axis u0 (bdim[u0] k + 1 entries each)
+  {
+    int32_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int u0 = a == 0 ? 1 : 0, u1 = a == 2 ? 1 : 2;
+      p.gstride[a] = p.bdim[u0] * k + 1;
+      const int32_t e = a < d ? (p.bdim[u0] * k + 1) * (d == 3 ? p.bdim[u1] * k + 1 : 1) : 0;
+      for (int side = 0; side < 2; ++side) {
+        p.goff[a][side] = off;
+        off += e;
+      }
+    }
+    if (off != p.pgrid) { p.bdim[0] = 0; return false; }
+  }
+  std::vector<uint8_t> invmask(p.ncell, 0);
+  for (int64_t c : p.inv_cells) invmask[c] = 1;
   const int64_t nl = p.nl;
   const int64_t nnodes = ipow_host(nl, d);
   std::vector<uint8_t> seen(nnodes, 0);
@@ -187,14 +200,50 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
           seen[lin] = 1;
         }
   }
+  // per plane node: the partial-grid entries of the bricks that hold an involved cell containing
+  // it, in increasing brick index (the order in which the fixup adds them); the entry of a brick
+  // is on its box face of the lowest axis on which the node lies on an inner brick boundary
+  p.poff.assign(1, 0);
   for (int64_t lin = 0; lin < nnodes; ++lin) {
     if (!seen[lin]) continue;
-    const int X = (int)(lin % nl), Y = (int)((lin / nl) % nl), Z = d == 3 ? (int)(lin / (nl * nl)) : 0;
-    const int64_t row = Y + (d == 3 ? nl * Z : 0);
-    const int64_t ci = p.compact(X, row);
-    if (ci < 0) return false;
-    const int32_t rec[4] = {(int32_t)ci, X, Y, Z};
-    p.pnode.insert(p.pnode.end(), rec, rec + 4);
+    const int X[3] = {(int)(lin % nl), (int)((lin / nl) % nl), d == 3 ? (int)(lin / (nl * nl)) : 0};
+    const int64_t row = X[1] + (d == 3 ? nl * X[2] : 0);
+    const int64_t ci = p.compact(X[0], row);
+    if (ci < 0) { p.bdim[0] = 0; return false; }
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, pa = -1;
+    for (int a = 0; a < d; ++a) {
+      const bool on = X[a] % k == 0;
+      c0[a] = on ? std::max(X[a] / k - 1, 0) : X[a] / k;
+      c1[a] = on ? std::min(X[a] / k, n - 1) : X[a] / k;
+      if (pa < 0 && X[a] % (p.bdim[a] * k) == 0 && X[a] > 0 && X[a] < n * k) pa = a;
+    }
+    const int u0 = pa == 0 ? 1 : 0, u1 = pa == 2 ? 1 : 2;
+    for (int bz = c0[2] / p.bdim[2]; bz <= c1[2] / p.bdim[2]; ++bz)
+      for (int by = c0[1] / p.bdim[1]; by <= c1[1] / p.bdim[1]; ++by)
+        for (int bx = c0[0] / p.bdim[0]; bx <= c1[0] / p.bdim[0]; ++bx) {
+          const int bb[3] = {bx, by, bz};
+          bool found = false;
+          for (int cz = c0[2]; cz <= c1[2]; ++cz)
+            for (int cy = c0[1]; cy <= c1[1]; ++cy)
+              for (int cx = c0[0]; cx <= c1[0]; ++cx)
+                if (cx / p.bdim[0] == bx && cy / p.bdim[1] == by && cz / p.bdim[2] == bz &&
+                    invmask[cx + (int64_t)n * (cy + (int64_t)(d == 3 ? n : 0) * cz)])
+                  found = true;
+          if (!found) continue;
+          const int32_t slot = p.bslot[bx + (int64_t)p.nbx[0] * (by + (int64_t)p.nbx[1] * bz)];
+          if (slot < 0) { p.bdim[0] = 0; return false; }
+          const int side = X[pa] == bb[pa] * p.bdim[pa] * k ? 0 : 1;
+          const int64_t g = (X[u0] - bb[u0] * p.bdim[u0] * k) +
+                            (d == 3 ? (int64_t)p.gstride[pa] * (X[u1] - bb[u1] * p.bdim[u1] * k) : 0);
+          const int64_t e = (int64_t)slot * p.pgrid + p.goff[pa][side] + g;
+          if (e < 0 || e >= (int64_t)(p.bdesc.size() / BDESC) * p.pgrid || e >= ((int64_t)1 << 31)) {
+            p.bdim[0] = 0;
+            return false;
+          }
+          p.pslot.push_back((int32_t)e);
+        }
+    p.pnode.push_back((int32_t)ci);
+    p.poff.push_back((int32_t)p.pslot.size());
   }
   // ---- bounds of every index the brick kernels read or write
   const int64_t ninv = (int64_t)p.inv_cells.size();
@@ -202,7 +251,6 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
     if (i < 0 || i >= ninv) { p.bdim[0] = 0; return false; }
   for (size_t i = 0; i < p.rowtab.size(); ++i)
     if (p.rowtab[i] < 0 || p.rowtab[i] + k + 1 > p.n_active) { p.bdim[0] = 0; return false; }
-  (void)L;
   return true;
 }
 

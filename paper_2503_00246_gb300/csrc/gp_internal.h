@@ -25,9 +25,9 @@ struct gp_ctx {
   int32_t* d_bccoord = nullptr;
   uint32_t* d_bface = nullptr;
   int32_t* d_rowtab = nullptr;
-  int32_t* d_bslot = nullptr;
-  int4* d_pnode = nullptr;
-  int8_t* d_invmask = nullptr;
+  int32_t* d_pnode = nullptr;
+  int32_t* d_poff = nullptr;
+  int32_t* d_pslot = nullptr;
   void* d_part = nullptr;
   bool no_scratch = false;
   void* d_xh = nullptr;          // gp_apply_host staging

@@ -129,9 +129,11 @@ cudaError_t run_brick(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, cu
   ba.nzblocks = (Ar.nzruns + ZGROUP - 1) / ZGROUP;
   const size_t smem = brick_smem<D, K, V>(ba.maxown, ba.maxcell, fb);
   if (smem > BRICK_MAX_SMEM) return cudaErrorInvalidConfiguration;
-  static bool smem_raised[64] = {};              // per instantiation and device, raised once
+  // the opt-in limit covers static + dynamic shared memory: raise it once per instantiation
+  // and device, whatever this launch needs
+  static bool smem_raised[64] = {};
   int dev = 0;
-  if (smem > 48 * 1024 && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !smem_raised[dev]) {
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !smem_raised[dev]) {
     const cudaError_t e = cudaFuncSetAttribute(brick_kernel<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)BRICK_MAX_SMEM);
     if (e != cudaSuccess) return e;
@@ -144,7 +146,7 @@ cudaError_t run_brick(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, cu
   if (Ar.pa.nplane > 0 && ba.nbricks > 0) {
     const int nb = (Ar.pa.nplane + 255) / 256;
     if (Ar.ev) {
-      plane_fixup_kernel<D, A><<<nb, 256, 0, st>>>((IO*)Ar.y, Ar.add, Ar.pa, Ar.k);
+      plane_fixup_kernel<A><<<nb, 256, 0, st>>>((IO*)Ar.y, Ar.add, Ar.pa);
     } else {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)nb);
@@ -155,7 +157,7 @@ cudaError_t run_brick(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, cu
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, plane_fixup_kernel<D, A>, (IO*)Ar.y, Ar.add, Ar.pa, Ar.k);
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, plane_fixup_kernel<A>, (IO*)Ar.y, Ar.add, Ar.pa);
       if (e != cudaSuccess) return e;
     }
   }

@@ -91,12 +91,16 @@ struct Plan {
   std::vector<int32_t> bccoord;   // parallel to bcell: packed local coords cx | cy << 8 | cz << 16 (own)
   std::vector<uint32_t> bface;    // per brick: packed faces (axis, local K-, local K+, own flags)
   std::vector<int32_t> bslot;     // dense brick index -> non-empty brick slot, or -1
-  std::vector<int32_t> pnode;     // 4 per plane node: compact index, lattice X, Y, Z
-  std::vector<int8_t> invmask;    // per cell: 1 if the cell is involved (K- or K+ of a ghost face)
+  std::vector<int32_t> pnode;     // per plane node: compact index of the DoF
+  std::vector<int32_t> poff;      // plane nodes + 1: CSR offsets into pslot
+  std::vector<int32_t> pslot;     // per plane node, in increasing brick index: the partial-grid
+                                  // entry of each brick holding an involved cell that contains it
   int64_t pgrid = 0;              // partial-grid entries per brick slot
+  int32_t goff[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // box face (axis, side) offset in a brick's grid
+  int32_t gstride[3] = {0, 0, 0};                 // row stride of box face a's grid
   int bmax_own = 0, bmax_cell = 0, bmax_face = 0;
   int64_t num_bricks() const { return bdim[0] == 0 ? 0 : (int64_t)bdesc.size() / BDESC; }
-  int64_t num_plane_nodes() const { return (int64_t)pnode.size() / 4; }
+  int64_t num_plane_nodes() const { return (int64_t)pnode.size(); }
 
   // FP64 1D reference data
   std::vector<double> gl;         // k+1 Gauss-Lobatto points on [0,1]
@@ -133,13 +137,11 @@ void reference_stiffness(int k, std::vector<double>& stiff);
 // false if the matrix is not of rank k with the expected parities.
 bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambda);
 // Brick tables for the fused face + lift kernel: picks the brick shape (largest first) whose
-// staged cell blocks and per-cell outputs fit smem_budget bytes of shared memory with values
-// of vbytes and accumulators of sbytes bytes (plus extra bytes that do not scale with the
-// brick), and fills bdim, nbx, bdesc, bcell, bccoord, bface, bslot, pnode, invmask, pgrid.
-// Returns false (bdim[0] = 0) when no shape fits; the two-kernel path is used then.
+// staged cell blocks, per-cell outputs and row starts fit smem_budget bytes of shared memory
+// with values of vbytes and accumulators of sbytes bytes (extra: the bytes of the jump planes
+// of one chunk of faces), and fills bdim, nbx, bdesc, bcell, bccoord, bface, bslot, pnode,
+// poff, pslot, pgrid, goff and gstride.  Returns false (bdim[0] = 0) when no shape fits.
 bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_budget);
-// Dynamic shared memory of the brick kernel for the plan's brick tables.
-size_t brick_smem_bytes(const Plan& p, int vbytes, int sbytes, size_t extra);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`

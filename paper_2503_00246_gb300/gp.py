@@ -468,8 +468,8 @@ def autotune_cached(ctx: Context, reps: int = 10, path: str | None = None) -> di
     import json
     import torch
     path = path or tiles_cache_path()
-    path = gp_kernel_path(ctx)["path"]
-    key = f"{torch.cuda.get_device_name(ctx.device)}|d{ctx.dim}|k{ctx.degree}|p{ctx.precision}|path{path}"
+    kpath = gp_kernel_path(ctx)["path"]
+    key = f"{torch.cuda.get_device_name(ctx.device)}|d{ctx.dim}|k{ctx.degree}|p{ctx.precision}|path{kpath}"
     cache = {}
     if os.path.exists(path):
         with open(path) as fh:
@@ -477,7 +477,7 @@ def autotune_cached(ctx: Context, reps: int = 10, path: str | None = None) -> di
     if key in cache:
         tiles = cache[key]
         gp_set_tiles(ctx, tiles)
-        if path == GP_PATH_FACE_LIFT:
+        if kpath == GP_PATH_FACE_LIFT:
             gp_tiles_record(ctx.device, ctx.dim, ctx.degree, ctx.precision, tiles)
         return tiles
     tiles, _ = gp_autotune(ctx, reps)

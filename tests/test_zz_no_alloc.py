@@ -64,10 +64,19 @@ def test_noalloc_matches_apply_twice(gplib, cuda, prec):
 
 
 def test_noalloc_refuses_oversized_problem(gplib, cuda):
-    pr = W.ball_3d_sweep(4)                  # 96^3 ball, k = 4: face outputs need ~145 MB in FP64
-    ctx = gplib.setup_problem(pr, precision=0)
+    # face + lift path: the 96^3 ball at k = 4 has ~114 MB of face outputs in FP64
+    pr = W.ball_3d_sweep(4)
+    ctx = gplib.setup_problem(pr, precision=0, path=gplib.GP_PATH_FACE_LIFT)
     need = ctx.n_faces * 9 * 25 * 8
     assert need > gplib.NOALLOC_SCRATCH_BYTES
+    x = cuda.zeros(ctx.n_active, dtype=cuda.float64, device="cuda")
+    y = cuda.zeros_like(x)
+    with pytest.raises(gplib.GpError) as e:
+        gplib.gp_apply_noalloc(ctx, x, y)
+    assert e.value.status == gplib.GP_EINVAL and "fixed scratch" in str(e.value)
+    # brick path: the partial sums of the 128^3 gyroid's plane nodes exceed 32 MiB in FP64
+    ctx = gplib.setup_problem(W.gyroid_3d(), precision=0, path=gplib.GP_PATH_BRICK)
+    assert gplib.gp_kernel_path(ctx)["scratch_bytes"] > gplib.NOALLOC_SCRATCH_BYTES
     x = cuda.zeros(ctx.n_active, dtype=cuda.float64, device="cuda")
     y = cuda.zeros_like(x)
     with pytest.raises(gplib.GpError) as e:
