@@ -35,11 +35,12 @@
 
 namespace gp {
 
-constexpr int BRICK_DESC = 8;   // ints per brick descriptor (BDESC of gp_plan.h)
+constexpr int BRICK_DESC = 10;  // ints per brick descriptor (BDESC of gp_plan.h)
 constexpr int BRICK_CMAP = 256; // cells per brick at most (bdim[0] bdim[1] bdim[2])
 
 struct BrickArgs {
-  const int32_t* bdesc;    // per brick: first local cell, own cells, local cells, first face, faces, bx, by, bz
+  const int32_t* bdesc;    // per brick: first local cell, own cells, local cells, first face, faces, bx, by, bz,
+                           // first face of axis 1, of axis 2 (within the brick's faces, sorted by axis)
   const int32_t* bcell;    // involved-cell index of every local cell (own first)
   const int32_t* bccoord;  // packed local coords cx | cy << 8 | cz << 16 of the own cells
   const uint32_t* bface;   // packed faces: axis | K- << 2 | K+ << 12 | K- own << 22 | K+ own << 23
@@ -114,6 +115,64 @@ __device__ __forceinline__ int block_pos(const int axis, const int bn, const int
   if (D == 2) return tau + K1 * bn;
   if (axis == 1) return (tau % K1) + K1 * bn + K1 * K1 * (tau / K1);
   return tau + K1 * K1 * bn;
+}
+
+// One chunk of faces [f0, min(f0 + fb, f1)) with normal AX: thread (fl, tau) gathers its
+// normal line from the staged x blocks, runs the three one-dimensional steps and adds the line's
+// outputs to the own cells' accumulators: the K+ parts (b = k..2k) of every face, a barrier, then
+// the K- parts (b < k).  Every thread of the CTA calls it (it synchronises).
+template <int D, int K, class A, int AX>
+__device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, const int f0, const int f1,
+                                            const int fl, const int tau, const int fb, const typename A::V* xs,
+                                            Sum<typename A::V>* ys,
+                                            typename A::V (*buf)[K][Shape<D, K>::L],
+                                            typename A::V (*sb2)[K][Shape<D, K>::L],
+                                            const typename A::V (*sm)[K + 1],
+                                            const Consts<typename A::V, K>& c) {
+  using V = typename A::V;
+  constexpr int L = Shape<D, K>::L, NN = 2 * K + 1, K1 = K + 1;
+  constexpr int NB = (D == 3) ? K1 * K1 * K1 : K1 * K1;
+  const int f = f0 + fl;
+  const bool valid = f < f1;
+  const uint32_t rec = valid ? __ldg(bface + f) : 0u;
+  const int lo = (int)((rec >> 2) & 1023u), hi = (int)((rec >> 12) & 1023u);
+  const bool lo_own = (rec >> 22) & 1u, hi_own = (rec >> 23) & 1u;
+  V v[NN];
+  if (valid) {
+#pragma unroll
+    for (int b = 0; b <= K; ++b) v[b] = xs[lo * NB + block_pos<D, K>(AX, b, tau)];
+#pragma unroll
+    for (int b = 1; b <= K; ++b) v[K + b] = xs[hi * NB + block_pos<D, K>(AX, b, tau)];
+  } else {
+#pragma unroll
+    for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
+  }
+  {
+    V tj[K];
+    line_jumps<K, V>(v, c, tj);
+#pragma unroll
+    for (int j = 0; j < K; ++j) buf[fl][j][tau] = tj[j];
+  }
+  __syncthreads();
+  V out[K];
+  line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
+  V w[NN];
+  if (valid) {
+    V sj[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) sj[j] = vmul(c.s[j], out[j]);
+    line_expand<K, V>(c, sj, w);
+  }
+  if (valid && hi_own) {
+#pragma unroll
+    for (int b = 0; b <= K; ++b) sum_add(ys[hi * NB + block_pos<D, K>(AX, b, tau)], w[K + b]);
+  }
+  __syncthreads();
+  if (valid && lo_own) {
+#pragma unroll
+    for (int b = 0; b < K; ++b) sum_add(ys[lo * NB + block_pos<D, K>(AX, b, tau)], w[b]);
+  }
+  __syncthreads();
 }
 
 template <int D, int K, class A>
@@ -194,59 +253,16 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
   }
   __syncthreads();
 
-  // ---- faces, fb per chunk, one thread per normal line
-  const int fl = t / L, tau = t - fl * L;
-  const int fls = fl < fb ? fl : 0;
-  for (int f0 = 0; f0 < nface; f0 += fb) {
-    const int f = f0 + fl;
-    const bool valid = fl < fb && f < nface;
-    const uint32_t rec = valid ? __ldg(ba.bface + face_off + f) : 0u;
-    const int axis = (int)(rec & 3u);
-    const int lo = (int)((rec >> 2) & 1023u), hi = (int)((rec >> 12) & 1023u);
-    const bool lo_own = (rec >> 22) & 1u, hi_own = (rec >> 23) & 1u;
-    V v[NN];
-    if (valid) {
-#pragma unroll
-      for (int b = 0; b <= K; ++b) v[b] = xs[lo * NB + block_pos<D, K>(axis, b, tau)];
-#pragma unroll
-      for (int b = 1; b <= K; ++b) v[K + b] = xs[hi * NB + block_pos<D, K>(axis, b, tau)];
-    } else {
-#pragma unroll
-      for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
-    }
-    {
-      V tj[K];
-      line_jumps<K, V>(v, c, tj);
-      if (fl < fb) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) buf[fl][j][tau] = tj[j];
-      }
-    }
-    __syncthreads();
-    V out[K];
-    line_tangential<D, K, V, L>(buf[fls], sb2[fls], sm, tau, out);
-    V w[NN];
-    if (valid) {
-      V sj[K];
-#pragma unroll
-      for (int j = 0; j < K; ++j) sj[j] = vmul(c.s[j], out[j]);
-      line_expand<K, V>(c, sj, w);
-    }
-    // add to the cell blocks, per axis: K+ parts (b = k..2k), then K- parts (b < k)
-    const int fend = min(nface, f0 + fb) - 1;
-    const int amin = (int)(__ldg(ba.bface + face_off + f0) & 3u);
-    const int amax = (int)(__ldg(ba.bface + face_off + fend) & 3u);
-    for (int a = amin; a <= amax; ++a) {
-      if (valid && axis == a && hi_own) {
-#pragma unroll
-        for (int b = 0; b <= K; ++b) sum_add(ys[hi * NB + block_pos<D, K>(a, b, tau)], w[K + b]);
-      }
-      __syncthreads();
-      if (valid && axis == a && lo_own) {
-#pragma unroll
-        for (int b = 0; b < K; ++b) sum_add(ys[lo * NB + block_pos<D, K>(a, b, tau)], w[b]);
-      }
-      __syncthreads();
+  // ---- faces, axis by axis, fb per chunk, one thread per normal line
+  {
+    const int fl = t / L, tau = t - fl * L;
+    const uint32_t* bf = ba.bface + face_off;
+    const int a1 = sd[8], a2 = (D == 3) ? sd[9] : nface;
+    for (int f0 = 0; f0 < a1; f0 += fb) brick_chunk<D, K, A, 0>(bf, f0, a1, fl, tau, fb, xs, ys, buf, sb2, sm, c);
+    for (int f0 = a1; f0 < a2; f0 += fb) brick_chunk<D, K, A, 1>(bf, f0, a2, fl, tau, fb, xs, ys, buf, sb2, sm, c);
+    if constexpr (D == 3) {
+      for (int f0 = a2; f0 < nface; f0 += fb)
+        brick_chunk<D, K, A, 2>(bf, f0, nface, fl, tau, fb, xs, ys, buf, sb2, sm, c);
     }
   }
 

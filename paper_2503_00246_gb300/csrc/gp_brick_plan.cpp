@@ -154,8 +154,13 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
         const int l0 = local_any(c0, o0), l1 = local_any(c1, o1);
         p.bface.push_back(pack_face(a, l0, l1, o0, o1));
       }
+      int32_t astart[3] = {0, 0, 0};   // first face of each axis within the brick's list
+      for (int a = 1; a < 3; ++a) {
+        astart[a] = astart[a - 1];
+        while (astart[a] < (int32_t)faces_of[b].size() && faces_of[b][astart[a]] < p.fstart[a]) ++astart[a];
+      }
       const int32_t desc[BDESC] = {cell_off, (int32_t)own[b].size(), (int32_t)loc.size(), face_off,
-                                   (int32_t)faces_of[b].size(), bx, by, bz};
+                                   (int32_t)faces_of[b].size(), bx, by, bz, astart[1], astart[2]};
       p.bdesc.insert(p.bdesc.end(), desc, desc + BDESC);
     }
     break;

@@ -13,8 +13,8 @@ namespace gp {
 constexpr int KMAX = 8;
 constexpr int ZRUN_MAX = 256;       // elements per zero run (one CTA pass)
 // ints per brick descriptor: first local cell, own cells, local cells, first face, faces,
-// brick coordinates bx, by, bz
-constexpr int BDESC = 8;
+// brick coordinates bx, by, bz, first face of axis 1 and of axis 2 (the faces are sorted by axis)
+constexpr int BDESC = 10;
 
 enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
 
