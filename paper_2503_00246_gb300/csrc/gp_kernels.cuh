@@ -45,15 +45,11 @@ struct Tiles {
 constexpr int MAX_CTA_THREADS = 512;
 constexpr size_t MAX_DYN_SMEM = 46 * 1024;   // plus < 2 KB of static shared memory: under the 48 KB default
 
-// dynamic shared memory of the face kernel: one region per CTA that holds, in turn, the fb
-// staged patches (P values each, read from x with coalesced loads), the k jump planes (and the
-// first tangential pass in 3D) of the fb faces, and the fb face outputs before their coalesced
-// store; its size is the larger of fb P and fb 2k L (3D) values
+// dynamic shared memory of the face kernel: the k jump planes (and the first
+// tangential pass in 3D) of fb faces
 template <int D, int K, typename V>
 __host__ __device__ constexpr size_t face_smem(int fb) {
-  constexpr int planes = ((D == 3) ? 2 : 1) * K;
-  constexpr int lines = 2 * K + 1 > planes ? 2 * K + 1 : planes;
-  return (size_t)fb * lines * Shape<D, K>::L * sizeof(V);
+  return (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
 }
 
 // Kernel constants (passed by value; they sit in the constant bank).
@@ -232,68 +228,26 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   const bool valid = f < fend;
   for (int i = t; i < K1 * K1; i += nt) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
 
-  // ---- stage the patches of this CTA's faces: patch element e of face fl at pt[fl P + e]
-  // (patch order, x fastest), consecutive threads reading consecutive x values of a row
-  V* pt = reinterpret_cast<V*>(dsm);
-  const int nfl = min(fb, fend - f0);
-  {
-    const int total = nfl * S::P;
-    const int32_t* fr = fa.frows + rbase + (int64_t)(f0 - fbase) * (axis == 0 ? L : ((D == 3) ? NN * K1 : NN));
-    for (int base = t; base < total; base += 4 * nt) {
-      IO v4[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = base + u * nt;
-        if (i < total) {
-          const int fl2 = i / S::P, e = i - fl2 * S::P;
-          int row, col;
-          if (axis == 0) {            // e = b + NN tau: row tau of the face, column b
-            row = fl2 * L + e / NN;
-            col = e % NN;
-          } else if (D == 2 || axis == 1) {
-            // e = tx + K1 (b + NN tz): row b + NN tz (2D: b), column tx
-            row = fl2 * ((D == 3) ? NN * K1 : NN) + e / K1;
-            col = e % K1;
-          } else {                    // e = tx + K1 (ty + K1 b): row b + NN ty, column tx
-            const int r2 = e / K1;
-            row = fl2 * NN * K1 + (r2 / K1) + NN * (r2 % K1);
-            col = e % K1;
-          }
-          v4[u] = __ldg(x + __ldg(fr + row) + col);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = base + u * nt;
-        if (i < total) pt[i] = from_io(v4[u], (V*)nullptr);
-      }
-    }
-  }
-  __syncthreads();
-  // ---- this thread's normal line (2k+1 values) from the staged patch
-  int pos0, pstride;          // patch position of node b of line tau: pos0 + pstride b
-  if (axis == 0) {            // b + NN tau
-    pos0 = NN * tau;
-    pstride = 1;
-  } else if (D == 2 || axis == 1) {
-    // 3D normal y: tx + K1 (b + NN tz); 2D normal y: tx + K1 b
-    const int tx = (D == 3) ? tau % K1 : tau;
-    const int tz = (D == 3) ? tau / K1 : 0;
-    pos0 = tx + K1 * NN * tz;
-    pstride = K1;
-  } else {                    // normal z: tx + K1 (ty + K1 b)
-    pos0 = tau;
-    pstride = K1 * K1;
-  }
+  // ---- gather this thread's normal line (2k+1 values)
   V v[NN];
   if (valid) {
+    if (axis == 0) {
+      const int32_t base = __ldg(fa.frows + rbase + (int64_t)(f - fbase) * L + tau);
 #pragma unroll
-    for (int b = 0; b < NN; ++b) v[b] = pt[fl * S::P + pos0 + pstride * b];
+      for (int b = 0; b < NN; ++b) v[b] = from_io(__ldg(x + base + b), (V*)nullptr);
+    } else {
+      // tau = tx + (K+1) tr; row b of the patch at outer tangential index tr
+      constexpr int R = (D == 3) ? NN * K1 : NN;
+      const int tx = (D == 3) ? tau % K1 : tau;
+      const int tr = (D == 3) ? tau / K1 : 0;
+      const int32_t* rows = fa.frows + rbase + (int64_t)(f - fbase) * R + NN * tr;
+#pragma unroll
+      for (int b = 0; b < NN; ++b) v[b] = from_io(__ldg(x + __ldg(rows + b) + tx), (V*)nullptr);
+    }
   } else {
 #pragma unroll
     for (int b = 0; b < NN; ++b) v[b] = vzero<V>();
   }
-  __syncthreads();            // the region now takes the jump planes
   // ---- contract with the k jump vectors, then the tangential reference masses
   {
     V t[K];
@@ -305,25 +259,30 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   V out[K];
   line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
-  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], into the region in patch order,
-  // then stored with coalesced writes (the faces of a CTA are consecutive in W)
-  V w[NN];
+  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored in patch order
   if (valid) {
     V sj[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) sj[j] = vmul(sc[j], out[j]);
+    V* dst = wp + (size_t)f * S::P;
+    int pos0, pstride;
+    if (axis == 0) {            // patch index b + NN * tau
+      pos0 = NN * tau;
+      pstride = 1;
+    } else if (D == 2 || axis == 1) {
+      // 3D normal y: tx + K1 (b + NN tz); 2D normal y: tx + K1 b
+      const int tx = (D == 3) ? tau % K1 : tau;
+      const int tz = (D == 3) ? tau / K1 : 0;
+      pos0 = tx + K1 * NN * tz;
+      pstride = K1;
+    } else {                    // normal z: tx + K1 (ty + K1 b)
+      pos0 = tau;
+      pstride = K1 * K1;
+    }
+    V w[NN];
     line_expand<K, V>(c, sj, w);
-  }
-  __syncthreads();            // every thread has read the planes
-  if (valid) {
 #pragma unroll
-    for (int bb = 0; bb < NN; ++bb) pt[fl * S::P + pos0 + pstride * bb] = w[bb];
-  }
-  __syncthreads();
-  {
-    V* dst = wp + (size_t)f0 * S::P;
-    const int total = nfl * S::P;
-    for (int i = t; i < total; i += nt) dst[i] = pt[i];
+    for (int bb = 0; bb < NN; ++bb) dst[pos0 + pstride * bb] = w[bb];
   }
 }
 
@@ -462,12 +421,7 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
     for (int sa = 0; sa < 3; ++sa) {
       if (a != 0 && sa == 0 && !nz) continue;
       if constexpr (SKIP) {
-        // native FP64: the loads of the (up to 4) faces of this (a, s_a) first (a missing face
-        // loads nothing), then the adds of the present faces only (warp-uniform by the host's
-        // cell order, so no FP64 issue goes to absent faces)
-        V ld[4 * K];
-        bool okf[4];
-        int n = 0, nf = 0;
+        // native FP64: skip the adds of a missing face (warp-uniform by the host's cell order)
 #pragma unroll
         for (int s1 = 0; s1 < 2; ++s1) {
           if (s1 == 0 && !xz) continue;
@@ -475,33 +429,14 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
           for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
             if (D == 3 && s2 == 0 && !yz) continue;
             const int f = win[(D == 3) ? a * 12 + sa * 4 + s1 * 2 + s2 : a * 6 + sa * 2 + s1];
-            const bool ok = f >= 0;
-            okf[nf++] = ok;
+            if (f < 0) continue;
             int cnt;
             const int pos = where(a, sa, s1, s2, cnt);
-            const V* src = wp + (size_t)(ok ? f : 0) * P + (ok ? pos : 0);
+            const V* src = wp + (size_t)f * P + pos;
 #pragma unroll
             for (int p = 0; p < K; ++p)
-              if (p < cnt) ld[n++] = ok ? src[p] : vzero<V>();
-            if (ok) found |= (cnt == 1) ? 1u : ALL;
-          }
-        }
-        n = 0;
-        nf = 0;
-#pragma unroll
-        for (int s1 = 0; s1 < 2; ++s1) {
-          if (s1 == 0 && !xz) continue;
-#pragma unroll
-          for (int s2 = 0; s2 < ((D == 3) ? 2 : 1); ++s2) {
-            if (D == 3 && s2 == 0 && !yz) continue;
-            const bool ok = okf[nf++];
-            const int cnt = (a == 0) ? ((sa == 0) ? 1 : K) : ((s1 == 0) ? 1 : K);
-            if (ok) {
-#pragma unroll
-              for (int p = 0; p < K; ++p)
-                if (p < cnt) sum_add(acc[p], ld[n + p]);
-            }
-            n += cnt;
+              if (p < cnt) sum_add(acc[p], src[p]);
+            found |= (cnt == 1) ? 1u : ALL;
           }
         }
       } else {

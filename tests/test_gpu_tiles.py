@@ -48,7 +48,7 @@ def test_every_shape_is_bitwise_equal(gplib, cuda, prec, dim, n, k, path):
     assert np.abs(ref - yo).max() <= tol * np.abs(yo).max()
     L = (k + 1) ** (dim - 1)
     vb = 4 if prec == 1 else 8
-    fb_max = min(512 // L, (46 * 1024) // ((2 * k + 1) * L * vb))
+    fb_max = min(512 // L, (46 * 1024) // ((2 if dim == 3 else 1) * k * L * vb))
     for sh in SHAPES:
         sh = dict(sh)
         sh["faces_per_cta"] = min(sh["faces_per_cta"], fb_max)
