@@ -197,7 +197,7 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
       const int2 run = zr[r];
-      for (int i = t; i < run.y; i += nt) y[run.x + i] = IO(0);
+      for (int i = t; i < run.y; i += nt) __stcs(y + run.x + i, IO(0));   // not read again: streaming
     }
     return;
   }

@@ -208,7 +208,8 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     __syncthreads();
     for (int r = 0; r < nr; ++r) {
       const int2 run = zr[r];
-      for (int i = threadIdx.x; i < run.y; i += nt) y[run.x + i] = IO(0);
+      // streaming stores: the zeros are not read again, so they should not push x out of L2
+      for (int i = threadIdx.x; i < run.y; i += nt) __stcs(y + run.x + i, IO(0));
     }
     return;
   }
