@@ -513,6 +513,7 @@ struct gp_batch {
   };
   std::vector<Group> groups;
   void* d_w = nullptr;
+  void* d_gs = nullptr;                // per problem: the scaled jump vectors s_j g_j
   size_t w_bytes = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -548,6 +549,7 @@ void batch_free(gp_batch* b) {
     }
   }
   if (b->d_w) cudaFree(b->d_w);
+  if (b->d_gs) cudaFree(b->d_gs);
   if (b->cap) cudaStreamDestroy(b->cap);
 }
 
@@ -607,6 +609,23 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
   cudaError_t e = cudaSuccess;
   if (total > 0) e = cudaMalloc(&b->d_w, total);
   b->w_bytes = total;
+  // the scaled jump vectors of every problem, in its group's arithmetic (256-byte aligned)
+  std::vector<size_t> gs_off(nprob, 0);
+  {
+    std::vector<unsigned char> all, one;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi)
+      for (size_t i = 0; i < b->groups[gi].prob.size(); ++i) {
+        const int pi = b->groups[gi].prob[i];
+        if (b->groups[gi].rhs[i] != 0) continue;
+        const gp::Plan& pl = ctxs[pi]->plan;
+        b->groups[gi].ops.jumps(pl.k, pl.jumps.data(), pl.scale.data(), one);
+        gs_off[pi] = all.size();
+        all.insert(all.end(), one.begin(), one.end());
+        all.resize((all.size() + 255) / 256 * 256, 0);
+      }
+    if (e == cudaSuccess && !all.empty()) e = cudaMalloc(&b->d_gs, all.size());
+    if (e == cudaSuccess && !all.empty()) e = cudaMemcpy(b->d_gs, all.data(), all.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
     auto& g = b->groups[gi];
@@ -627,7 +646,7 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       sp.la.nlift = (int32_t)pl.num_lift_cells();
       sp.la.n_active = (int32_t)pl.n_active;
       sp.wp = (char*)b->d_w + woff[gi][i];
-      for (int j = 0; j < pl.k; ++j) sp.s[j] = pl.scale[j];
+      sp.gs = (const char*)b->d_gs + gs_off[g.prob[i]];
     }
     std::vector<unsigned char> fs, ls;
     if (!g.ops.pack(g.k, specs, g.tiles, fs, ls, g.face_blocks, g.lift_blocks)) {

@@ -187,6 +187,11 @@ __device__ __forceinline__ void sum_add(Sum<ff64>& d, ff64 v) {
   d.c = __fadd_rn(__fadd_rn(d.c, v.lo), err);
 }
 
+// a sum holding exactly v (what sum_add of v to a zero sum gives, without the add)
+__device__ __forceinline__ void sum_set(Sum<float>& d, float v) { d.v = v; }
+__device__ __forceinline__ void sum_set(Sum<double>& d, double v) { d.v = v; }
+__device__ __forceinline__ void sum_set(Sum<ff64>& d, ff64 v) { d.s = v.hi; d.c = v.lo; }
+
 // d += o for two partial sums (the same compensated scheme for float-float)
 __device__ __forceinline__ void sum_merge(Sum<float>& d, const Sum<float>& o) { d.v += o.v; }
 __device__ __forceinline__ void sum_merge(Sum<double>& d, const Sum<double>& o) { d.v += o.v; }

@@ -149,20 +149,16 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
   }
   {
     V tj[K];
-    line_jumps<K, V>(v, c, tj);
+    line_jumps<K, V>(v, c.gs, tj);
 #pragma unroll
     for (int j = 0; j < K; ++j) buf[fl][j][tau] = tj[j];
   }
   __syncthreads();
   V out[K];
-  line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
+  if constexpr (sizeof(V) == 8) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
+  else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
   V w[NN];
-  if (valid) {
-    V sj[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) sj[j] = vmul(c.s[j], out[j]);
-    line_expand<K, V>(c, sj, w);
-  }
+  if (valid) line_expand<K, V>(c, out, w);   // s_j is folded into the first step
   if (valid && hi_own) {
 #pragma unroll
     for (int b = 0; b <= K; ++b) sum_add(ys[hi * NB + block_pos<D, K>(AX, b, tau)], w[K + b]);

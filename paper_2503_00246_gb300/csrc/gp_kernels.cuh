@@ -52,13 +52,32 @@ __host__ __device__ constexpr size_t face_smem(int fb) {
   return (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
 }
 
-// Kernel constants (passed by value; they sit in the constant bank).
+// Kernel constants (passed by value; they sit in the constant bank).  The per-order factor
+// s_j = c_j h^{d-2} is folded into the jump vectors of the first step (gs = s_j g_j), so the
+// normal expansion uses the plain g_j and no line multiplies by s_j.
 template <typename V, int K>
 struct Consts {
-  V g[K][2 * K + 1];  // jump of the j-th derivative of patch basis b (row j-1)
-  V m[K + 1][K + 1];  // reference mass matrix
-  V s[K];             // c_j h^{d-2}
+  V g[K][2 * K + 1];   // jump of the j-th derivative of patch basis b (row j-1)
+  V gs[K][2 * K + 1];  // s_j g_j[b], the jump vectors of the first step
+  V m[K + 1][K + 1];   // reference mass matrix
+  // even and odd halves of the centrosymmetric mass matrix (M^[N-1-p][N-1-i] = M^[p][i], N = k+1):
+  // me[p][i] = (M^[p][i] + M^[p][N-1-i]) / 2 (M^[p][i] for the middle i), mo[p][i] = (M^[p][i] - M^[p][N-1-i]) / 2
+  V me[(K + 2) / 2][(K + 2) / 2];
+  V mo[(K + 1) / 2][(K + 1) / 2];
 };
+
+// Fills the even / odd halves of the mass matrix m (row-major, (k+1)^2) into c.
+template <typename V, int K>
+void mass_halves(const double* m, Consts<V, K>& c) {
+  constexpr int N = K + 1, NE = (K + 2) / 2, H = (K + 1) / 2;
+  for (int p = 0; p < NE; ++p)
+    for (int i = 0; i < NE; ++i) {
+      const bool mid = 2 * i == N - 1;
+      c.me[p][i] = from_host<V>(mid ? m[p * N + i] : 0.5 * (m[p * N + i] + m[p * N + N - 1 - i]));
+    }
+  for (int p = 0; p < H; ++p)
+    for (int i = 0; i < H; ++i) c.mo[p][i] = from_host<V>(0.5 * (m[p * N + i] - m[p * N + N - 1 - i]));
+}
 
 struct FaceArgs {
   const int32_t* frows;   // per-face row starts of the patch (see rbase)
@@ -83,12 +102,12 @@ struct LiftArgs {
 // The three one-dimensional steps of the face apply for one normal line, shared by the
 // face kernel and the brick kernel (gp_brick.cuh).
 
-// Jump values t_j = g_j . v of the line (j = 1..k; row j - 1 of c.g).  Mirroring the patch
+// Jump values t_j = g_j . v of the line (j = 1..k; row j - 1 of g).  Mirroring the patch
 // about the face maps basis b to 2k - b, K- to K+ and d/dn to -d/dn, so
 // g_j[2k - b] = (-1)^(j+1) g_j[b]: odd orders see v[b] + v[2k-b], even orders
 // v[b] - v[2k-b], and only odd orders see the shared node b = k.
 template <int K, typename V>
-__device__ __forceinline__ void line_jumps(const V (&v)[2 * K + 1], const Consts<V, K>& c, V (&t)[K]) {
+__device__ __forceinline__ void line_jumps(const V (&v)[2 * K + 1], const V (*g)[2 * K + 1], V (&t)[K]) {
   constexpr int NN = 2 * K + 1;
   V vp[K], vm[K];
 #pragma unroll
@@ -99,10 +118,10 @@ __device__ __forceinline__ void line_jumps(const V (&v)[2 * K + 1], const Consts
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const bool odd = (j % 2) == 0;   // order j + 1
-    Dot<V> acc = dot_first(c.g[j][0], odd ? vp[0] : vm[0]);
+    Dot<V> acc = dot_first(g[j][0], odd ? vp[0] : vm[0]);
 #pragma unroll
-    for (int b = 1; b < K; ++b) dot_fma(acc, c.g[j][b], odd ? vp[b] : vm[b]);
-    if (odd) dot_fma(acc, c.g[j][K], v[K]);
+    for (int b = 1; b < K; ++b) dot_fma(acc, g[j][b], odd ? vp[b] : vm[b]);
+    if (odd) dot_fma(acc, g[j][K], v[K]);
     t[j] = dot_value(acc);
   }
 }
@@ -151,7 +170,75 @@ __device__ __forceinline__ void line_tangential(V (*plane)[L], V (*plane2)[L], c
   }
 }
 
-// Normal expansion w[b] = sum_j g_j[b] sj[j] (sj = s_j times the tangential result):
+// The mass matrix applied to one line of N = k+1 values u through its even and odd halves:
+// y[p] = E_p + O_p and y[N-1-p] = E_p - O_p, E_p = sum_i me[p][i] (u[i] + u[N-1-i]) (the middle
+// value once), O_p = sum_i mo[p][i] (u[i] - u[N-1-i]): (N/2)^2 + (N/2 rounded up)^2 terms and
+// 2 (N/2) folds and merges instead of N^2 terms.
+template <int K, typename V>
+__device__ __forceinline__ void mass_line_eo(const Consts<V, K>& c, const V (&u)[K + 1], V (&y)[K + 1]) {
+  constexpr int N = K + 1, NE = (K + 2) / 2, H = (K + 1) / 2;
+  V e[NE], o[H > 0 ? H : 1];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    e[i] = vadd_loose(u[i], u[N - 1 - i]);
+    o[i] = vsub_loose(u[i], u[N - 1 - i]);
+  }
+  if (N % 2 == 1) e[NE - 1] = u[NE - 1];
+#pragma unroll
+  for (int p = 0; p < NE; ++p) {
+    Dot<V> ev = dot_first(c.me[p][0], e[0]);
+#pragma unroll
+    for (int i = 1; i < NE; ++i) dot_fma(ev, c.me[p][i], e[i]);
+    if (p < H) {
+      Dot<V> ov = dot_first(c.mo[p][0], o[0]);
+#pragma unroll
+      for (int i = 1; i < H; ++i) dot_fma(ov, c.mo[p][i], o[i]);
+      y[p] = dot_merge<false>(ev, ov);
+      y[N - 1 - p] = dot_merge<true>(ev, ov);
+    } else {
+      y[p] = dot_value(ev);
+    }
+  }
+}
+
+// The tangential masses through the even / odd halves (FP64 and float-float, where an
+// arithmetic operation is expensive): one thread per (order j, tangential line) applies M^ to a
+// whole line of k+1 values, pass by pass, through plane2 and back into plane; each thread then
+// reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
+template <int D, int K, typename V, int L>
+__device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L], const Consts<V, K>& c,
+                                                   const int tau, V (&out)[K]) {
+  constexpr int N = K + 1;
+  const bool task = tau < ((D == 3) ? K * N : K);
+  const int j = (D == 3) ? tau / N : tau, tr = (D == 3) ? tau % N : 0;
+  if (task) {       // first pass: along t1 within the line t2 = tr (2D: the only pass)
+    V u[N], yv[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) u[q] = plane[j][q + N * tr];
+    mass_line_eo<K, V>(c, u, yv);
+#pragma unroll
+    for (int i = 0; i < N; ++i) plane2[j][i + N * tr] = yv[i];
+  }
+  __syncthreads();
+  if constexpr (D == 3) {
+    if (task) {     // second pass: along t2 within the line t1 = tr
+      V u[N], yv[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) u[q] = plane2[j][tr + N * q];
+      mass_line_eo<K, V>(c, u, yv);
+#pragma unroll
+      for (int i = 0; i < N; ++i) plane[j][tr + N * i] = yv[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < K; ++jj) out[jj] = plane[jj][tau];
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < K; ++jj) out[jj] = plane2[jj][tau];
+  }
+}
+
+// Normal expansion w[b] = sum_j g_j[b] sj[j] (sj: the tangential results of the line):
 // w[b] = E_b + O_b and w[2k-b] = E_b - O_b, with E_b (O_b) the sum over odd (even) orders of
 // g_j[b] sj[j]; w[k] = E_k.
 template <int K, typename V>
@@ -178,12 +265,13 @@ __device__ __forceinline__ void line_expand(const Consts<V, K>& c, const V (&sj)
 
 // ----------------------------------------------------------------- face --
 // One thread per (face, normal line tau); fb faces per CTA (blockDim.x = fb L).
-// `blk` is the CTA's index within its problem; `sc` points to the k scale
-// factors s_j; `dsm` is the face_smem<D, K, V>(fb) bytes of dynamic shared memory.
+// `blk` is the CTA's index within its problem; `gs` holds the scaled jump vectors s_j g_j of
+// the first step (c.gs, or a batch segment's copy in shared memory); `dsm` is the
+// face_smem<D, K, V>(fb) bytes of dynamic shared memory.
 template <int D, int K, class A>
 __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
                                           typename A::IO* __restrict__ y, const FaceArgs& fa,
-                                          const Consts<typename A::V, K>& c, const typename A::V* sc,
+                                          const Consts<typename A::V, K>& c, const typename A::V (*gs)[2 * K + 1],
                                           const int blk, const int fb, unsigned char* dsm) {
   using S = Shape<D, K>;
   using V = typename A::V;
@@ -252,19 +340,17 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   // ---- contract with the k jump vectors, then the tangential reference masses
   {
     V t[K];
-    line_jumps<K, V>(v, c, t);
+    line_jumps<K, V>(v, gs, t);
 #pragma unroll
     for (int j = 0; j < K; ++j) buf[fl][j][tau] = t[j];
   }
   __syncthreads();
   V out[K];
-  line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
+  if constexpr (sizeof(V) == 8) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
+  else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
-  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored in patch order
+  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] out[j] (s_j is in the first step), in patch order
   if (valid) {
-    V sj[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) sj[j] = vmul(sc[j], out[j]);
     V* dst = wp + (size_t)f * S::P;
     int pos0, pstride;
     if (axis == 0) {            // patch index b + NN * tau
@@ -281,7 +367,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
       pstride = K1 * K1;
     }
     V w[NN];
-    line_expand<K, V>(c, sj, w);
+    line_expand<K, V>(c, out, w);
 #pragma unroll
     for (int bb = 0; bb < NN; ++bb) dst[pos0 + pstride * bb] = w[bb];
   }
@@ -294,7 +380,7 @@ __global__ void __launch_bounds__(MAX_CTA_THREADS)
 face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
             typename A::IO* __restrict__ y, const FaceArgs fa, const int fb,
             const __grid_constant__ Consts<typename A::V, K> c) {
-  face_body<D, K, A>(x, wp, y, fa, c, c.s, blockIdx.x, fb, gp_dyn_smem);
+  face_body<D, K, A>(x, wp, y, fa, c, c.gs, blockIdx.x, fb, gp_dyn_smem);
 }
 
 // --------------------------------------------------------------- batches --
@@ -305,7 +391,7 @@ template <typename V, int K>
 struct FaceSeg {
   FaceArgs fa;
   V* wp;           // this segment's face outputs
-  V s[K];          // c_j h^{d-2} of the segment's problem
+  const V* gs;     // K x (2K+1) scaled jump vectors s_j g_j of the segment's problem
   int32_t block0;  // first CTA of the segment in the group's face launch
 };
 
@@ -337,15 +423,19 @@ __global__ void __launch_bounds__(MAX_CTA_THREADS)
 face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const int nseg,
                     const SegPtrs<typename A::IO>* __restrict__ ptrs, const int fb,
                     const __grid_constant__ Consts<typename A::V, K> c) {
-  __shared__ FaceSeg<typename A::V, K> seg;
+  using V = typename A::V;
+  __shared__ FaceSeg<V, K> seg;
   __shared__ SegPtrs<typename A::IO> sp;
+  __shared__ V sg[K][2 * K + 1];
   if (threadIdx.x == 0) {
     const int s = find_segment(segs, nseg, (int)blockIdx.x);
     seg = segs[s];
     sp = ptrs[s];
   }
   __syncthreads();
-  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, seg.s, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
+  for (int i = threadIdx.x; i < K * (2 * K + 1); i += blockDim.x) sg[i / (2 * K + 1)][i % (2 * K + 1)] = seg.gs[i];
+  __syncthreads();
+  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, sg, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
 }
 
 // ----------------------------------------------------------------- lift --
@@ -434,9 +524,13 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
             int cnt;
             const int pos = where(a, sa, s1, s2, cnt);
             const V* src = wp + (size_t)f * P + pos;
+            // the first contribution of a node sets its sum (no add with zero)
 #pragma unroll
             for (int p = 0; p < K; ++p)
-              if (p < cnt) sum_add(acc[p], src[p]);
+              if (p < cnt) {
+                if ((found >> p) & 1u) sum_add(acc[p], src[p]);
+                else sum_set(acc[p], src[p]);
+              }
             found |= (cnt == 1) ? 1u : ALL;
           }
         }

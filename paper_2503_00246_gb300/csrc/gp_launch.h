@@ -173,9 +173,11 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   Consts<V, K> c;
   for (int j = 0; j < K; ++j)
     for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(Ar.g[j * (2 * K + 1) + b]);
+  for (int j = 0; j < K; ++j)
+    for (int b = 0; b < 2 * K + 1; ++b) c.gs[j][b] = from_host<V>(Ar.s[j] * Ar.g[j * (2 * K + 1) + b]);
   for (int p = 0; p < K + 1; ++p)
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(Ar.m[p * (K + 1) + q]);
-  for (int j = 0; j < K; ++j) c.s[j] = from_host<V>(Ar.s[j]);
+  mass_halves<V, K>(Ar.m, c);
   if (Ar.brick) return run_brick<D, K, A>(Ar, c, st);
   Tiles t = Ar.tiles;
   if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
@@ -230,7 +232,7 @@ struct SegSpec {
   FaceArgs fa;          // frows, rbase, fstart, zruns, nzruns of the segment's problem
   LiftArgs la;
   void* wp = nullptr;   // the segment's face-output buffer
-  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const void* gs = nullptr;   // device: K x (2K+1) scaled jump vectors of the segment's problem
 };
 
 // Packs the segments of one (d, k, arithmetic) group into the device layouts of
@@ -254,7 +256,7 @@ bool pack_batch(const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned c
     }
     for (int a = D; a < 4; ++a) fs.fa.bstart[a] = nb;
     fs.wp = (V*)in[i].wp;
-    for (int j = 0; j < K; ++j) fs.s[j] = from_host<V>(in[i].s[j]);
+    fs.gs = (const V*)in[i].gs;
     fs.block0 = fb;
     fb += nb;
     LiftSeg ls;
@@ -281,7 +283,9 @@ cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, in
     for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
   for (int p = 0; p < K + 1; ++p)
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
-  for (int j = 0; j < K; ++j) c.s[j] = vzero<V>();   // per segment, in FaceSeg
+  mass_halves<V, K>(m, c);
+  for (int j = 0; j < K; ++j)
+    for (int b = 0; b < 2 * K + 1; ++b) c.gs[j][b] = vzero<V>();   // per segment: FaceSeg::gs
   if (face_blocks > 0)
     face_kernel_batched<D, K, A><<<face_blocks, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>(
         (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs, t.fb, c);
@@ -291,10 +295,22 @@ cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, in
   return cudaGetLastError();
 }
 
+// The scaled jump vectors s_j g_j[b] (k x (2k+1)) of one problem in the value type of the
+// arithmetic (4 or 8 bytes per value), as the face kernels use them.
+template <class A>
+void scaled_jumps(int k, const double* g, const double* s, std::vector<unsigned char>& out) {
+  using V = typename A::V;
+  out.assign((size_t)k * (2 * k + 1) * sizeof(V), 0);
+  V* o = reinterpret_cast<V*>(out.data());
+  for (int j = 0; j < k; ++j)
+    for (int b = 0; b < 2 * k + 1; ++b) o[j * (2 * k + 1) + b] = from_host<V>(s[j] * g[j * (2 * k + 1) + b]);
+}
+
 // Per translation unit: batch packing and launch for one (arithmetic, dimension).
 struct BatchOps {
   bool (*pack)(int k, const std::vector<SegSpec>&, Tiles&, std::vector<unsigned char>&,
                std::vector<unsigned char>&, int&, int&);
+  void (*jumps)(int k, const double* g, const double* s, std::vector<unsigned char>& out);
   cudaError_t (*run)(int k, const void*, const void*, const void*, int, int, int, const double*, const double*,
                      Tiles, cudaStream_t);
 };
@@ -307,6 +323,7 @@ BatchOps batch_ops_ff_d3();
 
 #define GP_BATCH_OPS(D, A)                                                                              \
   BatchOps ops;                                                                                         \
+  ops.jumps = scaled_jumps<A>;                                                                          \
   ops.pack = [](int k, const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned char>& fs,       \
                 std::vector<unsigned char>& ls, int& fb, int& lb) -> bool {                             \
     switch (k) {                                                                                        \
