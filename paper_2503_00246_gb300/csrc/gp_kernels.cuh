@@ -203,8 +203,9 @@ __device__ __forceinline__ void mass_line_eo(const Consts<V, K>& c, const V (&u)
 
 // The tangential masses through the even / odd halves (FP64 and float-float, where an
 // arithmetic operation is expensive): one thread per (order j, tangential line) applies M^ to a
-// whole line of k+1 values, pass by pass, through plane2 and back into plane; each thread then
-// reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
+// whole line of k+1 values, pass by pass, in 3D through plane2 and back into plane, in 2D in
+// place (plane2 is not used there: the 2D face kernels hold one plane per face); each thread
+// then reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
 template <int D, int K, typename V, int L>
 __device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L], const Consts<V, K>& c,
                                                    const int tau, V (&out)[K]) {
@@ -216,8 +217,9 @@ __device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L]
 #pragma unroll
     for (int q = 0; q < N; ++q) u[q] = plane[j][q + N * tr];
     mass_line_eo<K, V>(c, u, yv);
+    V (*dst)[L] = (D == 3) ? plane2 : plane;   // 2D: the task owns row j of plane
 #pragma unroll
-    for (int i = 0; i < N; ++i) plane2[j][i + N * tr] = yv[i];
+    for (int i = 0; i < N; ++i) dst[j][i + N * tr] = yv[i];
   }
   __syncthreads();
   if constexpr (D == 3) {
@@ -234,7 +236,7 @@ __device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L]
     for (int jj = 0; jj < K; ++jj) out[jj] = plane[jj][tau];
   } else {
 #pragma unroll
-    for (int jj = 0; jj < K; ++jj) out[jj] = plane2[jj][tau];
+    for (int jj = 0; jj < K; ++jj) out[jj] = plane[jj][tau];
   }
 }
 
