@@ -201,11 +201,14 @@ __device__ __forceinline__ void mass_line_eo(const Consts<V, K>& c, const V (&u)
   }
 }
 
-// The tangential masses through the even / odd halves (FP64 and float-float, where an
-// arithmetic operation is expensive): one thread per (order j, tangential line) applies M^ to a
+// The tangential masses through the even / odd halves (float-float, where an arithmetic
+// operation costs about 12 float instructions): one thread per (order j, tangential line) applies M^ to a
 // whole line of k+1 values, pass by pass, in 3D through plane2 and back into plane, in 2D in
 // place (plane2 is not used there: the 2D face kernels hold one plane per face); each thread
 // then reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
+// Native FP64 keeps the one-output-per-thread passes: only k (k+1) of the (k+1)^2 threads of a
+// face have a line here, and the FP64 pipe spends the same time on a partly idle warp (the
+// face kernel measured 2% slower at 128^3, k = 4).
 template <int D, int K, typename V, int L>
 __device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L], const Consts<V, K>& c,
                                                    const int tau, V (&out)[K]) {
@@ -348,7 +351,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   }
   __syncthreads();
   V out[K];
-  if constexpr (sizeof(V) == 8) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
+  if constexpr (std::is_same<V, ff64>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
   else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
   // ---- normal expansion W_F[b, tau] = sum_j g_j[b] out[j] (s_j is in the first step), in patch order
@@ -386,59 +389,12 @@ face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp
 }
 
 // --------------------------------------------------------------- batches --
-// A batch segment is one (problem, right-hand side) pair of a group of problems
-// with the same dimension, degree and arithmetic.  Its x and y pointers live in
-// a separate table the host rewrites for every apply.
-template <typename V, int K>
-struct FaceSeg {
-  FaceArgs fa;
-  V* wp;           // this segment's face outputs
-  const V* gs;     // K x (2K+1) scaled jump vectors s_j g_j of the segment's problem
-  int32_t block0;  // first CTA of the segment in the group's face launch
-};
-
-struct LiftSeg {
-  LiftArgs la;
-  int32_t block0;  // first CTA of the segment in the group's lift launch
-};
-
+// x and y of one problem of a batch (right-hand side 0; see gp_pbatch.cuh)
 template <typename IO>
 struct SegPtrs {
   const IO* x;
   IO* y;
 };
-
-// index of the segment holding CTA `blk`: the last segment whose block0 <= blk
-template <typename Seg>
-__device__ __forceinline__ int find_segment(const Seg* segs, const int nseg, const int blk) {
-  int lo = 0, hi = nseg - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&segs[mid].block0) <= blk) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <int D, int K, class A>
-__global__ void __launch_bounds__(MAX_CTA_THREADS)
-face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const int nseg,
-                    const SegPtrs<typename A::IO>* __restrict__ ptrs, const int fb,
-                    const __grid_constant__ Consts<typename A::V, K> c) {
-  using V = typename A::V;
-  __shared__ FaceSeg<V, K> seg;
-  __shared__ SegPtrs<typename A::IO> sp;
-  __shared__ V sg[K][2 * K + 1];
-  if (threadIdx.x == 0) {
-    const int s = find_segment(segs, nseg, (int)blockIdx.x);
-    seg = segs[s];
-    sp = ptrs[s];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < K * (2 * K + 1); i += blockDim.x) sg[i / (2 * K + 1)][i % (2 * K + 1)] = seg.gs[i];
-  __syncthreads();
-  face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, sg, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
-}
 
 // ----------------------------------------------------------------- lift --
 // Owner cell c = (ci, cj, cl) holds the lattice nodes (ci k + p, cj k + q, cl k + r),
@@ -659,23 +615,6 @@ __global__ void __launch_bounds__(MAX_CTA_THREADS)
 lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
             const LiftArgs la, const int cb) {
   lift_body<D, K, A>(wp, y, add, la, blockIdx.x, cb, gp_dyn_smem);
-}
-
-template <int D, int K, class A>
-__global__ void __launch_bounds__(MAX_CTA_THREADS)
-lift_kernel_batched(const LiftSeg* __restrict__ segs, const FaceSeg<typename A::V, K>* __restrict__ fsegs,
-                    const int nseg, const SegPtrs<typename A::IO>* __restrict__ ptrs, const int cb) {
-  __shared__ LiftSeg seg;
-  __shared__ typename A::V* wp;
-  __shared__ typename A::IO* y;
-  if (threadIdx.x == 0) {
-    const int s = find_segment(segs, nseg, (int)blockIdx.x);
-    seg = segs[s];
-    wp = fsegs[s].wp;
-    y = ptrs[s].y;
-  }
-  __syncthreads();
-  lift_body<D, K, A>(wp, y, 0, seg.la, (int)blockIdx.x - seg.block0, cb, gp_dyn_smem);
 }
 
 }  // namespace gp
