@@ -214,23 +214,12 @@ def run_profile(args):
 
 def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):
     """The batched workload: 64 independent 3D ball problems, n ~ U{16..96}, k ~ U{2..6},
-    4 right-hand sides each, replayed as one CUDA graph per apply.  Inputs (> 7 GB) exceed L2.
-    With tune_reps > 0 the tile shape of every degree is tuned on that degree's largest
-    problem and used by the whole group."""
+    4 right-hand sides each, replayed as one CUDA graph per apply (one persistent face launch
+    and one persistent lift launch over all degrees and right-hand sides).  Inputs (> 7 GB)
+    exceed L2."""
     probs = W.batched_3d()
     nrhs = 4
-    ctxs = [gp.setup_problem(p, precision=prec, device=dev.index or 0) for p in probs]
-    tuned = {}
-    if tune_reps > 0:
-        by_k = {}
-        for p, c in zip(probs, ctxs):
-            by_k.setdefault(p.degree, []).append(c)
-        for k in sorted(by_k):
-            big = max(by_k[k], key=lambda c: c.n_faces)
-            t, _ = gp.gp_autotune(big, tune_reps)
-            for c in by_k[k]:
-                gp.gp_set_tiles(c, t)
-            tuned[str(k)] = t
+    ctxs = [gp.setup_problem(p, precision=prec, device=dev.index or 0, path=gp.GP_PATH_FACE_LIFT) for p in probs]
     batch = gp.gp_batch_create(ctxs, nrhs)
     tdt = torch.float32 if prec == gp.GP_FP32 else torch.float64
     gen = torch.Generator(device=dev)
@@ -253,7 +242,7 @@ def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):
            "problems": len(probs), "rhs": nrhs, "dof_vectors_per_apply": units,
            "ghost_faces": sum(c.n_faces for c in ctxs), "kernel_groups": ngroups,
            "graph_launches_per_apply": 1, "kernels_per_apply": 2 * ngroups,
-           "scratch_bytes": scratch, "tiles_per_degree": tuned or None}
+           "scratch_bytes": scratch}
     batch.close()
     for c in ctxs:
         c.close()

@@ -500,10 +500,10 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
 struct gp_batch {
   int device = -1, nprob = 0, nrhs = 0;
   std::vector<gp_ctx*> ctxs;
-  // problems with one (dimension, arithmetic, stabilisation) share a group: one persistent face
-  // launch and one persistent lift launch over all their degrees and right-hand sides
+  // problems with one (dimension, degree, arithmetic, stabilisation) share a group: one
+  // persistent face launch and one persistent lift launch over all their right-hand sides
   struct Group {
-    int dim = 0, prec = 0, stab = 0;
+    int dim = 0, k = 0, prec = 0, stab = 0;
     std::vector<int> prob;             // problems of the group, in batch order
     void* d_probs = nullptr;
     int4* d_fitems = nullptr;
@@ -511,7 +511,8 @@ struct gp_batch {
     int nfitems = 0, nlitems = 0;
     void* d_ptrs[2] = {nullptr, nullptr};
     void* h_ptrs[2] = {nullptr, nullptr};  // pinned: read by the graph's copy node at replay
-    std::vector<unsigned char> consts;     // AllConsts of the group's degrees
+    const double* g = nullptr;             // the group's 1D data (jumps, mass), host
+    const double* m = nullptr;
     size_t fsm = 0, lsm = 0;
     gp::BatchOps ops{};
   };
@@ -587,11 +588,11 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
   b->nrhs = nrhs;
   b->ctxs.assign(ctxs, ctxs + nprob);
   DeviceGuard dg(b->device);
-  // groups by (dimension, arithmetic, stabilisation): one set of 1D data per degree
-  std::map<std::tuple<int, int, int>, int> key;
+  // groups by (dimension, degree, arithmetic, stabilisation): one set of 1D data per group
+  std::map<std::tuple<int, int, int, int>, int> key;
   for (int p = 0; p < nprob; ++p) {
     const gp::Plan& pl = ctxs[p]->plan;
-    auto kk = std::make_tuple(pl.dim, pl.precision, pl.stabilization);
+    auto kk = std::make_tuple(pl.dim, pl.k, pl.precision, pl.stabilization);
     auto it = key.find(kk);
     int gi;
     if (it == key.end()) {
@@ -599,8 +600,11 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       key[kk] = gi;
       b->groups.emplace_back();
       b->groups[gi].dim = pl.dim;
+      b->groups[gi].k = pl.k;
       b->groups[gi].prec = pl.precision;
       b->groups[gi].stab = pl.stabilization;
+      b->groups[gi].g = pl.jumps.data();
+      b->groups[gi].m = pl.mass.data();
       b->groups[gi].ops = ops_for(pl.precision, pl.dim);
     } else {
       gi = it->second;
@@ -630,7 +634,6 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
   for (auto& g : b->groups) {
     if (e != cudaSuccess) break;
     std::vector<gp::PBSpec> specs(g.prob.size());
-    std::vector<bool> seen_k(gp::KMAX + 1, false);
     for (size_t i = 0; i < g.prob.size(); ++i) {
       const gp_ctx* c = ctxs[g.prob[i]];
       const gp::Plan& pl = c->plan;
@@ -650,10 +653,7 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       sp.wp = (char*)b->d_w + woff[g.prob[i]];
       sp.wstride = pl.num_faces() * pl.L * (2 * pl.k + 1);
       sp.gs = (const char*)b->d_gs + gs_off[g.prob[i]];
-      if (!seen_k[pl.k]) {
-        seen_k[pl.k] = true;
-        g.ops.consts(pl.k, pl.jumps.data(), pl.mass.data(), g.consts);
-      }
+
     }
     std::vector<unsigned char> probs;
     std::vector<int4> fi, li;
@@ -685,7 +685,7 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       la.items = g.d_litems;
       la.nitems = g.nlitems;
       if (e == cudaSuccess)
-        e = g.ops.run(fa, la, g.consts.data(), b->face_threads, g.fsm, b->lift_threads, g.lsm, b->cap);
+        e = g.ops.run(g.k, fa, la, g.g, g.m, b->face_threads, g.fsm, b->lift_threads, g.lsm, b->cap);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);

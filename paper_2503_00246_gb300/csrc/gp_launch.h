@@ -274,8 +274,8 @@ inline size_t pb_lift_smem_rt(int d, int k, int lift_threads) {
 }
 
 // Device records of a group's problems (PBProb of the arithmetic) and the work lists: face
-// items (faces of one axis, then groups of zero runs) and lift items (owner cells), each list
-// ordered by decreasing degree; fsm / lsm receive the launches' dynamic shared memory.
+// items (faces of one axis, then groups of zero runs) and lift items (owner cells), in problem
+// order; fsm / lsm receive the launches' dynamic shared memory.
 template <int D, class A>
 void pb_pack(const std::vector<PBSpec>& in, int face_threads, int lift_threads, std::vector<unsigned char>& probs,
              std::vector<int4>& fitems, std::vector<int4>& litems, size_t& fsm, size_t& lsm) {
@@ -314,41 +314,7 @@ void pb_pack(const std::vector<PBSpec>& in, int face_threads, int lift_threads, 
     if (sp.fstart[D] > 0)
       for (int c = 0; c < sp.nlift; c += cb) litems.push_back(make_int4((int)i, 0, c, std::min(cb, sp.nlift - c)));
   }
-  auto by_k = [&](const int4& u, const int4& v) { return in[u.x].k > in[v.x].k; };
-  std::stable_sort(fitems.begin(), fitems.end(), by_k);
-  std::stable_sort(litems.begin(), litems.end(), by_k);
   fitems.insert(fitems.end(), zitems.begin(), zitems.end());
-}
-
-// The constants of the degrees of a group, from the 1D data (jumps g and mass m) per degree.
-template <class A, int K>
-void pb_consts_k(AllConsts<typename A::V>& all, const double* g, const double* m) {
-  using V = typename A::V;
-  Consts<V, K>& c = kconsts_mut<K, V>(all);
-  for (int j = 0; j < K; ++j)
-    for (int b = 0; b < 2 * K + 1; ++b) {
-      c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
-      c.gs[j][b] = vzero<V>();   // per problem: PBProb::gs
-    }
-  for (int p = 0; p < K + 1; ++p)
-    for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
-  mass_halves<V, K>(m, c);
-}
-template <class A>
-void pb_consts(int k, const double* g, const double* m, std::vector<unsigned char>& bytes) {
-  using V = typename A::V;
-  if (bytes.size() != sizeof(AllConsts<V>)) bytes.assign(sizeof(AllConsts<V>), 0);
-  AllConsts<V>& all = *reinterpret_cast<AllConsts<V>*>(bytes.data());
-  switch (k) {
-    case 1: pb_consts_k<A, 1>(all, g, m); break;
-    case 2: pb_consts_k<A, 2>(all, g, m); break;
-    case 3: pb_consts_k<A, 3>(all, g, m); break;
-    case 4: pb_consts_k<A, 4>(all, g, m); break;
-    case 5: pb_consts_k<A, 5>(all, g, m); break;
-    case 6: pb_consts_k<A, 6>(all, g, m); break;
-    case 7: pb_consts_k<A, 7>(all, g, m); break;
-    default: pb_consts_k<A, 8>(all, g, m); break;
-  }
 }
 
 // Persistent grid of one launch: resident CTAs per SM x SMs, at most one per item.
@@ -362,32 +328,56 @@ int pb_grid(F kernel, int threads, size_t smem, int nitems) {
   return std::max(1, std::min(g, nitems));
 }
 
-// The face launch and the lift launch of one group (consts: the group's AllConsts bytes).
-template <int D, class A>
-cudaError_t pb_run(const PBArgs& fa, const PBArgs& la, const unsigned char* consts, int face_threads, size_t fsm,
-                   int lift_threads, size_t lsm, cudaStream_t st) {
+// The face launch and the lift launch of one group of degree K (g, m: its 1D data).
+template <int D, int K, class A>
+cudaError_t pb_run_k(const PBArgs& fa, const PBArgs& la, const double* g, const double* m, int face_threads,
+                     size_t fsm, int lift_threads, size_t lsm, cudaStream_t st) {
   using V = typename A::V;
   static bool raised[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !raised[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(face_kernel_pb<D, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(face_kernel_pb<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(lift_kernel_pb<D, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      e = cudaFuncSetAttribute(lift_kernel_pb<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (e != cudaSuccess) return e;
     raised[dev] = true;
   }
   if (fsm > 96 * 1024 || lsm > 96 * 1024) return cudaErrorInvalidConfiguration;
-  AllConsts<V> cc;
-  std::memcpy(&cc, consts, sizeof(cc));
+  Consts<V, K> c;
+  for (int j = 0; j < K; ++j)
+    for (int b = 0; b < 2 * K + 1; ++b) {
+      c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
+      c.gs[j][b] = vzero<V>();   // per problem: PBProb::gs
+    }
+  for (int p = 0; p < K + 1; ++p)
+    for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
+  mass_halves<V, K>(m, c);
   if (fa.nitems > 0) {
-    const int g = pb_grid(face_kernel_pb<D, A>, face_threads, fsm, fa.nitems);
-    face_kernel_pb<D, A><<<g, face_threads, fsm, st>>>(fa, cc);
+    const int grid = pb_grid(face_kernel_pb<D, K, A>, face_threads, fsm, fa.nitems);
+    face_kernel_pb<D, K, A><<<grid, face_threads, fsm, st>>>(fa, c);
   }
   if (la.nitems > 0) {
-    const int g = pb_grid(lift_kernel_pb<D, A>, lift_threads, lsm, la.nitems);
-    lift_kernel_pb<D, A><<<g, lift_threads, lsm, st>>>(la);
+    const int grid = pb_grid(lift_kernel_pb<D, K, A>, lift_threads, lsm, la.nitems);
+    lift_kernel_pb<D, K, A><<<grid, lift_threads, lsm, st>>>(la);
   }
   return cudaGetLastError();
+}
+
+template <int D, class A>
+cudaError_t pb_run(int k, const PBArgs& fa, const PBArgs& la, const double* g, const double* m, int face_threads,
+                   size_t fsm, int lift_threads, size_t lsm, cudaStream_t st) {
+  switch (k) {
+    case 1: return pb_run_k<D, 1, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 2: return pb_run_k<D, 2, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 3: return pb_run_k<D, 3, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 4: return pb_run_k<D, 4, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 5: return pb_run_k<D, 5, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 6: return pb_run_k<D, 6, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 7: return pb_run_k<D, 7, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    case 8: return pb_run_k<D, 8, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Per translation unit: batch packing and launch for one (arithmetic, dimension).
@@ -395,8 +385,8 @@ struct BatchOps {
   void (*jumps)(int k, const double* g, const double* s, std::vector<unsigned char>& out);
   void (*pack)(const std::vector<PBSpec>&, int, int, std::vector<unsigned char>&, std::vector<int4>&,
                std::vector<int4>&, size_t&, size_t&);
-  void (*consts)(int k, const double* g, const double* m, std::vector<unsigned char>& bytes);
-  cudaError_t (*run)(const PBArgs&, const PBArgs&, const unsigned char*, int, size_t, int, size_t, cudaStream_t);
+  cudaError_t (*run)(int k, const PBArgs&, const PBArgs&, const double*, const double*, int, size_t, int, size_t,
+                     cudaStream_t);
   size_t vbytes;
 };
 BatchOps batch_ops_f64_d2();
@@ -410,7 +400,6 @@ BatchOps batch_ops_ff_d3();
   BatchOps ops;                      \
   ops.jumps = scaled_jumps<A>;       \
   ops.pack = pb_pack<D, A>;          \
-  ops.consts = pb_consts<A>;         \
   ops.run = pb_run<D, A>;            \
   ops.vbytes = sizeof(typename A::V); \
   return ops;

@@ -1,11 +1,14 @@
 // Batched applies of many independent problems with several right-hand sides (the batched
 // workload: meshes of uneven n, k and geometry), as two persistent launches per (dimension,
-// arithmetic, stabilisation): one face launch and one lift launch over a static work list.
+// degree, arithmetic, stabilisation): one face launch and one lift launch over a static work
+// list.
 //
-// A work item of the face launch is up to fb_k faces of one normal axis of one problem (or a
-// group of zero runs); of the lift launch up to cb_k owner cells of one problem.  Items of
-// every degree k share a launch (the kernel dispatches on the item's k), sorted by k, and the
-// CTAs of the launch walk the list with a fixed stride (no inter-CTA waits).  Each item runs
+// A work item of the face launch is up to fb faces of one normal axis of one problem (or a
+// group of zero runs); of the lift launch up to cb owner cells of one problem.  The CTAs of a
+// launch walk its list with a fixed stride (no inter-CTA waits).  One launch per degree: a
+// launch that dispatched on the degree of each item took the registers of its largest degree
+// (128 per thread with spills in FP32) for every item, and ran the batched workload at 60% of
+// the speed of per-degree launches.  Each item runs
 // all nrhs right-hand sides of its problem: the face item reads its row starts once and the
 // lift item its candidate windows and row starts once, so the tables are read once per item
 // instead of once per right-hand side.  The per-line arithmetic is that of the single-problem
@@ -42,35 +45,6 @@ struct PBArgs {
   int32_t nitems;
   int32_t nrhs;
 };
-
-// the constants of every degree 1..8 (a launch holds items of several degrees)
-template <typename V>
-struct AllConsts {
-  Consts<V, 1> c1;
-  Consts<V, 2> c2;
-  Consts<V, 3> c3;
-  Consts<V, 4> c4;
-  Consts<V, 5> c5;
-  Consts<V, 6> c6;
-  Consts<V, 7> c7;
-  Consts<V, 8> c8;
-};
-
-template <int K, typename V>
-__host__ __device__ __forceinline__ const Consts<V, K>& kconsts(const AllConsts<V>& a) {
-  if constexpr (K == 1) return a.c1;
-  else if constexpr (K == 2) return a.c2;
-  else if constexpr (K == 3) return a.c3;
-  else if constexpr (K == 4) return a.c4;
-  else if constexpr (K == 5) return a.c5;
-  else if constexpr (K == 6) return a.c6;
-  else if constexpr (K == 7) return a.c7;
-  else return a.c8;
-}
-template <int K, typename V>
-__host__ __forceinline__ Consts<V, K>& kconsts_mut(AllConsts<V>& a) {
-  return const_cast<Consts<V, K>&>(kconsts<K, V>(a));
-}
 
 // dynamic shared memory of a face item of degree k: fb + 1 jump planes (two in 3D)
 template <int D, int K, typename V>
@@ -199,9 +173,9 @@ __device__ __forceinline__ void pb_zero_item(const PBProb<typename A::V, typenam
   }
 }
 
-template <int D, class A>
+template <int D, int K, class A>
 __global__ void __launch_bounds__(MAX_CTA_THREADS)
-face_kernel_pb(const PBArgs a, const __grid_constant__ AllConsts<typename A::V> cc) {
+face_kernel_pb(const PBArgs a, const __grid_constant__ Consts<typename A::V, K> c) {
   using V = typename A::V;
   using IO = typename A::IO;
   __shared__ PBProb<V, IO> pr;
@@ -215,20 +189,8 @@ face_kernel_pb(const PBArgs a, const __grid_constant__ AllConsts<typename A::V> 
       sp = reinterpret_cast<const SegPtrs<IO>*>(a.ptrs)[it.x];
     }
     __syncthreads();
-    if (it.y == 3) {
-      pb_zero_item<A>(pr, sp, it, a.nrhs);
-    } else {
-      switch (pr.k) {
-        case 1: pb_face_item<D, 1, A>(pr, sp, it, a.nrhs, cc.c1, pb_dyn_smem); break;
-        case 2: pb_face_item<D, 2, A>(pr, sp, it, a.nrhs, cc.c2, pb_dyn_smem); break;
-        case 3: pb_face_item<D, 3, A>(pr, sp, it, a.nrhs, cc.c3, pb_dyn_smem); break;
-        case 4: pb_face_item<D, 4, A>(pr, sp, it, a.nrhs, cc.c4, pb_dyn_smem); break;
-        case 5: pb_face_item<D, 5, A>(pr, sp, it, a.nrhs, cc.c5, pb_dyn_smem); break;
-        case 6: pb_face_item<D, 6, A>(pr, sp, it, a.nrhs, cc.c6, pb_dyn_smem); break;
-        case 7: pb_face_item<D, 7, A>(pr, sp, it, a.nrhs, cc.c7, pb_dyn_smem); break;
-        default: pb_face_item<D, 8, A>(pr, sp, it, a.nrhs, cc.c8, pb_dyn_smem); break;
-      }
-    }
+    if (it.y == 3) pb_zero_item<A>(pr, sp, it, a.nrhs);
+    else pb_face_item<D, K, A>(pr, sp, it, a.nrhs, c, pb_dyn_smem);
     __syncthreads();            // the next item rewrites pr, sp, it
   }
 }
@@ -297,7 +259,7 @@ __device__ __forceinline__ void pb_lift_item(const PBProb<typename A::V, typenam
   }
 }
 
-template <int D, class A>
+template <int D, int K, class A>
 __global__ void __launch_bounds__(MAX_CTA_THREADS)
 lift_kernel_pb(const PBArgs a) {
   using V = typename A::V;
@@ -313,16 +275,7 @@ lift_kernel_pb(const PBArgs a) {
       sp = reinterpret_cast<const SegPtrs<IO>*>(a.ptrs)[it.x];
     }
     __syncthreads();
-    switch (pr.k) {
-      case 1: pb_lift_item<D, 1, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 2: pb_lift_item<D, 2, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 3: pb_lift_item<D, 3, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 4: pb_lift_item<D, 4, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 5: pb_lift_item<D, 5, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 6: pb_lift_item<D, 6, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      case 7: pb_lift_item<D, 7, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-      default: pb_lift_item<D, 8, A>(pr, sp, it, a.nrhs, pb_dyn_smem); break;
-    }
+    pb_lift_item<D, K, A>(pr, sp, it, a.nrhs, pb_dyn_smem);
     __syncthreads();
   }
 }
