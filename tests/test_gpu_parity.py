@@ -330,7 +330,7 @@ def test_batch_graph_replays(gplib, cuda, prec):
     ctxs = [gplib.setup_problem(p, precision=prec, path=gplib.GP_PATH_FACE_LIFT) for p in probs]
     batch = gplib.gp_batch_create(ctxs, nrhs)
     ngroups, scratch = gplib.gp_batch_info(batch)
-    assert ngroups == 2 and scratch > 0     # the 3D problems (k = 2, 3, 5) and the 2D one
+    assert ngroups == 4 and scratch > 0     # (3D,k2) x2, (3D,k3) x2, (3D,k5), (2D,k4)
     oracles = [Oracle(p) for p in probs]
     rng = np.random.default_rng(17)
     for call in range(3):
