@@ -326,15 +326,11 @@ gp_status gp_profile_read(gp_ctx* ctx, double ms[2], int64_t* calls);
 
 /* Batched form: several independent problems, nrhs right-hand sides each, replayed
  * as one CUDA graph (the batched workload of many meshes of uneven n, k and
- * geometry).  gp_batch_create groups the problems by (dimension, arithmetic,
- * stabilisation); each group is one persistent face launch and one persistent lift
- * launch over a static list of work items of all its degrees (faces of one axis, owner
- * cells, zero runs of one problem), each item running every right-hand side of its problem,
- * so that the face and lift tables are read once per item, not once per right-hand side.
- * The face outputs take nrhs * n_faces * (2k+1)(k+1)^(d-1) values per problem.  The graph
- * also holds the host-to-device copy of the table of x / y pointers, so each
- * gp_batch_apply writes that table (pinned host memory) and launches the graph.  The result
- * equals single applies of the face + lift path bit for bit.
+ * geometry).  gp_batch_create groups the problems by (dimension, degree,
+ * arithmetic, stabilisation); every (problem, right-hand side) pair gets its own face-output
+ * buffer, and one face launch plus one lift launch per group cover all pairs.  The
+ * graph also holds the host-to-device copy of the table of x / y pointers, so each
+ * gp_batch_apply writes that table (pinned host memory) and launches the graph.
  *   ctxs: contexts on one device; they must outlive the batch.
  *   x[p], y[p]: device arrays of nrhs * n_active(p) elements, layout [nrhs][n_active];
  *   y[p] is overwritten.  An apply waits for the apply issued two calls earlier

@@ -500,27 +500,21 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
 struct gp_batch {
   int device = -1, nprob = 0, nrhs = 0;
   std::vector<gp_ctx*> ctxs;
-  // problems with one (dimension, degree, arithmetic, stabilisation) share a group: one
-  // persistent face launch and one persistent lift launch over all their right-hand sides
   struct Group {
-    int dim = 0, k = 0, prec = 0, stab = 0;
-    std::vector<int> prob;             // problems of the group, in batch order
-    void* d_probs = nullptr;
-    int4* d_fitems = nullptr;
-    int4* d_litems = nullptr;
-    int nfitems = 0, nlitems = 0;
+    int dim = 0, k = 0, prec = 0;
+    std::vector<int> prob, rhs;        // segment -> problem, right-hand side
+    void* d_fsegs = nullptr;
+    void* d_lsegs = nullptr;
     void* d_ptrs[2] = {nullptr, nullptr};
     void* h_ptrs[2] = {nullptr, nullptr};  // pinned: read by the graph's copy node at replay
-    const double* g = nullptr;             // the group's 1D data (jumps, mass), host
-    const double* m = nullptr;
-    size_t fsm = 0, lsm = 0;
+    int face_blocks = 0, lift_blocks = 0;
     gp::BatchOps ops{};
+    gp::Tiles tiles{};                 // the tile shape of the group's first context
   };
   std::vector<Group> groups;
-  int face_threads = 256, lift_threads = 256;
   void* d_w = nullptr;
-  size_t w_bytes = 0;
   void* d_gs = nullptr;                // per problem: the scaled jump vectors s_j g_j
+  size_t w_bytes = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -547,9 +541,8 @@ void batch_free(gp_batch* b) {
     if (b->done[i]) cudaEventDestroy(b->done[i]);
   }
   for (auto& g : b->groups) {
-    if (g.d_probs) cudaFree(g.d_probs);
-    if (g.d_fitems) cudaFree(g.d_fitems);
-    if (g.d_litems) cudaFree(g.d_litems);
+    if (g.d_fsegs) cudaFree(g.d_fsegs);
+    if (g.d_lsegs) cudaFree(g.d_lsegs);
     for (int i = 0; i < 2; ++i) {
       if (g.d_ptrs[i]) cudaFree(g.d_ptrs[i]);
       if (g.h_ptrs[i]) cudaFreeHost(g.h_ptrs[i]);
@@ -558,15 +551,6 @@ void batch_free(gp_batch* b) {
   if (b->d_w) cudaFree(b->d_w);
   if (b->d_gs) cudaFree(b->d_gs);
   if (b->cap) cudaStreamDestroy(b->cap);
-}
-
-template <typename T>
-cudaError_t upload_bytes(T** dst, const void* src, size_t bytes) {
-  *dst = nullptr;
-  if (bytes == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)dst, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
 }
 
 }  // namespace
@@ -588,8 +572,8 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
   b->nrhs = nrhs;
   b->ctxs.assign(ctxs, ctxs + nprob);
   DeviceGuard dg(b->device);
-  // groups by (dimension, degree, arithmetic, stabilisation): one set of 1D data per group
-  std::map<std::tuple<int, int, int, int>, int> key;
+  // group problems by (dimension, degree, arithmetic, stabilisation)
+  std::map<std::tuple<int, int, int, int>, int> key;   // (d, k, arithmetic, stabilisation): one set of 1D data
   for (int p = 0; p < nprob; ++p) {
     const gp::Plan& pl = ctxs[p]->plan;
     auto kk = std::make_tuple(pl.dim, pl.k, pl.precision, pl.stabilization);
@@ -602,90 +586,95 @@ gp_status gp_batch_create(gp_ctx* const* ctxs, int nprob, int nrhs, gp_batch** o
       b->groups[gi].dim = pl.dim;
       b->groups[gi].k = pl.k;
       b->groups[gi].prec = pl.precision;
-      b->groups[gi].stab = pl.stabilization;
-      b->groups[gi].g = pl.jumps.data();
-      b->groups[gi].m = pl.mass.data();
       b->groups[gi].ops = ops_for(pl.precision, pl.dim);
+      b->groups[gi].tiles = ctxs[p]->tiles;
     } else {
       gi = it->second;
     }
-    b->groups[gi].prob.push_back(p);
+    for (int r = 0; r < nrhs; ++r) {
+      b->groups[gi].prob.push_back(p);
+      b->groups[gi].rhs.push_back(r);
+    }
   }
-  // face outputs: nrhs consecutive blocks of n_faces P values per problem (256-byte aligned),
-  // and the scaled jump vectors of every problem in its group's arithmetic
-  std::vector<size_t> woff(nprob, 0), gs_off(nprob, 0);
+  // face-output buffers, one per segment, 256-byte aligned in one allocation
+  std::vector<std::vector<size_t>> woff(b->groups.size());
   size_t total = 0;
-  std::vector<unsigned char> all, one;
-  for (auto& g : b->groups)
-    for (int p : g.prob) {
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    for (int p : b->groups[gi].prob) {
       const gp::Plan& pl = ctxs[p]->plan;
-      woff[p] = total;
-      total += ((size_t)nrhs * pl.num_faces() * pl.L * (2 * pl.k + 1) * g.ops.vbytes + 255) / 256 * 256;
-      g.ops.jumps(pl.k, pl.jumps.data(), pl.scale.data(), one);
-      gs_off[p] = all.size();
-      all.insert(all.end(), one.begin(), one.end());
-      all.resize((all.size() + 255) / 256 * 256, 0);
+      const size_t vb = pl.precision == GP_FP32 ? 4 : 8;
+      woff[gi].push_back(total);
+      total += ((size_t)pl.num_faces() * pl.L * (2 * pl.k + 1) * vb + 255) / 256 * 256;
     }
   cudaError_t e = cudaSuccess;
   if (total > 0) e = cudaMalloc(&b->d_w, total);
   b->w_bytes = total;
-  if (e == cudaSuccess && !all.empty()) e = upload_bytes(&b->d_gs, all.data(), all.size());
+  // the scaled jump vectors of every problem, in its group's arithmetic (256-byte aligned)
+  std::vector<size_t> gs_off(nprob, 0);
+  {
+    std::vector<unsigned char> all, one;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi)
+      for (size_t i = 0; i < b->groups[gi].prob.size(); ++i) {
+        const int pi = b->groups[gi].prob[i];
+        if (b->groups[gi].rhs[i] != 0) continue;
+        const gp::Plan& pl = ctxs[pi]->plan;
+        b->groups[gi].ops.jumps(pl.k, pl.jumps.data(), pl.scale.data(), one);
+        gs_off[pi] = all.size();
+        all.insert(all.end(), one.begin(), one.end());
+        all.resize((all.size() + 255) / 256 * 256, 0);
+      }
+    if (e == cudaSuccess && !all.empty()) e = cudaMalloc(&b->d_gs, all.size());
+    if (e == cudaSuccess && !all.empty()) e = cudaMemcpy(b->d_gs, all.data(), all.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  for (auto& g : b->groups) {
-    if (e != cudaSuccess) break;
-    std::vector<gp::PBSpec> specs(g.prob.size());
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    auto& g = b->groups[gi];
+    std::vector<gp::SegSpec> specs(g.prob.size());
     for (size_t i = 0; i < g.prob.size(); ++i) {
       const gp_ctx* c = ctxs[g.prob[i]];
       const gp::Plan& pl = c->plan;
-      gp::PBSpec& sp = specs[i];
-      sp.frows = c->d_frows;
-      sp.lwin = c->d_lwin;
-      sp.lrow = c->d_lrow;
-      sp.zruns = c->d_zruns;
+      gp::SegSpec& sp = specs[i];
+      sp.fa.frows = c->d_frows;
       for (int a = 0; a < 4; ++a) {
-        sp.rbase[a] = pl.rbase[a];
-        sp.fstart[a] = pl.fstart[a];
+        sp.fa.rbase[a] = pl.rbase[a];
+        sp.fa.fstart[a] = pl.fstart[a];
       }
-      sp.nlift = (int32_t)pl.num_lift_cells();
-      sp.n_active = (int32_t)pl.n_active;
-      sp.nzruns = (int32_t)pl.num_zero_runs();
-      sp.k = pl.k;
-      sp.wp = (char*)b->d_w + woff[g.prob[i]];
-      sp.wstride = pl.num_faces() * pl.L * (2 * pl.k + 1);
+      sp.fa.zruns = c->d_zruns;
+      sp.fa.nzruns = (int32_t)pl.num_zero_runs();
+      sp.la.lwin = c->d_lwin;
+      sp.la.lrow = c->d_lrow;
+      sp.la.nlift = (int32_t)pl.num_lift_cells();
+      sp.la.n_active = (int32_t)pl.n_active;
+      sp.wp = (char*)b->d_w + woff[gi][i];
       sp.gs = (const char*)b->d_gs + gs_off[g.prob[i]];
-
+      for (int j = 0; j < pl.k; ++j) sp.s[j] = pl.scale[j];
     }
-    std::vector<unsigned char> probs;
-    std::vector<int4> fi, li;
-    g.ops.pack(specs, b->face_threads, b->lift_threads, probs, fi, li, g.fsm, g.lsm);
-    g.nfitems = (int)fi.size();
-    g.nlitems = (int)li.size();
-    e = upload_bytes(&g.d_probs, probs.data(), probs.size());
-    if (e == cudaSuccess) e = upload_bytes(&g.d_fitems, fi.data(), fi.size() * sizeof(int4));
-    if (e == cudaSuccess) e = upload_bytes(&g.d_litems, li.data(), li.size() * sizeof(int4));
+    std::vector<unsigned char> fs, ls;
+    if (!g.ops.pack(g.k, specs, g.tiles, fs, ls, g.face_blocks, g.lift_blocks)) {
+      e = cudaErrorInvalidConfiguration;
+      break;
+    }
+    e = cudaMalloc(&g.d_fsegs, fs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_fsegs, fs.data(), fs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_lsegs, ls.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_lsegs, ls.data(), ls.size(), cudaMemcpyHostToDevice);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
       e = cudaMalloc(&g.d_ptrs[i], g.prob.size() * 2 * sizeof(void*));
       if (e == cudaSuccess) e = cudaMallocHost(&g.h_ptrs[i], g.prob.size() * 2 * sizeof(void*));
       if (e == cudaSuccess) std::memset(g.h_ptrs[i], 0, g.prob.size() * 2 * sizeof(void*));
     }
   }
-  // one graph per slot: per group, the copy of the pointer table, the face and the lift launch
+  // one graph per slot: copy the pointer table, then each group's face and lift launches
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     for (auto& g : b->groups) {
       if (e != cudaSuccess) break;
+      const gp::Plan& pl0 = ctxs[g.prob[0]]->plan;
       e = cudaMemcpyAsync(g.d_ptrs[i], g.h_ptrs[i], g.prob.size() * 2 * sizeof(void*), cudaMemcpyHostToDevice,
                           b->cap);
-      gp::PBArgs fa{}, la{};
-      fa.probs = la.probs = g.d_probs;
-      fa.ptrs = la.ptrs = g.d_ptrs[i];
-      fa.nrhs = la.nrhs = nrhs;
-      fa.items = g.d_fitems;
-      fa.nitems = g.nfitems;
-      la.items = g.d_litems;
-      la.nitems = g.nlitems;
       if (e == cudaSuccess)
-        e = g.ops.run(g.k, fa, la, g.g, g.m, b->face_threads, g.fsm, b->lift_threads, g.lsm, b->cap);
+        e = g.ops.run(g.k, g.d_fsegs, g.d_lsegs, g.d_ptrs[i], (int)g.prob.size(), g.face_blocks, g.lift_blocks,
+                      pl0.jumps.data(), pl0.mass.data(), g.tiles, b->cap);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
@@ -719,8 +708,10 @@ gp_status gp_batch_apply(gp_batch* b, const void* const* x, void* const* y, void
   for (auto& g : b->groups) {
     void** tab = (void**)g.h_ptrs[s];
     for (size_t i = 0; i < g.prob.size(); ++i) {
-      tab[2 * i] = (void*)x[g.prob[i]];
-      tab[2 * i + 1] = y[g.prob[i]];
+      const gp_ctx* c = b->ctxs[g.prob[i]];
+      const size_t off = (size_t)g.rhs[i] * c->plan.n_active * c->elem;
+      tab[2 * i] = (void*)((const char*)x[g.prob[i]] + off);
+      tab[2 * i + 1] = (void*)((char*)y[g.prob[i]] + off);
     }
   }
   cudaError_t e = cudaGraphLaunch(b->exec[s], (cudaStream_t)stream);

@@ -149,7 +149,7 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
   }
   {
     V tj[K];
-    line_jumps<K, V>(v, c.gs, tj);
+    line_jumps<K, V>(v, FoldScale<V>::value ? c.gs : c.g, tj);
 #pragma unroll
     for (int j = 0; j < K; ++j) buf[fl][j][tau] = tj[j];
   }
@@ -158,7 +158,13 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
   if constexpr (std::is_same<V, ff64>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
   else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
   V w[NN];
-  if (valid) line_expand<K, V>(c, out, w);   // s_j is folded into the first step
+  if (valid) {
+    if constexpr (!FoldScale<V>::value) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) out[j] = vmul(c.s[j], out[j]);
+    }
+    line_expand<K, V>(c, out, w);
+  }
   if (valid && hi_own) {
 #pragma unroll
     for (int b = 0; b <= K; ++b) sum_add(ys[hi * NB + block_pos<D, K>(AX, b, tau)], w[K + b]);

@@ -52,13 +52,20 @@ __host__ __device__ constexpr size_t face_smem(int fb) {
   return (size_t)((D == 3) ? 2 : 1) * fb * K * Shape<D, K>::L * sizeof(V);
 }
 
-// Kernel constants (passed by value; they sit in the constant bank).  The per-order factor
-// s_j = c_j h^{d-2} is folded into the jump vectors of the first step (gs = s_j g_j), so the
-// normal expansion uses the plain g_j and no line multiplies by s_j.
+// Kernel constants (passed by value; they sit in the constant bank).  In FP64 and float-float
+// the per-order factor s_j = c_j h^{d-2} is folded into the jump vectors of the first step
+// (gs = s_j g_j), so no line multiplies by s_j; FP32 multiplies each line's k tangential results
+// by s_j instead (its face kernel is bound by memory instructions, and a batch then needs no
+// per-problem table).
+template <typename V>
+struct FoldScale {
+  static constexpr bool value = !std::is_same<V, float>::value;
+};
 template <typename V, int K>
 struct Consts {
   V g[K][2 * K + 1];   // jump of the j-th derivative of patch basis b (row j-1)
-  V gs[K][2 * K + 1];  // s_j g_j[b], the jump vectors of the first step
+  V gs[K][2 * K + 1];  // s_j g_j[b], the jump vectors of the first step (FP64, float-float)
+  V s[K];              // s_j (FP32)
   V m[K + 1][K + 1];   // reference mass matrix
   // even and odd halves of the centrosymmetric mass matrix (M^[N-1-p][N-1-i] = M^[p][i], N = k+1):
   // me[p][i] = (M^[p][i] + M^[p][N-1-i]) / 2 (M^[p][i] for the middle i), mo[p][i] = (M^[p][i] - M^[p][N-1-i]) / 2
@@ -270,14 +277,15 @@ __device__ __forceinline__ void line_expand(const Consts<V, K>& c, const V (&sj)
 
 // ----------------------------------------------------------------- face --
 // One thread per (face, normal line tau); fb faces per CTA (blockDim.x = fb L).
-// `blk` is the CTA's index within its problem; `gs` holds the scaled jump vectors s_j g_j of
-// the first step (c.gs, or a batch segment's copy in shared memory); `dsm` is the
+// `blk` is the CTA's index within its problem; `gs` holds the jump vectors of the first step
+// (FP64, float-float: the scaled s_j g_j, c.gs or a batch segment's copy in shared memory;
+// FP32: the plain c.g) and `sc` the k factors s_j (FP32 only); `dsm` is the
 // face_smem<D, K, V>(fb) bytes of dynamic shared memory.
 template <int D, int K, class A>
 __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
                                           typename A::IO* __restrict__ y, const FaceArgs& fa,
                                           const Consts<typename A::V, K>& c, const typename A::V (*gs)[2 * K + 1],
-                                          const int blk, const int fb, unsigned char* dsm) {
+                                          const typename A::V* sc, const int blk, const int fb, unsigned char* dsm) {
   using S = Shape<D, K>;
   using V = typename A::V;
   using IO = typename A::IO;
@@ -354,7 +362,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   if constexpr (std::is_same<V, ff64>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
   else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
-  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] out[j] (s_j is in the first step), in patch order
+  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], in patch order
   if (valid) {
     V* dst = wp + (size_t)f * S::P;
     int pos0, pstride;
@@ -371,6 +379,10 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
       pos0 = tau;
       pstride = K1 * K1;
     }
+    if constexpr (!FoldScale<V>::value) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) out[j] = vmul(sc[j], out[j]);
+    }
     V w[NN];
     line_expand<K, V>(c, out, w);
 #pragma unroll
@@ -385,16 +397,68 @@ __global__ void __launch_bounds__(MAX_CTA_THREADS)
 face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp,
             typename A::IO* __restrict__ y, const FaceArgs fa, const int fb,
             const __grid_constant__ Consts<typename A::V, K> c) {
-  face_body<D, K, A>(x, wp, y, fa, c, c.gs, blockIdx.x, fb, gp_dyn_smem);
+  face_body<D, K, A>(x, wp, y, fa, c, FoldScale<typename A::V>::value ? c.gs : c.g, c.s, blockIdx.x, fb, gp_dyn_smem);
 }
 
 // --------------------------------------------------------------- batches --
-// x and y of one problem of a batch (right-hand side 0; see gp_pbatch.cuh)
+// A batch segment is one (problem, right-hand side) pair of a group of problems
+// with the same dimension, degree and arithmetic.  Its x and y pointers live in
+// a separate table the host rewrites for every apply.
+template <typename V, int K>
+struct FaceSeg {
+  FaceArgs fa;
+  V* wp;           // this segment's face outputs
+  const V* gs;     // FP64, float-float: K x (2K+1) scaled jump vectors s_j g_j of the problem
+  V s[K];          // FP32: s_j of the problem
+  int32_t block0;  // first CTA of the segment in the group's face launch
+};
+
+struct LiftSeg {
+  LiftArgs la;
+  int32_t block0;  // first CTA of the segment in the group's lift launch
+};
+
 template <typename IO>
 struct SegPtrs {
   const IO* x;
   IO* y;
 };
+
+// index of the segment holding CTA `blk`: the last segment whose block0 <= blk
+template <typename Seg>
+__device__ __forceinline__ int find_segment(const Seg* segs, const int nseg, const int blk) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&segs[mid].block0) <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
+face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const int nseg,
+                    const SegPtrs<typename A::IO>* __restrict__ ptrs, const int fb,
+                    const __grid_constant__ Consts<typename A::V, K> c) {
+  using V = typename A::V;
+  __shared__ FaceSeg<V, K> seg;
+  __shared__ SegPtrs<typename A::IO> sp;
+  __shared__ V sg[K][2 * K + 1];
+  if (threadIdx.x == 0) {
+    const int s = find_segment(segs, nseg, (int)blockIdx.x);
+    seg = segs[s];
+    sp = ptrs[s];
+  }
+  __syncthreads();
+  if constexpr (FoldScale<V>::value) {
+    for (int i = threadIdx.x; i < K * (2 * K + 1); i += blockDim.x) sg[i / (2 * K + 1)][i % (2 * K + 1)] = seg.gs[i];
+    __syncthreads();
+    face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, sg, seg.s, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
+  } else {
+    face_body<D, K, A>(sp.x, seg.wp, sp.y, seg.fa, c, c.g, seg.s, (int)blockIdx.x - seg.block0, fb, gp_dyn_smem);
+  }
+}
 
 // ----------------------------------------------------------------- lift --
 // Owner cell c = (ci, cj, cl) holds the lattice nodes (ci k + p, cj k + q, cl k + r),
@@ -615,6 +679,23 @@ __global__ void __launch_bounds__(MAX_CTA_THREADS)
 lift_kernel(const typename A::V* __restrict__ wp, typename A::IO* __restrict__ y, const int add,
             const LiftArgs la, const int cb) {
   lift_body<D, K, A>(wp, y, add, la, blockIdx.x, cb, gp_dyn_smem);
+}
+
+template <int D, int K, class A>
+__global__ void __launch_bounds__(MAX_CTA_THREADS)
+lift_kernel_batched(const LiftSeg* __restrict__ segs, const FaceSeg<typename A::V, K>* __restrict__ fsegs,
+                    const int nseg, const SegPtrs<typename A::IO>* __restrict__ ptrs, const int cb) {
+  __shared__ LiftSeg seg;
+  __shared__ typename A::V* wp;
+  __shared__ typename A::IO* y;
+  if (threadIdx.x == 0) {
+    const int s = find_segment(segs, nseg, (int)blockIdx.x);
+    seg = segs[s];
+    wp = fsegs[s].wp;
+    y = ptrs[s].y;
+  }
+  __syncthreads();
+  lift_body<D, K, A>(wp, y, 0, seg.la, (int)blockIdx.x - seg.block0, cb, gp_dyn_smem);
 }
 
 }  // namespace gp

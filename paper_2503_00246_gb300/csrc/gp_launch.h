@@ -6,12 +6,9 @@
 #include <vector>
 #include <cuda_runtime.h>
 
-#include <algorithm>
-
 #include "gp_brick.cuh"
 #include "gp_cell.cuh"
 #include "gp_kernels.cuh"
-#include "gp_pbatch.cuh"
 
 namespace gp {
 
@@ -176,8 +173,10 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   Consts<V, K> c;
   for (int j = 0; j < K; ++j)
     for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(Ar.g[j * (2 * K + 1) + b]);
-  for (int j = 0; j < K; ++j)
+  for (int j = 0; j < K; ++j) {
+    c.s[j] = from_host<V>(Ar.s[j]);
     for (int b = 0; b < 2 * K + 1; ++b) c.gs[j][b] = from_host<V>(Ar.s[j] * Ar.g[j * (2 * K + 1) + b]);
+  }
   for (int p = 0; p < K + 1; ++p)
     for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(Ar.m[p * (K + 1) + q]);
   mass_halves<V, K>(Ar.m, c);
@@ -230,19 +229,77 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- batches --
-// Host description of one problem of a batch group (gp_pbatch.cuh).
-struct PBSpec {
-  const int32_t* frows = nullptr;
-  const int32_t* lwin = nullptr;
-  const int32_t* lrow = nullptr;
-  const int2* zruns = nullptr;
-  int64_t rbase[4] = {0, 0, 0, 0};
-  int32_t fstart[4] = {0, 0, 0, 0};
-  int32_t nlift = 0, n_active = 0, nzruns = 0, k = 0;
-  void* wp = nullptr;        // face outputs of right-hand side 0
-  int64_t wstride = 0;       // values per right-hand side
-  const void* gs = nullptr;  // device: k x (2k+1) scaled jump vectors
+// Host description of one batch segment (one problem, one right-hand side).
+struct SegSpec {
+  FaceArgs fa;          // frows, rbase, fstart, zruns, nzruns of the segment's problem
+  LiftArgs la;
+  void* wp = nullptr;   // the segment's face-output buffer
+  const void* gs = nullptr;   // device: K x (2K+1) scaled jump vectors of the segment's problem
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // the problem's s_j
 };
+
+// Packs the segments of one (d, k, arithmetic) group into the device layouts of
+// FaceSeg<V, K> and LiftSeg, with the CTA offsets of both launches.
+template <int D, int K, class A>
+bool pack_batch(const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned char>& fsegs,
+                std::vector<unsigned char>& lsegs, int& face_blocks, int& lift_blocks) {
+  using V = typename A::V;
+  if (!resolve_tiles<D, K, V>(t)) return false;
+  fsegs.assign(in.size() * sizeof(FaceSeg<V, K>), 0);
+  lsegs.assign(in.size() * sizeof(LiftSeg), 0);
+  int fb = 0, lb = 0;
+  for (size_t i = 0; i < in.size(); ++i) {
+    FaceSeg<V, K> fs;
+    fs.fa = in[i].fa;
+    fs.fa.nzblocks = (fs.fa.nzruns + ZGROUP - 1) / ZGROUP;
+    int32_t nb = fs.fa.nzblocks;
+    for (int a = 0; a < D; ++a) {
+      fs.fa.bstart[a] = nb;
+      nb += (fs.fa.fstart[a + 1] - fs.fa.fstart[a] + t.fb - 1) / t.fb;
+    }
+    for (int a = D; a < 4; ++a) fs.fa.bstart[a] = nb;
+    fs.wp = (V*)in[i].wp;
+    fs.gs = (const V*)in[i].gs;
+    for (int j = 0; j < K; ++j) fs.s[j] = from_host<V>(in[i].s[j]);
+    fs.block0 = fb;
+    fb += nb;
+    LiftSeg ls;
+    ls.la = in[i].la;
+    ls.block0 = lb;
+    if (fs.fa.fstart[D] > 0) lb += (ls.la.nlift + t.lcb - 1) / t.lcb;
+    std::memcpy(&fsegs[i * sizeof(FaceSeg<V, K>)], &fs, sizeof(fs));
+    std::memcpy(&lsegs[i * sizeof(LiftSeg)], &ls, sizeof(ls));
+  }
+  face_blocks = fb;
+  lift_blocks = lb;
+  return true;
+}
+
+template <int D, int K, class A>
+cudaError_t run_batch(const void* fsegs, const void* lsegs, const void* ptrs, int nseg, int face_blocks,
+                      int lift_blocks, const double* g, const double* m, Tiles t, cudaStream_t st) {
+  using V = typename A::V;
+  using IO = typename A::IO;
+  using S = Shape<D, K>;
+  if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
+  Consts<V, K> c;
+  for (int j = 0; j < K; ++j)
+    for (int b = 0; b < 2 * K + 1; ++b) c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
+  for (int p = 0; p < K + 1; ++p)
+    for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
+  mass_halves<V, K>(m, c);
+  for (int j = 0; j < K; ++j) {
+    c.s[j] = vzero<V>();                                          // per segment: FaceSeg::s
+    for (int b = 0; b < 2 * K + 1; ++b) c.gs[j][b] = vzero<V>();  // per segment: FaceSeg::gs
+  }
+  if (face_blocks > 0)
+    face_kernel_batched<D, K, A><<<face_blocks, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>(
+        (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs, t.fb, c);
+  if (lift_blocks > 0)
+    lift_kernel_batched<D, K, A><<<lift_blocks, t.lnt, lift_smem<D, K>(t.lcb), st>>>(
+        (const LiftSeg*)lsegs, (const FaceSeg<V, K>*)fsegs, nseg, (const SegPtrs<IO>*)ptrs, t.lcb);
+  return cudaGetLastError();
+}
 
 // The scaled jump vectors s_j g_j[b] (k x (2k+1)) of one problem in the value type of the
 // arithmetic (4 or 8 bytes per value), as the face kernels use them.
@@ -255,139 +312,13 @@ void scaled_jumps(int k, const double* g, const double* s, std::vector<unsigned 
     for (int b = 0; b < 2 * k + 1; ++b) o[j * (2 * k + 1) + b] = from_host<V>(s[j] * g[j * (2 * k + 1) + b]);
 }
 
-// faces per face item, owner cells per lift item and the dynamic shared memory of either,
-// for degree k, the launches' thread counts and value size vb (the formulas of gp_pbatch.cuh)
-inline int pb_fb_rt(int d, int k, int face_threads) {
-  const int L = d == 3 ? (k + 1) * (k + 1) : k + 1;
-  return face_threads / L > 0 ? face_threads / L : 1;
-}
-inline int pb_cb_rt(int d, int k, int lift_threads) {
-  const int KR = d == 3 ? k * k : k;
-  return (2 * lift_threads) / KR > 0 ? (2 * lift_threads) / KR : 1;
-}
-inline size_t pb_face_smem_rt(int d, int k, int face_threads, size_t vb) {
-  const int L = d == 3 ? (k + 1) * (k + 1) : k + 1;
-  return (size_t)(d == 3 ? 2 : 1) * (pb_fb_rt(d, k, face_threads) + 1) * k * L * vb;
-}
-inline size_t pb_lift_smem_rt(int d, int k, int lift_threads) {
-  return (size_t)pb_cb_rt(d, k, lift_threads) * ((d == 3 ? 36 : 12) + 1) * sizeof(int);
-}
-
-// Device records of a group's problems (PBProb of the arithmetic) and the work lists: face
-// items (faces of one axis, then groups of zero runs) and lift items (owner cells), in problem
-// order; fsm / lsm receive the launches' dynamic shared memory.
-template <int D, class A>
-void pb_pack(const std::vector<PBSpec>& in, int face_threads, int lift_threads, std::vector<unsigned char>& probs,
-             std::vector<int4>& fitems, std::vector<int4>& litems, size_t& fsm, size_t& lsm) {
-  using V = typename A::V;
-  using IO = typename A::IO;
-  probs.assign(in.size() * sizeof(PBProb<V, IO>), 0);
-  fitems.clear();
-  litems.clear();
-  fsm = lsm = 0;
-  std::vector<int4> zitems;
-  for (size_t i = 0; i < in.size(); ++i) {
-    const PBSpec& sp = in[i];
-    PBProb<V, IO> pr{};
-    pr.frows = sp.frows;
-    pr.lwin = sp.lwin;
-    pr.lrow = sp.lrow;
-    pr.zruns = sp.zruns;
-    pr.wp = (V*)sp.wp;
-    pr.gs = (const V*)sp.gs;
-    for (int a = 0; a < 4; ++a) {
-      pr.rbase[a] = sp.rbase[a];
-      pr.fstart[a] = sp.fstart[a];
-    }
-    pr.wstride = sp.wstride;
-    pr.nlift = sp.nlift;
-    pr.n_active = sp.n_active;
-    pr.k = sp.k;
-    std::memcpy(&probs[i * sizeof(pr)], &pr, sizeof(pr));
-    const int fb = pb_fb_rt(D, sp.k, face_threads), cb = pb_cb_rt(D, sp.k, lift_threads);
-    fsm = std::max(fsm, pb_face_smem_rt(D, sp.k, face_threads, sizeof(V)));
-    lsm = std::max(lsm, pb_lift_smem_rt(D, sp.k, lift_threads));
-    for (int a = 0; a < D; ++a)
-      for (int f = sp.fstart[a]; f < sp.fstart[a + 1]; f += fb)
-        fitems.push_back(make_int4((int)i, a, f, std::min(fb, sp.fstart[a + 1] - f)));
-    for (int z = 0; z < sp.nzruns; z += ZGROUP) zitems.push_back(make_int4((int)i, 3, z, std::min(ZGROUP, sp.nzruns - z)));
-    if (sp.fstart[D] > 0)
-      for (int c = 0; c < sp.nlift; c += cb) litems.push_back(make_int4((int)i, 0, c, std::min(cb, sp.nlift - c)));
-  }
-  fitems.insert(fitems.end(), zitems.begin(), zitems.end());
-}
-
-// Persistent grid of one launch: resident CTAs per SM x SMs, at most one per item.
-template <class F>
-int pb_grid(F kernel, int threads, size_t smem, int nitems) {
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
-  const int g = std::max(1, per) * std::max(1, nsm);
-  return std::max(1, std::min(g, nitems));
-}
-
-// The face launch and the lift launch of one group of degree K (g, m: its 1D data).
-template <int D, int K, class A>
-cudaError_t pb_run_k(const PBArgs& fa, const PBArgs& la, const double* g, const double* m, int face_threads,
-                     size_t fsm, int lift_threads, size_t lsm, cudaStream_t st) {
-  using V = typename A::V;
-  static bool raised[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !raised[dev]) {
-    cudaError_t e =
-        cudaFuncSetAttribute(face_kernel_pb<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(lift_kernel_pb<D, K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e != cudaSuccess) return e;
-    raised[dev] = true;
-  }
-  if (fsm > 96 * 1024 || lsm > 96 * 1024) return cudaErrorInvalidConfiguration;
-  Consts<V, K> c;
-  for (int j = 0; j < K; ++j)
-    for (int b = 0; b < 2 * K + 1; ++b) {
-      c.g[j][b] = from_host<V>(g[j * (2 * K + 1) + b]);
-      c.gs[j][b] = vzero<V>();   // per problem: PBProb::gs
-    }
-  for (int p = 0; p < K + 1; ++p)
-    for (int q = 0; q < K + 1; ++q) c.m[p][q] = from_host<V>(m[p * (K + 1) + q]);
-  mass_halves<V, K>(m, c);
-  if (fa.nitems > 0) {
-    const int grid = pb_grid(face_kernel_pb<D, K, A>, face_threads, fsm, fa.nitems);
-    face_kernel_pb<D, K, A><<<grid, face_threads, fsm, st>>>(fa, c);
-  }
-  if (la.nitems > 0) {
-    const int grid = pb_grid(lift_kernel_pb<D, K, A>, lift_threads, lsm, la.nitems);
-    lift_kernel_pb<D, K, A><<<grid, lift_threads, lsm, st>>>(la);
-  }
-  return cudaGetLastError();
-}
-
-template <int D, class A>
-cudaError_t pb_run(int k, const PBArgs& fa, const PBArgs& la, const double* g, const double* m, int face_threads,
-                   size_t fsm, int lift_threads, size_t lsm, cudaStream_t st) {
-  switch (k) {
-    case 1: return pb_run_k<D, 1, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 2: return pb_run_k<D, 2, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 3: return pb_run_k<D, 3, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 4: return pb_run_k<D, 4, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 5: return pb_run_k<D, 5, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 6: return pb_run_k<D, 6, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 7: return pb_run_k<D, 7, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    case 8: return pb_run_k<D, 8, A>(fa, la, g, m, face_threads, fsm, lift_threads, lsm, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 // Per translation unit: batch packing and launch for one (arithmetic, dimension).
 struct BatchOps {
+  bool (*pack)(int k, const std::vector<SegSpec>&, Tiles&, std::vector<unsigned char>&,
+               std::vector<unsigned char>&, int&, int&);
   void (*jumps)(int k, const double* g, const double* s, std::vector<unsigned char>& out);
-  void (*pack)(const std::vector<PBSpec>&, int, int, std::vector<unsigned char>&, std::vector<int4>&,
-               std::vector<int4>&, size_t&, size_t&);
-  cudaError_t (*run)(int k, const PBArgs&, const PBArgs&, const double*, const double*, int, size_t, int, size_t,
-                     cudaStream_t);
-  size_t vbytes;
+  cudaError_t (*run)(int k, const void*, const void*, const void*, int, int, int, const double*, const double*,
+                     Tiles, cudaStream_t);
 };
 BatchOps batch_ops_f64_d2();
 BatchOps batch_ops_f64_d3();
@@ -396,12 +327,37 @@ BatchOps batch_ops_f32_d3();
 BatchOps batch_ops_ff_d2();
 BatchOps batch_ops_ff_d3();
 
-#define GP_BATCH_OPS(D, A)           \
-  BatchOps ops;                      \
-  ops.jumps = scaled_jumps<A>;       \
-  ops.pack = pb_pack<D, A>;          \
-  ops.run = pb_run<D, A>;            \
-  ops.vbytes = sizeof(typename A::V); \
+#define GP_BATCH_OPS(D, A)                                                                              \
+  BatchOps ops;                                                                                         \
+  ops.jumps = scaled_jumps<A>;                                                                          \
+  ops.pack = [](int k, const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned char>& fs,       \
+                std::vector<unsigned char>& ls, int& fb, int& lb) -> bool {                             \
+    switch (k) {                                                                                        \
+      case 1: return pack_batch<D, 1, A>(in, t, fs, ls, fb, lb);                                        \
+      case 2: return pack_batch<D, 2, A>(in, t, fs, ls, fb, lb);                                        \
+      case 3: return pack_batch<D, 3, A>(in, t, fs, ls, fb, lb);                                        \
+      case 4: return pack_batch<D, 4, A>(in, t, fs, ls, fb, lb);                                        \
+      case 5: return pack_batch<D, 5, A>(in, t, fs, ls, fb, lb);                                        \
+      case 6: return pack_batch<D, 6, A>(in, t, fs, ls, fb, lb);                                        \
+      case 7: return pack_batch<D, 7, A>(in, t, fs, ls, fb, lb);                                        \
+      case 8: return pack_batch<D, 8, A>(in, t, fs, ls, fb, lb);                                        \
+      default: return false;                                                                            \
+    }                                                                                                   \
+  };                                                                                                    \
+  ops.run = [](int k, const void* fs, const void* ls, const void* pt, int ns, int fb, int lb,          \
+               const double* g, const double* m, Tiles t, cudaStream_t st) -> cudaError_t {             \
+    switch (k) {                                                                                        \
+      case 1: return run_batch<D, 1, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 2: return run_batch<D, 2, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 3: return run_batch<D, 3, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 4: return run_batch<D, 4, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 5: return run_batch<D, 5, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 6: return run_batch<D, 6, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 7: return run_batch<D, 7, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      case 8: return run_batch<D, 8, A>(fs, ls, pt, ns, fb, lb, g, m, t, st);                           \
+      default: return cudaErrorInvalidValue;                                                            \
+    }                                                                                                   \
+  };                                                                                                    \
   return ops;
 
 // y (+)= (wm M_active + ws K_active) x over the active cells (cell kernel + gather; add = 1:
