@@ -155,7 +155,7 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
   }
   __syncthreads();
   V out[K];
-  if constexpr (std::is_same<V, ff64>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
+  if constexpr (TangentialByLine<V>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
   else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
   V w[NN];
   if (valid) {

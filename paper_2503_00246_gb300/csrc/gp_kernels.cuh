@@ -208,8 +208,17 @@ __device__ __forceinline__ void mass_line_eo(const Consts<V, K>& c, const V (&u)
   }
 }
 
-// The tangential masses through the even / odd halves (float-float, where an arithmetic
-// operation costs about 12 float instructions): one thread per (order j, tangential line) applies M^ to a
+// Which tangential pass an arithmetic takes: line_tangential_eo (one thread per line of k+1
+// values, even / odd halves of M^) for float-float, where an operation costs about 12 float
+// instructions, and for FP32, whose face kernel is bound by its memory instructions (the
+// line form moves 2 (k+1) shared-memory values per line instead of (k+1)^2); line_tangential
+// (one output per thread) for native FP64.
+template <typename V>
+struct TangentialByLine {
+  static constexpr bool value = !std::is_same<V, double>::value;
+};
+
+// The tangential masses through the even / odd halves: one thread per (order j, tangential line) applies M^ to a
 // whole line of k+1 values, pass by pass, in 3D through plane2 and back into plane, in 2D in
 // place (plane2 is not used there: the 2D face kernels hold one plane per face); each thread
 // then reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
@@ -359,7 +368,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   }
   __syncthreads();
   V out[K];
-  if constexpr (std::is_same<V, ff64>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
+  if constexpr (TangentialByLine<V>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
   else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
 
   // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], in patch order
