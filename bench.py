@@ -157,21 +157,32 @@ class Clocks:
 
 # ---------------------------------------------------------------- GPU arm --
 
-def _flops_face(d, k, nf):
+def _flops_face(d, k, nf, prec="fp64"):
     """Flops the face kernel executes (a multiply-add counts 2, a multiply or add 1; an
     n-term dot product 2n - 1), per normal line: the even-odd split (2k adds), the k
-    jump dot products (k + 1 terms for odd orders, k for even ones), (d-1) tangential
-    passes of k (k+1)-term dot products, k scalings, and the expansion (per node b <= k
-    one odd-order and, for b < k, one even-order partial sum, plus 2 adds)."""
+    jump dot products (k + 1 terms for odd orders, k for even ones), the tangential
+    masses, the scaling by s_j (FP32 only: FP64 and float-float fold s_j into the jump
+    vectors), and the expansion (per node b <= k one odd-order and, for b < k, one
+    even-order partial sum, plus 2 adds).  Tangential masses: native FP64 runs (d-1)
+    passes of k (k+1)-term dot products per line; FP32 and float-float apply M^ to whole
+    lines of N = k+1 values through its even / odd halves (2 floor(N/2) folds,
+    ceil(N/2) dot products of ceil(N/2) terms, floor(N/2) of floor(N/2) terms, 2 floor(N/2)
+    merges per N outputs), k N such lines per pass and face in 3D (k in 2D)."""
     L = (k + 1) ** (d - 1)
     n_odd, n_even = (k + 1) // 2, k // 2            # orders j = 1, 3, ... and j = 2, 4, ...
     contraction = 2 * k + n_odd * (2 * (k + 1) - 1) + n_even * (2 * k - 1)
-    tangential = (d - 1) * k * (2 * (k + 1) - 1)
+    if prec == "fp64":
+        tangential_face = L * (d - 1) * k * (2 * (k + 1) - 1)
+    else:
+        N = k + 1
+        H, NE = N // 2, (N + 1) // 2
+        task = 2 * H + NE * (2 * NE - 1) + H * (2 * H - 1) + 2 * H
+        tangential_face = (d - 1) * k * N * task if d == 3 else k * task
+    scaling = k if prec == "fp32" else 0
     expansion = (k + 1) * (2 * n_odd - 1)
     if k > 1:
         expansion += k * ((2 * n_even - 1) + 2)
-    per_line = contraction + tangential + k + expansion
-    return float(nf) * L * per_line
+    return float(nf) * (L * (contraction + scaling + expansion) + tangential_face)
 
 
 def _flops_paper(d, k, nf):
@@ -311,7 +322,8 @@ def run_sweep(args):
             tf = ms_face / calls * 1e-3
             nf = ctx.n_faces
             w = 4 if prec == gp.GP_FP32 else 8
-            fl_exec, fl_paper = _flops_face(pr.dim, k, nf), _flops_paper(pr.dim, k, nf)
+            fl_exec = _flops_face(pr.dim, k, nf, tags[prec].replace("ff64", "ff"))
+            fl_paper = _flops_paper(pr.dim, k, nf)
             r = {"gdofs": ctx.n_active / t / 1e9, "ms": t * 1e3, "face_ms": tf * 1e3, "lift_ms": ms_lift / calls,
                  "gfaces_per_s": nf / t / 1e9,
                  "face_tflops_executed": fl_exec / tf / 1e12, "face_frac_of_peak": fl_exec / tf / 1e12 / peak[prec],
@@ -547,7 +559,7 @@ def form_summary(rec, pr, prec, gp, hbm, peak_src, ws=1):
     fp32_peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     peak = {gp.GP_FP64: fp64_peak, gp.GP_FP32: fp32_peak, gp.GP_FP64_FF: fp32_peak / FF_OPS_PER_FMA}[prec]
     kname = {gp.GP_FP64: "double", gp.GP_FP32: "float", gp.GP_FP64_FF: "ff64"}[prec]
-    flop_face = _flops_face(d, k, nf)
+    flop_face = _flops_face(d, k, nf, {gp.GP_FP64: "fp64", gp.GP_FP32: "fp32", gp.GP_FP64_FF: "ff"}[prec])
     brick = rec["kernel_path"]["path"] == gp.GP_PATH_BRICK
     kernels = ("brick_kernel", "plane_fixup_kernel") if brick else ("face_kernel", "lift_kernel")
     roof = {"bound": "alu", "kernel": f"{kernels[0]}<{d},{k},{kname}>",

@@ -18,11 +18,17 @@ def test_executed_flop_count_below_paper_count():
     # and the count grows with the number of faces
     for d in (2, 3):
         for k in range(1, 9):
-            f1 = bench._flops_face(d, k, 1)
-            assert 0 < f1 < bench._flops_paper(d, k, 1)
-            assert bench._flops_face(d, k, 5) == 5 * f1
-    # d = 3, k = 3: 16 normal lines of 91 flops (the count the bench's roofline uses)
-    assert bench._flops_face(3, 3, 1) == 16 * 91
+            for prec in ("fp64", "fp32", "ff"):
+                f1 = bench._flops_face(d, k, 1, prec)
+                assert 0 < f1 < bench._flops_paper(d, k, 1)
+                assert bench._flops_face(d, k, 5, prec) == 5 * f1
+    # d = 3, k = 3, native FP64: 16 normal lines of 88 flops (91 before s_j was folded into the
+    # jump vectors: 3 multiplies less per line)
+    assert bench._flops_face(3, 3, 1) == 16 * 88
+    assert bench._flops_face(3, 3, 1, "fp32") == 16 * 88 + 16 * 3 + (bench._flops_face(3, 3, 1, "ff") - 16 * 88)
+    # the line form of the tangential masses does fewer flops than (d-1) k (2k+1) per line from k = 4 on
+    for k in (4, 6, 8):
+        assert bench._flops_face(3, k, 1, "ff") < bench._flops_face(3, k, 1, "fp64")
 
 
 def test_traffic_lookup_follows_the_committed_counters(tmp_path, monkeypatch):
