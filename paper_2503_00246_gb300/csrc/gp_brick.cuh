@@ -127,7 +127,6 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
                                             Sum<typename A::V>* ys,
                                             typename A::V (*buf)[K][Shape<D, K>::L],
                                             typename A::V (*sb2)[K][Shape<D, K>::L],
-                                            const typename A::V (*sm)[K + 1],
                                             const Consts<typename A::V, K>& c) {
   using V = typename A::V;
   constexpr int L = Shape<D, K>::L, NN = 2 * K + 1, K1 = K + 1;
@@ -155,8 +154,7 @@ __device__ __forceinline__ void brick_chunk(const uint32_t* __restrict__ bface, 
   }
   __syncthreads();
   V out[K];
-  if constexpr (TangentialByLine<V>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
-  else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
+  line_tangential_eo<D, K, V, L>(buf, sb2, fb, c, fl, tau, out);
   V w[NN];
   if (valid) {
     if constexpr (!FoldScale<V>::value) {
@@ -205,10 +203,8 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
   }
   const int brick = (int)blockIdx.x - ba.nzblocks;
   __shared__ int sd[BRICK_DESC];
-  __shared__ V sm[K1][K1];
   __shared__ short cmap[BRICK_CMAP];
   for (int i = t; i < BRICK_DESC; i += nt) sd[i] = __ldg(ba.bdesc + (size_t)brick * BRICK_DESC + i);
-  for (int i = t; i < K1 * K1; i += nt) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
   for (int i = t; i < BRICK_CMAP; i += nt) cmap[i] = -1;
   __syncthreads();
   const int cell_off = sd[0], nown = sd[1], ncell = sd[2], face_off = sd[3], nface = sd[4];
@@ -260,11 +256,11 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
     const int fl = t / L, tau = t - fl * L;
     const uint32_t* bf = ba.bface + face_off;
     const int a1 = sd[8], a2 = (D == 3) ? sd[9] : nface;
-    for (int f0 = 0; f0 < a1; f0 += fb) brick_chunk<D, K, A, 0>(bf, f0, a1, fl, tau, fb, xs, ys, buf, sb2, sm, c);
-    for (int f0 = a1; f0 < a2; f0 += fb) brick_chunk<D, K, A, 1>(bf, f0, a2, fl, tau, fb, xs, ys, buf, sb2, sm, c);
+    for (int f0 = 0; f0 < a1; f0 += fb) brick_chunk<D, K, A, 0>(bf, f0, a1, fl, tau, fb, xs, ys, buf, sb2, c);
+    for (int f0 = a1; f0 < a2; f0 += fb) brick_chunk<D, K, A, 1>(bf, f0, a2, fl, tau, fb, xs, ys, buf, sb2, c);
     if constexpr (D == 3) {
       for (int f0 = a2; f0 < nface; f0 += fb)
-        brick_chunk<D, K, A, 2>(bf, f0, nface, fl, tau, fb, xs, ys, buf, sb2, sm, c);
+        brick_chunk<D, K, A, 2>(bf, f0, nface, fl, tau, fb, xs, ys, buf, sb2, c);
     }
   }
 

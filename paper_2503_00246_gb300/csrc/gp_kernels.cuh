@@ -133,50 +133,6 @@ __device__ __forceinline__ void line_jumps(const V (&v)[2 * K + 1], const V (*g)
   }
 }
 
-// Tangential reference masses of one face: plane[j][tau] holds the jump values of the face's
-// lines (written by every line, then a barrier); each thread returns out[j] for its line
-// tau = t1 + (k+1) t2.  3D: two passes through plane2 with a barrier between them.  Every
-// thread of the CTA must call it (it synchronises).
-template <int D, int K, typename V, int L>
-__device__ __forceinline__ void line_tangential(V (*plane)[L], V (*plane2)[L], const V (*sm)[K + 1], const int tau,
-                                                V (&out)[K]) {
-  constexpr int K1 = K + 1;
-  if constexpr (D == 3) {
-    const int t1 = tau % K1, t2 = tau / K1;
-    V m1[K1];
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[t1][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], plane[j][K1 * t2]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane[j][q + K1 * t2]);
-      plane2[j][tau] = dot_value(acc);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[t2][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], plane2[j][t1]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane2[j][t1 + K1 * q]);
-      out[j] = dot_value(acc);
-    }
-  } else {
-    V m1[K1];
-#pragma unroll
-    for (int q = 0; q < K1; ++q) m1[q] = sm[tau][q];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      Dot<V> acc = dot_first(m1[0], plane[j][0]);
-#pragma unroll
-      for (int q = 1; q < K1; ++q) dot_fma(acc, m1[q], plane[j][q]);
-      out[j] = dot_value(acc);
-    }
-  }
-}
-
 // The mass matrix applied to one line of N = k+1 values u through its even and odd halves:
 // y[p] = E_p + O_p and y[N-1-p] = E_p - O_p, E_p = sum_i me[p][i] (u[i] + u[N-1-i]) (the middle
 // value once), O_p = sum_i mo[p][i] (u[i] - u[N-1-i]): (N/2)^2 + (N/2 rounded up)^2 terms and
@@ -208,55 +164,48 @@ __device__ __forceinline__ void mass_line_eo(const Consts<V, K>& c, const V (&u)
   }
 }
 
-// Which tangential pass an arithmetic takes: line_tangential_eo (one thread per line of k+1
-// values, even / odd halves of M^) for float-float, where an operation costs about 12 float
-// instructions, and for FP32, whose face kernel is bound by its memory instructions (the
-// line form moves 2 (k+1) shared-memory values per line instead of (k+1)^2); line_tangential
-// (one output per thread) for native FP64.
-template <typename V>
-struct TangentialByLine {
-  static constexpr bool value = !std::is_same<V, double>::value;
-};
-
-// The tangential masses through the even / odd halves: one thread per (order j, tangential line) applies M^ to a
-// whole line of k+1 values, pass by pass, in 3D through plane2 and back into plane, in 2D in
-// place (plane2 is not used there: the 2D face kernels hold one plane per face); each thread
-// then reads out[j] of its own line.  Every thread of the CTA must call it (it synchronises).
-// Native FP64 keeps the one-output-per-thread passes: only k (k+1) of the (k+1)^2 threads of a
-// face have a line here, and the FP64 pipe spends the same time on a partly idle warp (the
-// face kernel measured 2% slower at 128^3, k = 4).
+// The tangential masses applied line by line through the even / odd halves of M^: a task is
+// one (face, order j, tangential line of k+1 values); the tasks of the CTA's fb faces are
+// spread over its threads in order (task u on thread u), so the busy threads fill whole warps
+// and the rest of the CTA idles at the barriers.  Each task moves 2 (k+1) shared-memory values
+// instead of the (k+1)^2 of one output per thread, and does (k+1)^2 / 2 + O(k) instead of
+// (k+1)^2 multiply-adds.  3D: pass 1 along t1 from `plane` into `plane2`, pass 2 along t2 back
+// into `plane`; 2D: one pass, in place (the 2D kernels hold one plane per face).  Thread
+// (fl, tau) then reads out[j] = plane[fl][j][tau].  Every thread of the CTA must call it (it
+// synchronises); nt >= fb L.
 template <int D, int K, typename V, int L>
-__device__ __forceinline__ void line_tangential_eo(V (*plane)[L], V (*plane2)[L], const Consts<V, K>& c,
-                                                   const int tau, V (&out)[K]) {
+__device__ __forceinline__ void line_tangential_eo(V (*plane)[K][L], V (*plane2)[K][L], const int fb,
+                                                   const Consts<V, K>& c, const int fl, const int tau,
+                                                   V (&out)[K]) {
   constexpr int N = K + 1;
-  const bool task = tau < ((D == 3) ? K * N : K);
-  const int j = (D == 3) ? tau / N : tau, tr = (D == 3) ? tau % N : 0;
+  constexpr int T = (D == 3) ? K * N : K;     // tasks per face and pass
+  const int u = threadIdx.x;
+  const bool task = u < fb * T;
+  const int tf = u / T, w = u - tf * T;
+  const int j = (D == 3) ? w / N : w, tr = (D == 3) ? w % N : 0;
   if (task) {       // first pass: along t1 within the line t2 = tr (2D: the only pass)
-    V u[N], yv[N];
+    V uu[N], yv[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) u[q] = plane[j][q + N * tr];
-    mass_line_eo<K, V>(c, u, yv);
-    V (*dst)[L] = (D == 3) ? plane2 : plane;   // 2D: the task owns row j of plane
+    for (int q = 0; q < N; ++q) uu[q] = plane[tf][j][q + N * tr];
+    mass_line_eo<K, V>(c, uu, yv);
+    V (*dst)[K][L] = (D == 3) ? plane2 : plane;   // 2D: the task owns row j of its face's plane
 #pragma unroll
-    for (int i = 0; i < N; ++i) dst[j][i + N * tr] = yv[i];
+    for (int i = 0; i < N; ++i) dst[tf][j][i + N * tr] = yv[i];
   }
   __syncthreads();
   if constexpr (D == 3) {
     if (task) {     // second pass: along t2 within the line t1 = tr
-      V u[N], yv[N];
+      V uu[N], yv[N];
 #pragma unroll
-      for (int q = 0; q < N; ++q) u[q] = plane2[j][tr + N * q];
-      mass_line_eo<K, V>(c, u, yv);
+      for (int q = 0; q < N; ++q) uu[q] = plane2[tf][j][tr + N * q];
+      mass_line_eo<K, V>(c, uu, yv);
 #pragma unroll
-      for (int i = 0; i < N; ++i) plane[j][tr + N * i] = yv[i];
+      for (int i = 0; i < N; ++i) plane[tf][j][tr + N * i] = yv[i];
     }
     __syncthreads();
-#pragma unroll
-    for (int jj = 0; jj < K; ++jj) out[jj] = plane[jj][tau];
-  } else {
-#pragma unroll
-    for (int jj = 0; jj < K; ++jj) out[jj] = plane[jj][tau];
   }
+#pragma unroll
+  for (int jj = 0; jj < K; ++jj) out[jj] = plane[fl][jj][tau];
 }
 
 // Normal expansion w[b] = sum_j g_j[b] sj[j] (sj: the tangential results of the line):
@@ -302,7 +251,6 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   typedef V Plane[K][L];
   Plane* buf = reinterpret_cast<Plane*>(dsm);            // [fb][K][L]
   Plane* sb2 = buf + fb;                                  // [fb][K][L], 3D only
-  __shared__ V sm[K1][K1];
   const int nt = (int)blockDim.x;
   // the lift may start its prologue as soon as every face CTA is running (programmatic
   // dependent launch; it waits for this grid's completion before it reads W)
@@ -337,7 +285,6 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   const int fl = t / L, tau = t - fl * L;
   const int f = f0 + fl;
   const bool valid = f < fend;
-  for (int i = t; i < K1 * K1; i += nt) sm[i / K1][i % K1] = c.m[i / K1][i % K1];
 
   // ---- gather this thread's normal line (2k+1 values)
   V v[NN];
@@ -368,8 +315,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   }
   __syncthreads();
   V out[K];
-  if constexpr (TangentialByLine<V>::value) line_tangential_eo<D, K, V, L>(buf[fl], sb2[fl], c, tau, out);
-  else line_tangential<D, K, V, L>(buf[fl], sb2[fl], sm, tau, out);
+  line_tangential_eo<D, K, V, L>(buf, sb2, fb, c, fl, tau, out);
 
   // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], in patch order
   if (valid) {
