@@ -157,21 +157,22 @@ class Clocks:
 
 # ---------------------------------------------------------------- GPU arm --
 
-def _flops_face(d, k, nf, prec="fp64"):
+def _flops_face(d, k, nf, prec="fp64", per_output=False):
     """Flops the face kernel executes (a multiply-add counts 2, a multiply or add 1; an
     n-term dot product 2n - 1), per normal line: the even-odd split (2k adds), the k
     jump dot products (k + 1 terms for odd orders, k for even ones), the tangential
     masses, the scaling by s_j (FP32 only: FP64 and float-float fold s_j into the jump
     vectors), and the expansion (per node b <= k one odd-order and, for b < k, one
-    even-order partial sum, plus 2 adds).  Tangential masses: native FP64 runs (d-1)
-    passes of k (k+1)-term dot products per line; FP32 and float-float apply M^ to whole
-    lines of N = k+1 values through its even / odd halves (2 floor(N/2) folds,
-    ceil(N/2) dot products of ceil(N/2) terms, floor(N/2) of floor(N/2) terms, 2 floor(N/2)
-    merges per N outputs), k N such lines per pass and face in 3D (k in 2D)."""
+    even-order partial sum, plus 2 adds).  Tangential masses: M^ applied to whole lines of
+    N = k+1 values through its even / odd halves (2 floor(N/2) folds, ceil(N/2) dot
+    products of ceil(N/2) terms, floor(N/2) of floor(N/2) terms, 2 floor(N/2) merges per N
+    outputs), k N such lines per pass and face in 3D (k in 2D).  prec = "fp64" with
+    per_output=True gives the earlier one-output-per-thread count ((d-1) passes of k
+    (k+1)-term dot products per line)."""
     L = (k + 1) ** (d - 1)
     n_odd, n_even = (k + 1) // 2, k // 2            # orders j = 1, 3, ... and j = 2, 4, ...
     contraction = 2 * k + n_odd * (2 * (k + 1) - 1) + n_even * (2 * k - 1)
-    if prec == "fp64":
+    if per_output:
         tangential_face = L * (d - 1) * k * (2 * (k + 1) - 1)
     else:
         N = k + 1

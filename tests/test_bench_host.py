@@ -22,13 +22,14 @@ def test_executed_flop_count_below_paper_count():
                 f1 = bench._flops_face(d, k, 1, prec)
                 assert 0 < f1 < bench._flops_paper(d, k, 1)
                 assert bench._flops_face(d, k, 5, prec) == 5 * f1
-    # d = 3, k = 3, native FP64: 16 normal lines of 88 flops (91 before s_j was folded into the
-    # jump vectors: 3 multiplies less per line)
-    assert bench._flops_face(3, 3, 1) == 16 * 88
-    assert bench._flops_face(3, 3, 1, "fp32") == 16 * 88 + 16 * 3 + (bench._flops_face(3, 3, 1, "ff") - 16 * 88)
+    # d = 3, k = 3, one output per thread: 16 normal lines of 88 flops (91 before s_j was folded
+    # into the jump vectors: 3 multiplies less per line); FP32 keeps the 3 multiplies
+    assert bench._flops_face(3, 3, 1, per_output=True) == 16 * 88
+    assert bench._flops_face(3, 3, 1, "fp32") == bench._flops_face(3, 3, 1, "fp64") + 16 * 3
+    assert bench._flops_face(3, 3, 1, "ff") == bench._flops_face(3, 3, 1, "fp64")
     # the line form of the tangential masses does fewer flops than (d-1) k (2k+1) per line from k = 4 on
     for k in (4, 6, 8):
-        assert bench._flops_face(3, k, 1, "ff") < bench._flops_face(3, k, 1, "fp64")
+        assert bench._flops_face(3, k, 1) < bench._flops_face(3, k, 1, per_output=True)
 
 
 def test_traffic_lookup_follows_the_committed_counters(tmp_path, monkeypatch):
