@@ -488,7 +488,7 @@ def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tun
     stream = torch.cuda.current_stream()
     steps = args.steps if steps is None else steps
     path = {"auto": gp.GP_PATH_AUTO, "face_lift": gp.GP_PATH_FACE_LIFT, "brick": gp.GP_PATH_BRICK}[args.path]
-    ctx = gp.setup_problem(pr, precision=prec, device=dev.index or 0, path=path)
+    ctx = gp.setup_problem(pr, precision=prec, device=dev.index or 0, path=path, slabs=args.slabs)
     kp = gp.gp_kernel_path(ctx)
     tiles = None
     if tune and args.tune_reps > 0:          # tile shape picked on this GPU, before any timing
@@ -828,6 +828,8 @@ def main():
     ap.add_argument("--precision", default="all", choices=["fp64", "fp32", "ff", "all"])
     ap.add_argument("--check-rows", type=int, default=2000, help="sampled rows of the oracle error check")
     ap.add_argument("--no-sweep", action="store_true", help="leave out the bounded 96^3 degree sweep")
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="face + lift launch pipeline: 0 or 1 one launch pair, n about n slabs")
     ap.add_argument("--path", default="auto", choices=["auto", "face_lift", "brick"],
                     help="kernel path of the single-problem applies (gp_opts.kernel_path)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -122,6 +122,11 @@ typedef struct {
   int kernel_path;          /* GP_PATH_AUTO (0), GP_PATH_FACE_LIFT or GP_PATH_BRICK */
   int brick_smem;           /* brick path: shared-memory budget in bytes that picks the brick
                                shape (0: 100 KB) */
+  int slabs;                /* face + lift path: 0 or 1 = one face and one lift launch; n > 1 =
+                               a pipeline of about n slabs along the last axis (a face and a
+                               lift launch per slab, so that a slab's face outputs are still in
+                               L2 when its lift reads them).  Results are identical; on the
+                               128^3 gyroid (k = 4) every n > 1 measured slower on GB300. */
 } gp_opts;
 
 /* Kernel paths of gp_apply / gp_apply_add (same operator, same accuracy, rounding may differ):
@@ -293,7 +298,9 @@ gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream);
 /* Kernel path of a context: *path receives GP_PATH_BRICK or GP_PATH_FACE_LIFT; on the brick
  * path bdim (3 ints, may be NULL) receives the brick shape in cells and counts (3 int64, may
  * be NULL) the bricks that hold faces, the plane nodes shared by several bricks and the bytes
- * of the partial sums (the path's scratch). */
+ * of the partial sums (the path's scratch).  On the face + lift path bdim receives zeros and
+ * counts the slabs of gp_apply's launch pipeline (1: one face and one lift launch), 0 and the
+ * bytes of the face outputs. */
 gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* counts);
 
 /* End-to-end form with HOST buffers: copies x (n_active elements of the

@@ -139,6 +139,8 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
   a.ev = ev;
   a.tiles = tiles ? *tiles : c->tiles;
   a.which = which;
+  a.slabs = p.slabs.data();
+  a.nslab = p.num_slabs();
   if (brick) {
     a.brick = true;
     gp::BrickArgs& ba = a.ba;
@@ -241,6 +243,18 @@ gp_status gp_setup(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* op
     if (opts->kernel_path == GP_PATH_BRICK && !c->use_brick && p.num_faces() > 0) {
       delete c;
       return fail(nullptr, GP_EUNSUPPORTED, "no brick shape fits the shared-memory budget (use GP_PATH_AUTO)");
+    }
+    if (!c->use_brick) {
+      if (opts->slabs < 0) {
+        delete c;
+        return fail(nullptr, GP_EINVAL, "slabs must be >= 0");
+      }
+      try {
+        gp::build_slabs(p, std::min(opts->slabs, gpi::MAX_SLABS));
+      } catch (const std::bad_alloc&) {
+        delete c;
+        return fail(nullptr, GP_ENOMEM, "host allocation failed while building the slab pipeline");
+      }
     }
   }
   if (opts->device >= 0) {
@@ -392,9 +406,10 @@ gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* c
   if (bdim)
     for (int a = 0; a < 3; ++a) bdim[a] = ctx->use_brick ? p.bdim[a] : 0;
   if (counts) {
-    counts[0] = ctx->use_brick ? p.num_bricks() : 0;
+    counts[0] = ctx->use_brick ? p.num_bricks() : std::max(1, p.num_slabs());
     counts[1] = ctx->use_brick ? p.num_plane_nodes() : 0;
-    counts[2] = ctx->use_brick ? (int64_t)gpi::brick_scratch_bytes(ctx) : 0;
+    counts[2] = ctx->use_brick ? (int64_t)gpi::brick_scratch_bytes(ctx)
+                               : p.num_faces() * p.L * (2 * p.k + 1) * (p.precision == GP_FP32 ? 4 : 8);
   }
   return GP_OK;
 }

@@ -181,7 +181,7 @@ brick_kernel(const typename A::IO* __restrict__ x, typename A::IO* __restrict__ 
              const BrickArgs ba, const int fb, const __grid_constant__ Consts<typename A::V, K> c) {
   using V = typename A::V;
   using IO = typename A::IO;
-  constexpr int L = Shape<D, K>::L, NN = 2 * K + 1, K1 = K + 1;
+  constexpr int L = Shape<D, K>::L, K1 = K + 1;
   constexpr int NB = (D == 3) ? K1 * K1 * K1 : K1 * K1;
   typedef V Plane[K][L];
   const int t = threadIdx.x, nt = (int)blockDim.x;

@@ -47,9 +47,10 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
   p.pslot.clear();
   const int64_t nf = p.num_faces();
   if (nf == 0 || p.partitioned) return false;
-  std::vector<BrickShape> shapes;
-  if (d == 3) shapes = {{{4, 4, 4}}, {{4, 4, 2}}, {{4, 2, 2}}, {{2, 2, 2}}};
-  else shapes = {{{16, 16, 1}}, {{8, 8, 1}}, {{4, 4, 1}}, {{2, 2, 1}}};
+  static const BrickShape shapes3[4] = {{{4, 4, 4}}, {{4, 4, 2}}, {{4, 2, 2}}, {{2, 2, 2}}};
+  static const BrickShape shapes2[4] = {{{16, 16, 1}}, {{8, 8, 1}}, {{4, 4, 1}}, {{2, 2, 1}}};
+  const BrickShape* shapes = d == 3 ? shapes3 : shapes2;
+  constexpr size_t nshapes = 4;
   const int64_t stride[3] = {1, n, (int64_t)n * n};
   auto coords = [&](int64_t c, int out[3]) {
     out[0] = (int)(c % n);
@@ -60,7 +61,7 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
   for (size_t i = 0; i < p.inv_cells.size(); ++i) inv_of[p.inv_cells[i]] = (int32_t)i;
   const int64_t nbl = ipow_host(k + 1, d);
   // pick the largest shape whose busiest brick fits the budget
-  for (size_t si = 0; si < shapes.size(); ++si) {
+  for (size_t si = 0; si < nshapes; ++si) {
     const int* B = shapes[si].b;
     int nbx[3] = {1, 1, 1};
     for (int a = 0; a < d; ++a) nbx[a] = (n + B[a] - 1) / B[a];
@@ -103,7 +104,7 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
     // the local row starts or the jump planes (extra bytes), each rounded up to 16 bytes
     const size_t need = (size_t)max_cell * nbl * vbytes + (size_t)max_own * nbl * sbytes + (size_t)max_own * 4 +
                         std::max(extra, (size_t)max_cell * L * 4) + 48;
-    const bool last = si + 1 == shapes.size();
+    const bool last = si + 1 == nshapes;
     if (max_cell >= 1024 || (need > smem_budget && !last)) continue;
     if (need > smem_budget) return false;
     // ---- commit this shape

@@ -66,6 +66,9 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m);
 gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
                  bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3);
 
+// Slab pipeline of the face + lift path (gp_opts.slabs): at most MAX_SLABS slabs.
+static_assert(gp::SLAB == gp::SLAB_INTS, "the plan's and the launcher's slab records differ");
+constexpr int MAX_SLABS = 64;
 // Default faces per chunk of the brick kernel (about 256 threads).
 int brick_default_fb(int dim, int k);
 // Bytes of the brick path's partial grids (its scratch) for context c.

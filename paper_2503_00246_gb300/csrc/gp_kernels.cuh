@@ -88,12 +88,15 @@ void mass_halves(const double* m, Consts<V, K>& c) {
 
 struct FaceArgs {
   const int32_t* frows;   // per-face row starts of the patch (see rbase)
-  int64_t rbase[4];       // first row entry of each axis' faces
-  int32_t fstart[4];      // first face of each axis; fstart[D] = nf
+  int64_t rbase[4];       // row entry of face fstart[a] of each axis
+  int32_t fstart[4];      // first face of each axis in this launch
+  int32_t fend[4];        // one past the last face of each axis in this launch
   int32_t bstart[4];      // first CTA of each axis (after the zero-fill CTAs); bstart[D] = grid
   const int2* zruns;      // (c0, len <= 256) runs of untouched active DoFs
   int32_t nzruns;         // 0 for the add form
   int32_t nzblocks;       // zero-fill CTAs at the front of the grid
+  int32_t tail_wait;      // 1: before exiting, wait for the grid this launch programmatically
+                          // depends on (slab pipeline: so that this grid completes after it)
 };
 
 constexpr int ZGROUP = 16;  // zero runs per zero-fill CTA
@@ -272,13 +275,13 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     return;
   }
   // axis of this CTA's faces (constant indices only: no local-memory copy of fa)
-  int axis = 0, fbase = fa.fstart[0], fend = fa.fstart[1], bbase = fa.bstart[0];
+  int axis = 0, fbase = fa.fstart[0], fend = fa.fend[0], bbase = fa.bstart[0];
   int64_t rbase = fa.rbase[0];
   if (D >= 2 && blk >= fa.bstart[1]) {
-    axis = 1; fbase = fa.fstart[1]; fend = fa.fstart[2]; bbase = fa.bstart[1]; rbase = fa.rbase[1];
+    axis = 1; fbase = fa.fstart[1]; fend = fa.fend[1]; bbase = fa.bstart[1]; rbase = fa.rbase[1];
   }
   if (D >= 3 && blk >= fa.bstart[2]) {
-    axis = 2; fbase = fa.fstart[2]; fend = fa.fstart[3]; bbase = fa.bstart[2]; rbase = fa.rbase[2];
+    axis = 2; fbase = fa.fstart[2]; fend = fa.fend[2]; bbase = fa.bstart[2]; rbase = fa.rbase[2];
   }
   const int f0 = fbase + (blk - bbase) * fb;
   const int t = threadIdx.x;
@@ -353,6 +356,7 @@ face_kernel(const typename A::IO* __restrict__ x, typename A::V* __restrict__ wp
             typename A::IO* __restrict__ y, const FaceArgs fa, const int fb,
             const __grid_constant__ Consts<typename A::V, K> c) {
   face_body<D, K, A>(x, wp, y, fa, c, FoldScale<typename A::V>::value ? c.gs : c.g, c.s, blockIdx.x, fb, gp_dyn_smem);
+  if (fa.tail_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // --------------------------------------------------------------- batches --

@@ -30,6 +30,8 @@ struct ApplyArgs {
   cudaEvent_t* ev = nullptr;  // optional: 3 events recorded around the two kernels
   Tiles tiles{};              // 0 fields: the defaults of default_tiles
   int which = 3;              // bit 0: face kernel, bit 1: lift kernel (the autotuner times them apart)
+  const int32_t* slabs = nullptr;  // host: SLAB ints per slab (see Plan::slabs); nslab > 1: slab pipeline
+  int nslab = 0;
   bool brick = false;         // the brick path (brick kernel + plane fixup) instead of face + lift
   BrickArgs ba{};             // brick tables (zero-run fields are filled by the launcher)
   PlaneArgs pa{};             // plane-fixup tables
@@ -165,6 +167,83 @@ cudaError_t run_brick(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, cu
   return cudaGetLastError();
 }
 
+// ints per slab of the slab pipeline: owner range [lo, hi), then per axis the face range [lo, hi)
+constexpr int SLAB_INTS = 8;
+
+// Launches kernel with programmatic stream serialization (it may start when its predecessor
+// signals griddepcontrol.launch_dependents).
+template <typename... P, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// The face + lift path as a pipeline of slabs along the last axis, so that the face outputs of a
+// slab are still in L2 when its lift reads them: face(0), lift(0), face(1), lift(1), ...  Slab s
+// holds a range of owner cells and the faces that range needs and no earlier range needed.
+// lift(s) waits for face(s) before it reads W; face(s + 1) starts once every CTA of lift(s) has
+// passed that wait, overlaps lift(s) (it writes other face outputs and reads only x), and waits for
+// lift(s) only before it exits, so that each grid completes after all earlier ones (the last lift
+// completes last).  The first face launch also zero-fills.
+template <int D, int K, class A>
+cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, const Tiles& t, cudaStream_t st) {
+  using S = Shape<D, K>;
+  using V = typename A::V;
+  using IO = typename A::IO;
+  const int R[3] = {S::L, (D == 3) ? S::NN * (K + 1) : S::NN, S::NN * (K + 1)};   // row entries per face
+  constexpr int KR = LiftShape<D, K>::KR, NW = LiftShape<D, K>::NW;
+  for (int s = 0; s < Ar.nslab; ++s) {
+    const int32_t* sl = Ar.slabs + (size_t)s * SLAB_INTS;
+    FaceArgs fa;
+    fa.frows = Ar.frows;
+    fa.zruns = Ar.zruns;
+    fa.nzruns = s == 0 ? Ar.nzruns : 0;
+    fa.nzblocks = (fa.nzruns + ZGROUP - 1) / ZGROUP;
+    fa.tail_wait = s > 0;
+    int32_t nb = fa.nzblocks;
+    for (int a = 0; a < 4; ++a) {
+      const bool in = a < D;
+      fa.fstart[a] = in ? sl[2 + 2 * a] : 0;
+      fa.fend[a] = in ? sl[3 + 2 * a] : 0;
+      fa.rbase[a] = in ? Ar.rbase[a] + (int64_t)(fa.fstart[a] - Ar.fstart[a]) * R[a] : 0;
+    }
+    for (int a = 0; a < D; ++a) {
+      fa.bstart[a] = nb;
+      nb += (fa.fend[a] - fa.fstart[a] + t.fb - 1) / t.fb;
+    }
+    for (int a = D; a < 4; ++a) fa.bstart[a] = nb;
+    if (nb > 0) {
+      const cudaError_t e =
+          s == 0 ? (face_kernel<D, K, A><<<nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>(
+                        (const IO*)Ar.x, (V*)Ar.tp, (IO*)Ar.y, fa, t.fb, c),
+                    cudaGetLastError())
+                 : launch_pdl(face_kernel<D, K, A>, nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st, (const IO*)Ar.x,
+                              (V*)Ar.tp, (IO*)Ar.y, fa, (int)t.fb, c);
+      if (e != cudaSuccess) return e;
+    }
+    LiftArgs la = Ar.la;
+    la.lwin = Ar.la.lwin + (size_t)sl[0] * NW;
+    la.lrow = Ar.la.lrow + (size_t)sl[0] * KR;
+    la.nlift = sl[1] - sl[0];
+    const int32_t nlb = (la.nlift + t.lcb - 1) / t.lcb;
+    if (nlb > 0) {
+      const cudaError_t e = launch_pdl(lift_kernel<D, K, A>, nlb, t.lnt, lift_smem<D, K>(t.lcb), st, (const V*)Ar.tp,
+                                       (IO*)Ar.y, Ar.add, la, (int)t.lcb);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
 template <int D, int K, class A>
 cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   using S = Shape<D, K>;
@@ -183,14 +262,17 @@ cudaError_t run_apply(const ApplyArgs& Ar, cudaStream_t st) {
   if (Ar.brick) return run_brick<D, K, A>(Ar, c, st);
   Tiles t = Ar.tiles;
   if (!resolve_tiles<D, K, V>(t)) return cudaErrorInvalidConfiguration;
+  if (Ar.nslab > 1 && !Ar.ev && Ar.which == 3) return run_slabs<D, K, A>(Ar, c, t, st);
   FaceArgs fa;
   fa.frows = Ar.frows;
   for (int a = 0; a < 4; ++a) fa.rbase[a] = Ar.rbase[a];
   fa.zruns = Ar.zruns;
   fa.nzruns = Ar.nzruns;
   fa.nzblocks = (Ar.nzruns + ZGROUP - 1) / ZGROUP;
+  fa.tail_wait = 0;
   int32_t nb = fa.nzblocks;
   for (int a = 0; a < 4; ++a) fa.fstart[a] = Ar.fstart[a];
+  for (int a = 0; a < 4; ++a) fa.fend[a] = a < D ? Ar.fstart[a + 1] : Ar.fstart[D];
   for (int a = 0; a < D; ++a) {
     fa.bstart[a] = nb;
     nb += (Ar.fstart[a + 1] - Ar.fstart[a] + t.fb - 1) / t.fb;
@@ -252,6 +334,8 @@ bool pack_batch(const std::vector<SegSpec>& in, Tiles& t, std::vector<unsigned c
     FaceSeg<V, K> fs;
     fs.fa = in[i].fa;
     fs.fa.nzblocks = (fs.fa.nzruns + ZGROUP - 1) / ZGROUP;
+    fs.fa.tail_wait = 0;
+    for (int a = 0; a < 4; ++a) fs.fa.fend[a] = a < D ? fs.fa.fstart[a + 1] : fs.fa.fstart[D];
     int32_t nb = fs.fa.nzblocks;
     for (int a = 0; a < D; ++a) {
       fs.fa.bstart[a] = nb;

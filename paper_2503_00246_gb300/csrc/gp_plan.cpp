@@ -517,6 +517,34 @@ static bool classify_sampled(const Plan& p, const gp_levelset* ls, int n, double
 
 // ----------------------------------------------------------- numbering --
 
+void build_slabs(Plan& p, int nslab) {
+  p.slabs.clear();
+  const int64_t nlift = p.num_lift_cells(), ngroup = (nlift + SLAB_GROUP - 1) / SLAB_GROUP;
+  if (nslab <= 1 || ngroup < 2 || p.num_faces() == 0) return;
+  nslab = (int)std::min<int64_t>(nslab, ngroup);
+  const int d = p.dim, nw = p.lwin_width / d;
+  int32_t done[3] = {p.fstart[0], p.fstart[1], p.fstart[2]};   // faces of earlier slabs: [fstart, done)
+  for (int s = 0; s < nslab; ++s) {
+    const int64_t lo = std::min(nlift, (ngroup * s / nslab) * SLAB_GROUP);
+    const int64_t hi = s == nslab - 1 ? nlift : std::min(nlift, (ngroup * (s + 1) / nslab) * SLAB_GROUP);
+    int32_t need[3] = {done[0], done[1], done[2]};
+    for (int64_t i = lo; i < hi; ++i)
+      for (int a = 0; a < d; ++a)
+        for (int w = 0; w < nw; ++w) {
+          const int32_t f = p.lwin[(size_t)p.lwin_width * i + a * nw + w];
+          if (f >= 0) need[a] = std::max(need[a], f + 1);
+        }
+    int32_t sl[SLAB] = {(int32_t)lo, (int32_t)hi, 0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      const int32_t end = s == nslab - 1 ? p.fstart[a + 1] : need[a];
+      sl[2 + 2 * a] = done[a];
+      sl[3 + 2 * a] = end;
+      done[a] = end;
+    }
+    p.slabs.insert(p.slabs.end(), sl, sl + SLAB);
+  }
+}
+
 int64_t Plan::compact(int X, int64_t row) const {
   int64_t base = row_start[row];
   for (int r = run_off[row]; r < run_off[row + 1]; ++r) {
@@ -959,7 +987,7 @@ gp_status build_plan(const gp_mesh* mesh, const gp_levelset* ls, const gp_opts* 
     // lexicographic order, so a warp's loads and stores stay in neighbouring memory (FP32 issue
     // is cheap on this GPU).
     if (opts->precision == GP_FP64) {
-      constexpr size_t LIFT_SORT_GROUP = 256;
+      constexpr size_t LIFT_SORT_GROUP = SLAB_GROUP;
       for (size_t g0 = 0; g0 < order.size(); g0 += LIFT_SORT_GROUP)
         std::stable_sort(order.begin() + g0, order.begin() + std::min(order.size(), g0 + LIFT_SORT_GROUP),
                          [](const std::pair<uint64_t, int64_t>& x, const std::pair<uint64_t, int64_t>& y) {

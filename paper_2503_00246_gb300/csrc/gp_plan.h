@@ -15,6 +15,7 @@ constexpr int ZRUN_MAX = 256;       // elements per zero run (one CTA pass)
 // ints per brick descriptor: first local cell, own cells, local cells, first face, faces,
 // brick coordinates bx, by, bz, first face of axis 1 and of axis 2 (the faces are sorted by axis)
 constexpr int BDESC = 10;
+constexpr int SLAB = 8;             // ints per slab of the slab pipeline
 
 enum : int8_t { OUTSIDE = 0, CUT = 1, INSIDE = 2 };
 
@@ -100,6 +101,12 @@ struct Plan {
   int32_t gstride[3] = {0, 0, 0};                 // row stride of box face a's grid
   int bmax_own = 0, bmax_cell = 0, bmax_face = 0;
   int64_t num_bricks() const { return bdim[0] == 0 ? 0 : (int64_t)bdesc.size() / BDESC; }
+
+  // slab pipeline of the face + lift path (build_slabs): SLAB ints per slab, the owner range
+  // [lo, hi) of the lift, then per axis the face range [lo, hi) that the slab's face launch
+  // evaluates (axes >= dim: 0, 0)
+  std::vector<int32_t> slabs;
+  int num_slabs() const { return (int)(slabs.size() / SLAB); }
   int64_t num_plane_nodes() const { return (int64_t)pnode.size(); }
 
   // FP64 1D reference data
@@ -142,6 +149,13 @@ bool macro_patch_1d(int k, std::vector<double>& vecs, std::vector<double>& lambd
 // of one chunk of faces), and fills bdim, nbx, bdesc, bcell, bccoord, bface, bslot, pnode,
 // poff, pslot, pgrid, goff and gstride.  Returns false (bdim[0] = 0) when no shape fits.
 bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_budget);
+// Slab pipeline of the face + lift path: cuts the lift owners (lexicographic, or sorted within
+// groups of SLAB_GROUP) into about nslab ranges of whole groups, and gives each range the faces
+// of each axis that it needs and no earlier range needed (the faces of an axis follow the
+// lexicographic order of their lower cells, as the owners do, so each is an id range).  The last
+// range also takes the remaining faces.  Fills slabs; nslab <= 1, or fewer than two ranges: empty.
+constexpr int SLAB_GROUP = 256;
+void build_slabs(Plan& p, int nslab);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`

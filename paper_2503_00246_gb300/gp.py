@@ -60,7 +60,8 @@ class gp_opts(C.Structure):
     _fields_ = [("degree", C.c_int), ("nweights", C.c_int), ("weights", C.POINTER(C.c_double)),
                 ("gamma", C.c_double), ("precision", C.c_int), ("all_faces", C.c_int),
                 ("device", C.c_int), ("part_lo", C.c_int), ("part_hi", C.c_int), ("stabilization", C.c_int),
-                ("no_scratch", C.c_int), ("kernel_path", C.c_int), ("brick_smem", C.c_int)]
+                ("no_scratch", C.c_int), ("kernel_path", C.c_int), ("brick_smem", C.c_int),
+                ("slabs", C.c_int)]
 
 
 class gp_tiles(C.Structure):
@@ -506,12 +507,15 @@ def gp_partition_slabs(mesh: gp_mesh, levelset: gp_levelset, opts: gp_opts, npar
 
 
 def gp_kernel_path(ctx: Context) -> dict:
-    """{"path": GP_PATH_*, "bdim": brick shape, "bricks", "plane_nodes", "scratch_bytes"}."""
+    """{"path": GP_PATH_*, "bdim": brick shape, "bricks", "plane_nodes", "scratch_bytes", "slabs"}
+    (bricks and plane_nodes 0 on the face + lift path, slabs 0 on the brick path)."""
     path = C.c_int()
     bd = (C.c_int32 * 3)()
     cn = (C.c_int64 * 3)()
     _check(lib.gp_kernel_path(ctx.handle, C.byref(path), bd, cn), ctx)
-    return {"path": path.value, "bdim": list(bd), "bricks": cn[0], "plane_nodes": cn[1], "scratch_bytes": cn[2]}
+    brick = path.value == GP_PATH_BRICK
+    return {"path": path.value, "bdim": list(bd), "bricks": cn[0] if brick else 0,
+            "plane_nodes": cn[1], "scratch_bytes": cn[2], "slabs": 0 if brick else cn[0]}
 
 
 def gp_reference_1d(ctx: Context):
@@ -547,9 +551,10 @@ def gp_version() -> str:
 
 # ------------------------------------------------------------ marshalling --
 
-def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None, path: int = GP_PATH_AUTO):
+def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None, path: int = GP_PATH_AUTO,
+                slabs: int = 0):
     """gp_mesh / gp_levelset / gp_opts for a workloads.Problem (kept alive in the tuple);
-    path is the kernel path (GP_PATH_*)."""
+    path is the kernel path (GP_PATH_*), slabs gp_opts.slabs."""
     mesh = gp_mesh()
     mesh.dim = pr.dim
     for a in range(3):
@@ -584,14 +589,16 @@ def structs_for(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=N
     if part is not None:
         opts.part_lo, opts.part_hi = int(part[0]), int(part[1])
     opts.kernel_path = int(path)
+    opts.slabs = int(slabs)
     return mesh, ls, opts, keep
 
 
 def setup_problem(pr: W.Problem, precision: int = GP_FP64, device: int = 0, part=None,
-                  path: int = GP_PATH_AUTO) -> Context:
+                  path: int = GP_PATH_AUTO, slabs: int = 0) -> Context:
     """Context for a workloads.Problem; part = (layer_lo, layer_hi) selects a slab partition,
-    path the kernel path (GP_PATH_AUTO, GP_PATH_FACE_LIFT, GP_PATH_BRICK)."""
-    mesh, ls, opts, keep = structs_for(pr, precision, device, part, path)
+    path the kernel path (GP_PATH_AUTO, GP_PATH_FACE_LIFT, GP_PATH_BRICK), slabs the face + lift
+    launch pipeline (gp_opts.slabs: 0 or 1 off, n about n slabs)."""
+    mesh, ls, opts, keep = structs_for(pr, precision, device, part, path, slabs)
     return gp_setup(mesh, ls, opts)
 
 
