@@ -320,23 +320,10 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
   V out[K];
   line_tangential_eo<D, K, V, L>(buf, sb2, fb, c, fl, tau, out);
 
-  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], in patch order
+  // ---- normal expansion W_F[b, tau] = sum_j g_j[b] s_j out[j], stored at tau + L b (the
+  // lanes of a face store neighbouring values)
   if (valid) {
-    V* dst = wp + (size_t)f * S::P;
-    int pos0, pstride;
-    if (axis == 0) {            // patch index b + NN * tau
-      pos0 = NN * tau;
-      pstride = 1;
-    } else if (D == 2 || axis == 1) {
-      // 3D normal y: tx + K1 (b + NN tz); 2D normal y: tx + K1 b
-      const int tx = (D == 3) ? tau % K1 : tau;
-      const int tz = (D == 3) ? tau / K1 : 0;
-      pos0 = tx + K1 * NN * tz;
-      pstride = K1;
-    } else {                    // normal z: tx + K1 (ty + K1 b)
-      pos0 = tau;
-      pstride = K1 * K1;
-    }
+    V* dst = wp + (size_t)f * S::P + tau;
     if constexpr (!FoldScale<V>::value) {
 #pragma unroll
       for (int j = 0; j < K; ++j) out[j] = vmul(sc[j], out[j]);
@@ -344,7 +331,7 @@ __device__ __forceinline__ void face_body(const typename A::IO* __restrict__ x, 
     V w[NN];
     line_expand<K, V>(c, out, w);
 #pragma unroll
-    for (int bb = 0; bb < NN; ++bb) dst[pos0 + pstride * bb] = w[bb];
+    for (int bb = 0; bb < NN; ++bb) dst[L * bb] = w[bb];
   }
 }
 
@@ -427,7 +414,9 @@ face_kernel_batched(const FaceSeg<typename A::V, K>* __restrict__ segs, const in
 // normal index b = p_a + (2 - s_a) k and tangential index tau_t = p_t + (1 - s_t) k.
 //
 // One thread takes one x-row (q, r) of an owner cell: its k nodes p = 0..k-1 are
-// contiguous in y and read contiguous entries of each face output.  The row type
+// contiguous in y.  Face outputs are stored as W_F[b][tau] (tau + L b, x the fastest
+// tangential index), so the row's nodes read entries L apart in a face of normal x and
+// contiguous entries in the other faces.  The row type
 // (q == 0, r == 0) fixes at compile time which of the 36 candidate faces can reach
 // the row (p = 0 is the only node on the lower x face).  Each node sums its
 // contributions in the fixed order (axis, s_a, s_1, s_2): bitwise reproducible.
@@ -458,8 +447,8 @@ template <int D, int K, class A, int M>
 __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, const int* win, const int q,
                                          const int r, Sum<typename A::V> (&acc)[K], unsigned& found) {
   using V = typename A::V;
-  constexpr int K1 = K + 1, NN = 2 * K + 1;
-  constexpr int P = Shape<D, K>::P;
+  constexpr int K1 = K + 1;
+  constexpr int P = Shape<D, K>::P, L = Shape<D, K>::L;
   constexpr bool SKIP = std::is_same<V, double>::value;
   constexpr bool QZ = (M & 1) != 0;   // q == 0
   constexpr bool RZ = (M & 2) != 0;   // r == 0 (3D)
@@ -467,24 +456,25 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
   // patch position of node p = 0 of this row in the face (a, s_a, s_1, s_2), and how
   // many of the row's k nodes that face reaches
   auto where = [&](const int a, const int sa, const int s1, const int s2, int& cnt) -> int {
-    if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face
+    if (a == 0) {             // b = p + (2 - s_a) k on the x-line (q', r') of the face (stride L)
       cnt = (sa == 0) ? 1 : K;
       const int tq = q + (1 - s1) * K;
       const int tr = (D == 3) ? r + (1 - s2) * K : 0;
-      return (2 - sa) * K + NN * (tq + K1 * tr);
+      return (2 - sa) * K * L + (tq + K1 * tr);
     }
     cnt = (s1 == 0) ? 1 : K;
-    if (a == 1) {             // x index p + (1 - s1) k, normal b = q + (2 - s_a) k
+    if (a == 1) {             // x index p + (1 - s1) k, z index r + (1 - s2) k, b = q + (2 - s_a) k
       const int bb = q + (2 - sa) * K;
       const int tz = (D == 3) ? r + (1 - s2) * K : 0;
-      return (1 - s1) * K + K1 * (bb + NN * tz);
+      return (1 - s1) * K + K1 * tz + L * bb;
     }
     const int ty = q + (1 - s2) * K;   // normal z: x index p + (1 - s1) k, y index q + (1 - s2) k
     const int bb = r + (2 - sa) * K;
-    return (1 - s1) * K + K1 * (ty + K1 * bb);
+    return (1 - s1) * K + K1 * ty + L * bb;
   };
 #pragma unroll
   for (int a = 0; a < D; ++a) {
+    const int ps = (a == 0) ? L : 1;   // patch stride between the row's nodes
     // zero-ness of the normal coordinate and of the two tangential coordinates
     const bool nz = (a == 0) ? true : ((a == 1) ? QZ : RZ);
     const bool xz = (a == 0) ? QZ : true;         // first tangential: y (a = 0) or x
@@ -509,8 +499,8 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
 #pragma unroll
             for (int p = 0; p < K; ++p)
               if (p < cnt) {
-                if ((found >> p) & 1u) sum_add(acc[p], src[p]);
-                else sum_set(acc[p], src[p]);
+                if ((found >> p) & 1u) sum_add(acc[p], src[p * ps]);
+                else sum_set(acc[p], src[p * ps]);
               }
             found |= (cnt == 1) ? 1u : ALL;
           }
@@ -534,7 +524,7 @@ __device__ __forceinline__ void lift_row(const typename A::V* __restrict__ wp, c
 #pragma unroll
             for (int p = 0; p < K; ++p)
               if (p < cnt) {
-                const V v = src[p];
+                const V v = src[p * ps];
                 ld[n++] = ok ? v : vzero<V>();
               }
             if (ok) found |= (cnt == 1) ? 1u : ALL;
