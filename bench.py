@@ -226,9 +226,9 @@ def run_profile(args):
 
 def run_batched(gp, W, torch, dev, prec, steps, warmup, tune_reps=0):
     """The batched workload: 64 independent 3D ball problems, n ~ U{16..96}, k ~ U{2..6},
-    4 right-hand sides each, replayed as one CUDA graph per apply (one persistent face launch
-    and one persistent lift launch over all degrees and right-hand sides).  Inputs (> 7 GB)
-    exceed L2."""
+    4 right-hand sides each, replayed as one CUDA graph per apply (one face launch and one
+    lift launch per degree, each over all problems and right-hand sides of that degree).
+    Inputs (> 7 GB) exceed L2."""
     probs = W.batched_3d()
     nrhs = 4
     ctxs = [gp.setup_problem(p, precision=prec, device=dev.index or 0, path=gp.GP_PATH_FACE_LIFT) for p in probs]
