@@ -104,6 +104,10 @@ typedef struct {
   int samples;              /* sub-intervals per cell edge for sampled kinds (<=0: 4) */
 } gp_levelset;
 
+/* Options of gp_setup.  Zero-initialise the struct (memset, or = {0} in C) and set the fields you
+ * need: 0 selects the default of every field (precision GP_FP64, device 0, the whole mesh, the
+ * ghost penalty, automatic kernel path, ...) except degree, which must be set, and gamma, whose 0
+ * gives G = 0 unless weights are given. */
 typedef struct {
   int degree;               /* k, 1 <= k <= 8 */
   int nweights;             /* 0, or k: per-order weights c_1..c_k */

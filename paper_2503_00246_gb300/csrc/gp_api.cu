@@ -202,7 +202,7 @@ gp_status check_apply(const gp_ctx* c, const void* x, const void* y) {
 
 extern "C" {
 
-const char* gp_version(void) { return "gp-gb300 0.1 (sm_103a)"; }
+const char* gp_version(void) { return "gp-gb300 0.2 (sm_103a)"; }
 
 const char* gp_last_error(const gp_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
