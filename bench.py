@@ -528,7 +528,8 @@ def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tun
            "wall_ms_per_step": wall * 1e3 / steps, "face_ms": ms_face / calls, "lift_ms": ms_lift / calls,
            "tiles": tiles, "rel_err_vs_oracle": err}
     if e2e:
-        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+        # end to end through the C ABI with pinned host buffers (the transfers inside the timed
+        # region: x gathered from the host on the touched DoFs, y copied back whole)
         xh = torch.tensor(x_np, dtype=tdt).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
         for _ in range(2):
@@ -541,7 +542,7 @@ def measure_form(gp, W, torch, pr, prec, dev, args, flush, o=None, e2e=True, tun
         e1.record(stream)
         torch.cuda.synchronize()
         rec["t_e2e"] = e0.elapsed_time(e1) / ne
-        rec["h2d"] = rec["d2h"] = xh.numel() * xh.element_size()
+        rec["h2d"], rec["d2h"] = gp.gp_apply_host_bytes(ctx)
         del xh, yh
     ctx.close()
     del x, y

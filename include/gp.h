@@ -307,10 +307,15 @@ gp_status gp_apply_noalloc(gp_ctx* ctx, const void* x, void* y, void* stream);
  * bytes of the face outputs. */
 gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* counts);
 
-/* End-to-end form with HOST buffers: copies x (n_active elements of the
- * context's precision) to the device, applies G, copies y back and waits
- * for completion.  Uses device buffers owned by the context. */
+/* End-to-end form with HOST buffers (n_active elements of the context's precision each):
+ * y = G x, waiting for completion.  A page-locked x (cudaHostAlloc, cudaHostRegister, torch
+ * pin_memory) is read by a gather kernel on the DoFs some face patch touches only (the only
+ * entries the face kernel reads); other host memory is copied whole.  y is computed in a device
+ * buffer owned by the context and copied back whole. */
 gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* stream);
+
+/* Bytes the last gp_apply_host of ctx moved from host to device and from device to host. */
+gp_status gp_apply_host_bytes(const gp_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
 /* Several independent problems, nrhs right-hand sides each (the batched workload
  * of many meshes of uneven n, k and geometry): x[p] and y[p] point to nrhs

@@ -19,7 +19,35 @@ cudaError_t noalloc_scratch(int device, void** out);
 
 namespace {
 thread_local std::string g_err;
+
+// dst[c0 + i] = src[c0 + i] over the runs (c0, len): one warp per run, consecutive lanes on
+// consecutive elements (src: a device view of page-locked host memory)
+template <typename T>
+__global__ void __launch_bounds__(256) gather_runs_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                         const int2* __restrict__ runs, const int nruns) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int r = w0; r < nruns; r += nw) {
+    const int2 run = __ldg(runs + r);
+    for (int i = lane; i < run.y; i += 32) dst[run.x + i] = src[run.x + i];
+  }
+}
 }  // namespace
+
+namespace gpi {
+cudaError_t gather_runs(const void* src, void* dst, const int2* runs, int nruns, int elem, cudaStream_t st) {
+  if (nruns <= 0) return cudaSuccess;
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::max(1, std::min((nruns + 7) / 8, 8 * nsm));
+  if (elem == 4)
+    gather_runs_kernel<float><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, runs, nruns);
+  else
+    gather_runs_kernel<double><<<blocks, 256, 0, st>>>((const double*)src, (double*)dst, runs, nruns);
+  return cudaGetLastError();
+}
+}  // namespace gpi
 
 namespace gpi {
 
@@ -27,6 +55,39 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m) {
   if (c) const_cast<gp_ctx*>(c)->err = m;
   else g_err = m;
   return s;
+}
+
+const void* device_view(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();   // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+cudaError_t ensure_touched_runs(gp_ctx* c) {
+  if (c->ntruns >= 0) return cudaSuccess;
+  // the touched DoFs are the active DoFs outside the zero runs (which are sorted and disjoint)
+  constexpr int32_t RUN_MAX = 1024;
+  const gp::Plan& p = c->plan;
+  std::vector<int2> runs;
+  auto emit = [&](int64_t a, int64_t b) {
+    for (; a < b; a += RUN_MAX) runs.push_back(make_int2((int)a, (int)std::min<int64_t>(RUN_MAX, b - a)));
+  };
+  int64_t pos = 0;
+  for (int64_t r = 0; r < p.num_zero_runs(); ++r) {
+    emit(pos, p.zruns[2 * r]);
+    pos = (int64_t)p.zruns[2 * r] + p.zruns[2 * r + 1];
+  }
+  emit(pos, p.n_active);
+  cudaError_t e = cudaSuccess;
+  if (!runs.empty()) {
+    e = cudaMalloc(&c->d_truns, runs.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_truns, runs.data(), runs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) c->ntruns = (int32_t)runs.size();
+  return e;
 }
 
 size_t brick_scratch_bytes(const gp_ctx* c) {
@@ -72,7 +133,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 }
 
 void free_device(gp_ctx* c) {
-  void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow, c->d_zruns, c->d_tp, c->d_xh, c->d_yh,
+  void* ptrs[] = {c->d_frows, c->d_lwin, c->d_lrow, c->d_zruns, c->d_tp, c->d_xh, c->d_yh, c->d_truns,
                   c->d_bdesc, c->d_bcell, c->d_bccoord, c->d_bface, c->d_rowtab,
                   c->d_pnode, c->d_poff, c->d_pslot, c->d_part};
   for (void* p : ptrs)
@@ -80,6 +141,8 @@ void free_device(gp_ctx* c) {
   c->d_frows = c->d_lwin = c->d_lrow = nullptr;
   c->d_zruns = nullptr;
   c->d_tp = c->d_xh = c->d_yh = nullptr;
+  c->d_truns = nullptr;
+  c->ntruns = -1;
   c->d_bdesc = c->d_bcell = c->d_bccoord = c->d_rowtab = nullptr;
   c->d_pnode = c->d_poff = c->d_pslot = nullptr;
   c->d_bface = nullptr;
@@ -493,19 +556,38 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
   if (!ctx) return fail(nullptr, GP_EINVAL, "null context");
   if (!ctx->on_device) return fail(ctx, GP_EDEVICE, "context was built host-only (device = -1)");
   const int64_t n = ctx->plan.n_active;
+  ctx->host_bytes[0] = ctx->host_bytes[1] = 0;
   if (n == 0) return GP_OK;
   if (!x_host || !y_host) return fail(ctx, GP_EINVAL, "null x or y");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, GP_ECUDA, "cudaSetDevice failed");
   const size_t bytes = (size_t)n * ctx->elem;
   if (!ctx->d_xh) GP_CUDA(ctx, cudaMalloc(&ctx->d_xh, bytes));
-  if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
   cudaStream_t st = (cudaStream_t)stream;
-  GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
+  // a page-locked x is read by a gather kernel on the touched DoFs only (the only entries the
+  // face kernel reads); y goes back by one copy
+  const void* xdev = gpi::device_view(x_host);
+  if (xdev) {
+    GP_CUDA(ctx, gpi::ensure_touched_runs(ctx));
+    GP_CUDA(ctx, gpi::gather_runs(xdev, ctx->d_xh, ctx->d_truns, ctx->ntruns, ctx->elem, st));
+    ctx->host_bytes[0] = ctx->plan.n_touched * ctx->elem;
+  } else {
+    GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
+    ctx->host_bytes[0] = (int64_t)bytes;
+  }
+  if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
   gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st);
   if (s != GP_OK) return s;
   GP_CUDA(ctx, cudaMemcpyAsync(y_host, ctx->d_yh, bytes, cudaMemcpyDeviceToHost, st));
+  ctx->host_bytes[1] = (int64_t)bytes;
   GP_CUDA(ctx, cudaStreamSynchronize(st));
+  return GP_OK;
+}
+
+gp_status gp_apply_host_bytes(const gp_ctx* ctx, int64_t* h2d, int64_t* d2h) {
+  if (!ctx || !h2d || !d2h) return fail(ctx, GP_EINVAL, "null argument");
+  *h2d = ctx->host_bytes[0];
+  *d2h = ctx->host_bytes[1];
   return GP_OK;
 }
 

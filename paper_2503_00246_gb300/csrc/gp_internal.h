@@ -32,6 +32,9 @@ struct gp_ctx {
   bool no_scratch = false;
   void* d_xh = nullptr;          // gp_apply_host staging
   void* d_yh = nullptr;
+  int2* d_truns = nullptr;       // gp_apply_host: runs (c0, len) of the touched DoFs
+  int32_t ntruns = -1;           // -1: not built yet
+  int64_t host_bytes[2] = {0, 0};  // bytes the last gp_apply_host moved host -> device, device -> host
   gp::Tiles tiles{};             // tile shape of the face and lift launches (0: defaults)
   std::string err;
   // tracing: one event triple per traced apply
@@ -69,6 +72,11 @@ gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, vo
 // Slab pipeline of the face + lift path (gp_opts.slabs): at most MAX_SLABS slabs.
 static_assert(gp::SLAB == gp::SLAB_INTS, "the plan's and the launcher's slab records differ");
 constexpr int MAX_SLABS = 64;
+// gp_apply_host: the device address of a page-locked host buffer (nullptr for other memory),
+// the runs of touched DoFs (built on first use), and the copy of those runs of x.
+const void* device_view(const void* host);
+cudaError_t ensure_touched_runs(gp_ctx* c);
+cudaError_t gather_runs(const void* src, void* dst, const int2* runs, int nruns, int elem, cudaStream_t st);
 // Default faces per chunk of the brick kernel (about 256 threads).
 int brick_default_fb(int dim, int k);
 // Bytes of the brick path's partial grids (its scratch) for context c.

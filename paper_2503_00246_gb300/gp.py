@@ -104,6 +104,7 @@ def _load():
         "gp_apply_add": ([P, P, P, P], C.c_int),
         "gp_apply_noalloc": ([P, P, P, P], C.c_int),
         "gp_apply_host": ([P, P, P, P], C.c_int),
+        "gp_apply_host_bytes": ([P, i64p, i64p], C.c_int),
         "gp_apply_batched": ([C.POINTER(P), C.c_int, C.c_int, C.POINTER(P), C.POINTER(P), P], C.c_int),
         "gp_apply_batched_info": ([C.POINTER(P), C.c_int, C.c_int, i64p], C.c_int),
         "gp_kernel_path": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int32), i64p], C.c_int),
@@ -139,7 +140,7 @@ ABI_SYMBOLS = ("gp_setup", "gp_destroy", "gp_num_active_dofs", "gp_num_ghost_fac
                "gp_batch_destroy", "gp_system_create", "gp_system_apply", "gp_system_solve",
                "gp_system_destroy", "gp_partition_info", "gp_partition_slabs", "gp_get_tiles",
                "gp_set_tiles", "gp_autotune", "gp_tiles_record", "gp_tiles_lookup", "gp_system_cells",
-               "gp_apply_batched_info", "gp_kernel_path")
+               "gp_apply_batched_info", "gp_kernel_path", "gp_apply_host_bytes")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -250,6 +251,13 @@ def gp_apply_host(ctx: Context, x: np.ndarray, y: np.ndarray | None = None, stre
         xp, yp = x.data_ptr(), y.data_ptr()
     _check(lib.gp_apply_host(ctx.handle, xp, yp, stream if isinstance(stream, int) else stream.cuda_stream), ctx)
     return y
+
+
+def gp_apply_host_bytes(ctx: Context):
+    """(host -> device, device -> host) bytes the last gp_apply_host of ctx moved."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib.gp_apply_host_bytes(ctx.handle, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
 
 
 def gp_apply_batched(ctxs, nrhs, xs, ys, stream=None):

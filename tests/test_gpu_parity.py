@@ -163,6 +163,35 @@ def test_host_buffers_end_to_end(gplib, cuda):
     assert np.array_equal(y_host, y_dev)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_buffers_page_locked(gplib, cuda, prec):
+    """Page-locked host buffers: the GPU gathers x on the touched DoFs only (y starts as NaN, so
+    every entry must come back); bitwise equal to the device apply and to the copy path of
+    pageable buffers, with the bytes each path moves."""
+    dt = cuda.float32 if prec == 1 else cuda.float64
+    for pr in (W.small_ball(3, 12, 2, seed=9), W.small_ball(2, 30, 3, seed=10)):
+        ctx = gplib.setup_problem(pr, precision=prec)
+        x = W.x_vectors(pr, ctx.n_active)[0]
+        y_dev = _apply(gplib, cuda, ctx, x, prec)
+        xh = cuda.tensor(x, dtype=dt).pin_memory()
+        yh = cuda.full((ctx.n_active,), float("nan"), dtype=dt).pin_memory()
+        gplib.gp_apply_host(ctx, xh, yh)
+        assert np.array_equal(yh.double().numpy(), y_dev)
+        w = xh.element_size()
+        assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_touched * w, ctx.n_active * w)
+        y_pageable = gplib.gp_apply_host(ctx, xh.numpy().copy())
+        assert np.array_equal(y_pageable.astype(np.float64), y_dev)
+        assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_active * w, ctx.n_active * w)
+    # no ghost faces: nothing to gather, y is all zeros
+    pr = W.box_problem(3, 4, 2, all_faces=False)      # every cell inside
+    ctx = gplib.setup_problem(pr, precision=prec)
+    assert ctx.n_faces == 0
+    xh = cuda.ones(ctx.n_active, dtype=dt).pin_memory()
+    yh = cuda.full((ctx.n_active,), float("nan"), dtype=dt).pin_memory()
+    gplib.gp_apply_host(ctx, xh, yh)
+    assert not yh.any().item() and gplib.gp_apply_host_bytes(ctx)[0] == 0
+
+
 def _batched_c(gplib):
     """gp_apply_batched as the exported C symbol (ctypes.CDLL on the library file)."""
     import ctypes
