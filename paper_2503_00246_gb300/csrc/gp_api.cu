@@ -90,6 +90,24 @@ cudaError_t ensure_touched_runs(gp_ctx* c) {
   return e;
 }
 
+cudaError_t ensure_host_pipeline(gp_ctx* c) {
+  if (c->hpipe_built) return cudaSuccess;
+  if (!c->use_brick) {
+    c->hslabs = gp::slab_table(c->plan, HOST_SLABS);
+    c->hbounds = gp::slab_y_bounds(c->plan, c->hslabs);
+  }
+  const size_t ns = c->hslabs.size() / gp::SLAB;
+  cudaError_t e = cudaSuccess;
+  while (e == cudaSuccess && c->hev.size() < ns) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) c->hev.push_back(ev);
+  }
+  if (e == cudaSuccess && ns > 1 && !c->hcopy) e = cudaStreamCreateWithFlags(&c->hcopy, cudaStreamNonBlocking);
+  if (e == cudaSuccess) c->hpipe_built = true;
+  return e;
+}
+
 size_t brick_scratch_bytes(const gp_ctx* c) {
   const gp::Plan& p = c->plan;
   return (size_t)p.num_bricks() * (size_t)p.pgrid * (p.precision == GP_FP32 ? 4 : 8);
@@ -149,6 +167,11 @@ void free_device(gp_ctx* c) {
   c->d_part = nullptr;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
+  for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
+  c->hev.clear();
+  if (c->hcopy) cudaStreamDestroy(c->hcopy);
+  c->hcopy = nullptr;
+  c->hpipe_built = false;
 }
 
 #define GP_CUDA(ctx, call)                                                            \
@@ -162,7 +185,7 @@ void free_device(gp_ctx* c) {
 }  // namespace
 
 gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch, bool trace,
-                      const gp::Tiles* tiles, int which) {
+                      const gp::Tiles* tiles, int which, const SlabRun* run) {
   const gp::Plan& p = c->plan;
   const bool brick = c->use_brick && which == 3;
   if (!scratch && p.num_faces() > 0 && (brick ? (!c->d_part && p.num_plane_nodes() > 0) : !c->d_tp))
@@ -202,8 +225,9 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
   a.ev = ev;
   a.tiles = tiles ? *tiles : c->tiles;
   a.which = which;
-  a.slabs = p.slabs.data();
-  a.nslab = p.num_slabs();
+  a.slabs = run ? run->table : p.slabs.data();
+  a.nslab = run ? run->n : p.num_slabs();
+  a.slab_events = run ? run->events : nullptr;
   if (brick) {
     a.brick = true;
     gp::BrickArgs& ba = a.ba;
@@ -576,10 +600,34 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
     ctx->host_bytes[0] = (int64_t)bytes;
   }
   if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
+  ctx->host_bytes[1] = (int64_t)bytes;
+  if (gpi::device_view(y_host)) {
+    // a page-locked y: the apply runs as a slab pipeline and each slab's finished part of y goes
+    // back on a second stream while the later slabs compute
+    GP_CUDA(ctx, gpi::ensure_host_pipeline(ctx));
+    const int ns = (int)(ctx->hslabs.size() / gp::SLAB);
+    if (ns > 1) {
+      gpi::SlabRun run;
+      run.table = ctx->hslabs.data();
+      run.n = ns;
+      run.events = ctx->hev.data();
+      gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st, nullptr, false, nullptr, 3, &run);
+      if (s != GP_OK) return s;
+      for (int sl = 0; sl < ns; ++sl) {
+        const int64_t lo = ctx->hbounds[sl], hi = ctx->hbounds[sl + 1];
+        GP_CUDA(ctx, cudaStreamWaitEvent(ctx->hcopy, ctx->hev[sl], 0));
+        if (hi > lo)
+          GP_CUDA(ctx, cudaMemcpyAsync((char*)y_host + lo * ctx->elem, (const char*)ctx->d_yh + lo * ctx->elem,
+                                       (size_t)(hi - lo) * ctx->elem, cudaMemcpyDeviceToHost, ctx->hcopy));
+      }
+      GP_CUDA(ctx, cudaStreamSynchronize(ctx->hcopy));
+      GP_CUDA(ctx, cudaStreamSynchronize(st));
+      return GP_OK;
+    }
+  }
   gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st);
   if (s != GP_OK) return s;
   GP_CUDA(ctx, cudaMemcpyAsync(y_host, ctx->d_yh, bytes, cudaMemcpyDeviceToHost, st));
-  ctx->host_bytes[1] = (int64_t)bytes;
   GP_CUDA(ctx, cudaStreamSynchronize(st));
   return GP_OK;
 }

@@ -35,6 +35,13 @@ struct gp_ctx {
   int2* d_truns = nullptr;       // gp_apply_host: runs (c0, len) of the touched DoFs
   int32_t ntruns = -1;           // -1: not built yet
   int64_t host_bytes[2] = {0, 0};  // bytes the last gp_apply_host moved host -> device, device -> host
+  // gp_apply_host with a page-locked y: a slab pipeline whose finished parts of y go back on a
+  // second stream while later slabs compute (built on first use)
+  bool hpipe_built = false;
+  std::vector<int32_t> hslabs;   // slab table (gp::slab_table)
+  std::vector<int64_t> hbounds;  // y chunk of slab s: [hbounds[s], hbounds[s + 1])
+  std::vector<cudaEvent_t> hev;  // one per slab, recorded after its lift
+  cudaStream_t hcopy = nullptr;  // the D2H stream
   gp::Tiles tiles{};             // tile shape of the face and lift launches (0: defaults)
   std::string err;
   // tracing: one event triple per traced apply
@@ -66,8 +73,14 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m);
 // context's face-output buffer when given; `trace` = false never records events.
 // `tiles` overrides the context's tile shape; `which` (bit 0 face, bit 1 lift) drops a
 // kernel (the autotuner times them apart).
+// A slab pipeline for one launch: a slab table (SLAB ints per slab) and an event per slab.
+struct SlabRun {
+  const int32_t* table = nullptr;
+  int n = 0;
+  cudaEvent_t* events = nullptr;
+};
 gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
-                 bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3);
+                 bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3, const SlabRun* run = nullptr);
 
 // Slab pipeline of the face + lift path (gp_opts.slabs): at most MAX_SLABS slabs.
 static_assert(gp::SLAB == gp::SLAB_INTS, "the plan's and the launcher's slab records differ");
@@ -76,6 +89,9 @@ constexpr int MAX_SLABS = 64;
 // the runs of touched DoFs (built on first use), and the copy of those runs of x.
 const void* device_view(const void* host);
 cudaError_t ensure_touched_runs(gp_ctx* c);
+// The host-apply slab pipeline of c (HOST_SLABS slabs; none when the plan has too few owners).
+constexpr int HOST_SLABS = 8;
+cudaError_t ensure_host_pipeline(gp_ctx* c);
 cudaError_t gather_runs(const void* src, void* dst, const int2* runs, int nruns, int elem, cudaStream_t st);
 // Default faces per chunk of the brick kernel (about 256 threads).
 int brick_default_fb(int dim, int k);

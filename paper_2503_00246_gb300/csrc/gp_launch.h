@@ -32,6 +32,8 @@ struct ApplyArgs {
   int which = 3;              // bit 0: face kernel, bit 1: lift kernel (the autotuner times them apart)
   const int32_t* slabs = nullptr;  // host: SLAB ints per slab (see Plan::slabs); nslab > 1: slab pipeline
   int nslab = 0;
+  cudaEvent_t* slab_events = nullptr;  // host, nslab events: recorded after each slab's lift (the
+                                       // face launches then follow them in plain stream order)
   bool brick = false;         // the brick path (brick kernel + plane fixup) instead of face + lift
   BrickArgs ba{};             // brick tables (zero-run fields are filled by the launcher)
   PlaneArgs pa{};             // plane-fixup tables
@@ -193,7 +195,9 @@ cudaError_t launch_pdl(void (*kernel)(P...), int grid, int threads, size_t smem,
 // lift(s) waits for face(s) before it reads W; face(s + 1) starts once every CTA of lift(s) has
 // passed that wait, overlaps lift(s) (it writes other face outputs and reads only x), and waits for
 // lift(s) only before it exits, so that each grid completes after all earlier ones (the last lift
-// completes last).  The first face launch also zero-fills.
+// completes last).  The first face launch also zero-fills.  With slab_events, an event is
+// recorded after every lift (another stream can then take the slab's finished part of y) and
+// each face launch follows it in plain stream order.
 template <int D, int K, class A>
 cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, const Tiles& t, cudaStream_t st) {
   using S = Shape<D, K>;
@@ -208,7 +212,7 @@ cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, co
     fa.zruns = Ar.zruns;
     fa.nzruns = s == 0 ? Ar.nzruns : 0;
     fa.nzblocks = (fa.nzruns + ZGROUP - 1) / ZGROUP;
-    fa.tail_wait = s > 0;
+    fa.tail_wait = s > 0 && !Ar.slab_events;
     int32_t nb = fa.nzblocks;
     for (int a = 0; a < 4; ++a) {
       const bool in = a < D;
@@ -223,11 +227,12 @@ cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, co
     for (int a = D; a < 4; ++a) fa.bstart[a] = nb;
     if (nb > 0) {
       const cudaError_t e =
-          s == 0 ? (face_kernel<D, K, A><<<nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>(
-                        (const IO*)Ar.x, (V*)Ar.tp, (IO*)Ar.y, fa, t.fb, c),
-                    cudaGetLastError())
-                 : launch_pdl(face_kernel<D, K, A>, nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st, (const IO*)Ar.x,
-                              (V*)Ar.tp, (IO*)Ar.y, fa, (int)t.fb, c);
+          (s == 0 || Ar.slab_events)
+              ? (face_kernel<D, K, A><<<nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st>>>((const IO*)Ar.x, (V*)Ar.tp,
+                                                                                     (IO*)Ar.y, fa, t.fb, c),
+                 cudaGetLastError())
+              : launch_pdl(face_kernel<D, K, A>, nb, t.fb * S::L, face_smem<D, K, V>(t.fb), st, (const IO*)Ar.x,
+                           (V*)Ar.tp, (IO*)Ar.y, fa, (int)t.fb, c);
       if (e != cudaSuccess) return e;
     }
     LiftArgs la = Ar.la;
@@ -236,8 +241,18 @@ cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, co
     la.nlift = sl[1] - sl[0];
     const int32_t nlb = (la.nlift + t.lcb - 1) / t.lcb;
     if (nlb > 0) {
-      const cudaError_t e = launch_pdl(lift_kernel<D, K, A>, nlb, t.lnt, lift_smem<D, K>(t.lcb), st, (const V*)Ar.tp,
-                                       (IO*)Ar.y, Ar.add, la, (int)t.lcb);
+      // programmatic dependent of this slab's face launch (a plain launch after an event)
+      const cudaError_t e =
+          (nb > 0 || !Ar.slab_events)
+              ? launch_pdl(lift_kernel<D, K, A>, nlb, t.lnt, lift_smem<D, K>(t.lcb), st, (const V*)Ar.tp, (IO*)Ar.y,
+                           Ar.add, la, (int)t.lcb)
+              : (lift_kernel<D, K, A><<<nlb, t.lnt, lift_smem<D, K>(t.lcb), st>>>((const V*)Ar.tp, (IO*)Ar.y, Ar.add, la,
+                                                                                 t.lcb),
+                 cudaGetLastError());
+      if (e != cudaSuccess) return e;
+    }
+    if (Ar.slab_events) {
+      const cudaError_t e = cudaEventRecord(Ar.slab_events[s], st);
       if (e != cudaSuccess) return e;
     }
   }

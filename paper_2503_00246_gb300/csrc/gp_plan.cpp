@@ -517,10 +517,32 @@ static bool classify_sampled(const Plan& p, const gp_levelset* ls, int n, double
 
 // ----------------------------------------------------------- numbering --
 
-void build_slabs(Plan& p, int nslab) {
-  p.slabs.clear();
+void build_slabs(Plan& p, int nslab) { p.slabs = slab_table(p, nslab); }
+
+std::vector<int64_t> slab_y_bounds(const Plan& p, const std::vector<int32_t>& table) {
+  const int ns = (int)(table.size() / SLAB);
+  const int KR = p.num_lift_cells() > 0 ? (int)(p.lrow.size() / p.num_lift_cells()) : 0;
+  std::vector<int64_t> b(ns + 1, 0);
+  b[ns] = p.n_active;
+  // b[s] = the smallest compact index a lift owner of slab s or later writes (each of its rows
+  // writes base .. base + k - 1), so every index below it is final once slab s - 1 is lifted
+  int64_t lo = p.n_active;
+  for (int s = ns - 1; s >= 1; --s) {
+    for (int64_t o = table[(size_t)s * SLAB]; o < table[(size_t)s * SLAB + 1]; ++o)
+      for (int r = 0; r < KR; ++r) {
+        const int32_t base = p.lrow[(size_t)o * KR + r];
+        if (base >= 0) lo = std::min<int64_t>(lo, base);
+      }
+    b[s] = lo;
+  }
+  for (int s = 1; s <= ns; ++s) b[s] = std::max(b[s], b[s - 1]);
+  return b;
+}
+
+std::vector<int32_t> slab_table(const Plan& p, int nslab) {
+  std::vector<int32_t> table;
   const int64_t nlift = p.num_lift_cells(), ngroup = (nlift + SLAB_GROUP - 1) / SLAB_GROUP;
-  if (nslab <= 1 || ngroup < 2 || p.num_faces() == 0) return;
+  if (nslab <= 1 || ngroup < 2 || p.num_faces() == 0) return table;
   nslab = (int)std::min<int64_t>(nslab, ngroup);
   const int d = p.dim, nw = p.lwin_width / d;
   int32_t done[3] = {p.fstart[0], p.fstart[1], p.fstart[2]};   // faces of earlier slabs: [fstart, done)
@@ -541,8 +563,9 @@ void build_slabs(Plan& p, int nslab) {
       sl[3 + 2 * a] = end;
       done[a] = end;
     }
-    p.slabs.insert(p.slabs.end(), sl, sl + SLAB);
+    table.insert(table.end(), sl, sl + SLAB);
   }
+  return table;
 }
 
 int64_t Plan::compact(int X, int64_t row) const {

@@ -155,7 +155,11 @@ bool build_bricks(Plan& p, int vbytes, int sbytes, size_t extra, size_t smem_bud
 // lexicographic order of their lower cells, as the owners do, so each is an id range).  The last
 // range also takes the remaining faces.  Fills slabs; nslab <= 1, or fewer than two ranges: empty.
 constexpr int SLAB_GROUP = 256;
-void build_slabs(Plan& p, int nslab);
+std::vector<int32_t> slab_table(const Plan& p, int nslab);
+void build_slabs(Plan& p, int nslab);   // p.slabs = slab_table(p, nslab)
+// For a slab table of ns slabs: ns + 1 compact indices b, b[0] = 0, b[ns] = n_active, such that
+// the entries [b[s], b[s + 1]) of y are final once slabs 0..s are lifted (and the zero fill done).
+std::vector<int64_t> slab_y_bounds(const Plan& p, const std::vector<int32_t>& table);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`

@@ -165,11 +165,12 @@ def test_host_buffers_end_to_end(gplib, cuda):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_host_buffers_page_locked(gplib, cuda, prec):
-    """Page-locked host buffers: the GPU gathers x on the touched DoFs only (y starts as NaN, so
+    """Page-locked host buffers: the GPU gathers x on the touched DoFs only, and y comes back in
+    slab chunks while later slabs compute (the third problem has 8 slabs; y starts as NaN, so
     every entry must come back); bitwise equal to the device apply and to the copy path of
     pageable buffers, with the bytes each path moves."""
     dt = cuda.float32 if prec == 1 else cuda.float64
-    for pr in (W.small_ball(3, 12, 2, seed=9), W.small_ball(2, 30, 3, seed=10)):
+    for pr in (W.small_ball(3, 12, 2, seed=9), W.small_ball(2, 30, 3, seed=10), W.small_ball(3, 24, 3, seed=12)):
         ctx = gplib.setup_problem(pr, precision=prec)
         x = W.x_vectors(pr, ctx.n_active)[0]
         y_dev = _apply(gplib, cuda, ctx, x, prec)
@@ -179,6 +180,9 @@ def test_host_buffers_page_locked(gplib, cuda, prec):
         assert np.array_equal(yh.double().numpy(), y_dev)
         w = xh.element_size()
         assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_touched * w, ctx.n_active * w)
+        yh.fill_(float("nan"))
+        gplib.gp_apply_host(ctx, xh, yh)                   # again: the pipeline's second use
+        assert np.array_equal(yh.double().numpy(), y_dev)
         y_pageable = gplib.gp_apply_host(ctx, xh.numpy().copy())
         assert np.array_equal(y_pageable.astype(np.float64), y_dev)
         assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_active * w, ctx.n_active * w)
