@@ -86,24 +86,44 @@ cudaError_t ensure_touched_runs(gp_ctx* c) {
     e = cudaMalloc(&c->d_truns, runs.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_truns, runs.data(), runs.size() * sizeof(int2), cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess) c->ntruns = (int32_t)runs.size();
+  if (e == cudaSuccess) {
+    c->ntruns = (int32_t)runs.size();
+    c->htruns.swap(runs);
+  }
   return e;
 }
 
 cudaError_t ensure_host_pipeline(gp_ctx* c) {
   if (c->hpipe_built) return cudaSuccess;
+  cudaError_t e = ensure_touched_runs(c);
+  if (e != cudaSuccess) return e;
   if (!c->use_brick) {
     c->hslabs = gp::slab_table(c->plan, HOST_SLABS);
     c->hbounds = gp::slab_y_bounds(c->plan, c->hslabs);
+    // the touched runs slab s gathers: those that start below the x its face launch reads and
+    // were not gathered for an earlier slab (the last slab takes the rest)
+    const std::vector<int64_t> xb = gp::slab_x_bounds(c->plan, c->hslabs);
+    const int ns = (int)xb.size();
+    c->hxrun.assign(ns + 1, 0);
+    int32_t r = 0;
+    for (int s = 0; s < ns; ++s) {
+      while (r < c->ntruns && (s == ns - 1 || c->htruns[r].x < xb[s])) ++r;
+      c->hxrun[s + 1] = r;
+    }
   }
   const size_t ns = c->hslabs.size() / gp::SLAB;
-  cudaError_t e = cudaSuccess;
   while (e == cudaSuccess && c->hev.size() < ns) {
     cudaEvent_t ev;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) c->hev.push_back(ev);
   }
+  while (e == cudaSuccess && c->hgev.size() < ns) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) c->hgev.push_back(ev);
+  }
   if (e == cudaSuccess && ns > 1 && !c->hcopy) e = cudaStreamCreateWithFlags(&c->hcopy, cudaStreamNonBlocking);
+  if (e == cudaSuccess && ns > 1 && !c->hin) e = cudaStreamCreateWithFlags(&c->hin, cudaStreamNonBlocking);
   if (e == cudaSuccess) c->hpipe_built = true;
   return e;
 }
@@ -169,8 +189,11 @@ void free_device(gp_ctx* c) {
   c->ev.clear();
   for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
   c->hev.clear();
+  for (cudaEvent_t e : c->hgev) cudaEventDestroy(e);
+  c->hgev.clear();
   if (c->hcopy) cudaStreamDestroy(c->hcopy);
-  c->hcopy = nullptr;
+  if (c->hin) cudaStreamDestroy(c->hin);
+  c->hcopy = c->hin = nullptr;
   c->hpipe_built = false;
 }
 
@@ -228,6 +251,7 @@ gp_status gpi::launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t s
   a.slabs = run ? run->table : p.slabs.data();
   a.nslab = run ? run->n : p.num_slabs();
   a.slab_events = run ? run->events : nullptr;
+  a.slab_inputs = run ? run->inputs : nullptr;
   if (brick) {
     a.brick = true;
     gp::BrickArgs& ba = a.ba;
@@ -588,22 +612,21 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
   const size_t bytes = (size_t)n * ctx->elem;
   if (!ctx->d_xh) GP_CUDA(ctx, cudaMalloc(&ctx->d_xh, bytes));
   cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
+  ctx->host_bytes[1] = (int64_t)bytes;
   // a page-locked x is read by a gather kernel on the touched DoFs only (the only entries the
-  // face kernel reads); y goes back by one copy
+  // face kernel reads); other memory is copied whole
   const void* xdev = gpi::device_view(x_host);
   if (xdev) {
     GP_CUDA(ctx, gpi::ensure_touched_runs(ctx));
-    GP_CUDA(ctx, gpi::gather_runs(xdev, ctx->d_xh, ctx->d_truns, ctx->ntruns, ctx->elem, st));
     ctx->host_bytes[0] = ctx->plan.n_touched * ctx->elem;
   } else {
-    GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
     ctx->host_bytes[0] = (int64_t)bytes;
   }
-  if (!ctx->d_yh) GP_CUDA(ctx, cudaMalloc(&ctx->d_yh, bytes));
-  ctx->host_bytes[1] = (int64_t)bytes;
   if (gpi::device_view(y_host)) {
-    // a page-locked y: the apply runs as a slab pipeline and each slab's finished part of y goes
-    // back on a second stream while the later slabs compute
+    // a page-locked y: the apply runs as a slab pipeline; each slab's part of x is gathered on
+    // one stream before its face launch, and each slab's finished part of y goes back on another
+    // while the later slabs compute
     GP_CUDA(ctx, gpi::ensure_host_pipeline(ctx));
     const int ns = (int)(ctx->hslabs.size() / gp::SLAB);
     if (ns > 1) {
@@ -611,6 +634,16 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
       run.table = ctx->hslabs.data();
       run.n = ns;
       run.events = ctx->hev.data();
+      if (xdev) {
+        for (int sl = 0; sl < ns; ++sl) {
+          const int32_t r0 = ctx->hxrun[sl], r1 = ctx->hxrun[sl + 1];
+          GP_CUDA(ctx, gpi::gather_runs(xdev, ctx->d_xh, ctx->d_truns + r0, r1 - r0, ctx->elem, ctx->hin));
+          GP_CUDA(ctx, cudaEventRecord(ctx->hgev[sl], ctx->hin));
+        }
+        run.inputs = ctx->hgev.data();
+      } else {
+        GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
+      }
       gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st, nullptr, false, nullptr, 3, &run);
       if (s != GP_OK) return s;
       for (int sl = 0; sl < ns; ++sl) {
@@ -621,10 +654,13 @@ gp_status gp_apply_host(gp_ctx* ctx, const void* x_host, void* y_host, void* str
                                        (size_t)(hi - lo) * ctx->elem, cudaMemcpyDeviceToHost, ctx->hcopy));
       }
       GP_CUDA(ctx, cudaStreamSynchronize(ctx->hcopy));
+      GP_CUDA(ctx, cudaStreamSynchronize(ctx->hin));
       GP_CUDA(ctx, cudaStreamSynchronize(st));
       return GP_OK;
     }
   }
+  if (xdev) GP_CUDA(ctx, gpi::gather_runs(xdev, ctx->d_xh, ctx->d_truns, ctx->ntruns, ctx->elem, st));
+  else GP_CUDA(ctx, cudaMemcpyAsync(ctx->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
   gp_status s = launch(ctx, ctx->d_xh, ctx->d_yh, 0, st);
   if (s != GP_OK) return s;
   GP_CUDA(ctx, cudaMemcpyAsync(y_host, ctx->d_yh, bytes, cudaMemcpyDeviceToHost, st));

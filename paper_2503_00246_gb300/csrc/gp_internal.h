@@ -42,6 +42,10 @@ struct gp_ctx {
   std::vector<int64_t> hbounds;  // y chunk of slab s: [hbounds[s], hbounds[s + 1])
   std::vector<cudaEvent_t> hev;  // one per slab, recorded after its lift
   cudaStream_t hcopy = nullptr;  // the D2H stream
+  std::vector<int2> htruns;      // host copy of d_truns
+  std::vector<int32_t> hxrun;    // touched runs gathered for slab s: [hxrun[s], hxrun[s + 1])
+  std::vector<cudaEvent_t> hgev; // one per slab, recorded after its gather
+  cudaStream_t hin = nullptr;    // the gather stream
   gp::Tiles tiles{};             // tile shape of the face and lift launches (0: defaults)
   std::string err;
   // tracing: one event triple per traced apply
@@ -77,7 +81,8 @@ gp_status fail(const gp_ctx* c, gp_status s, const std::string& m);
 struct SlabRun {
   const int32_t* table = nullptr;
   int n = 0;
-  cudaEvent_t* events = nullptr;
+  cudaEvent_t* events = nullptr;   // recorded after each slab's lift
+  cudaEvent_t* inputs = nullptr;   // waited for before each slab's face launch (or nullptr)
 };
 gp_status launch(gp_ctx* c, const void* x, void* y, int add, cudaStream_t st, void* scratch = nullptr,
                  bool trace = true, const gp::Tiles* tiles = nullptr, int which = 3, const SlabRun* run = nullptr);

@@ -34,6 +34,8 @@ struct ApplyArgs {
   int nslab = 0;
   cudaEvent_t* slab_events = nullptr;  // host, nslab events: recorded after each slab's lift (the
                                        // face launches then follow them in plain stream order)
+  cudaEvent_t* slab_inputs = nullptr;  // host, nslab events (with slab_events): the face launch of
+                                       // slab s waits for slab_inputs[s] (its part of x is in place)
   bool brick = false;         // the brick path (brick kernel + plane fixup) instead of face + lift
   BrickArgs ba{};             // brick tables (zero-run fields are filled by the launcher)
   PlaneArgs pa{};             // plane-fixup tables
@@ -225,6 +227,10 @@ cudaError_t run_slabs(const ApplyArgs& Ar, const Consts<typename A::V, K>& c, co
       nb += (fa.fend[a] - fa.fstart[a] + t.fb - 1) / t.fb;
     }
     for (int a = D; a < 4; ++a) fa.bstart[a] = nb;
+    if (Ar.slab_inputs) {
+      const cudaError_t e = cudaStreamWaitEvent(st, Ar.slab_inputs[s], 0);
+      if (e != cudaSuccess) return e;
+    }
     if (nb > 0) {
       const cudaError_t e =
           (s == 0 || Ar.slab_events)

@@ -539,6 +539,25 @@ std::vector<int64_t> slab_y_bounds(const Plan& p, const std::vector<int32_t>& ta
   return b;
 }
 
+std::vector<int64_t> slab_x_bounds(const Plan& p, const std::vector<int32_t>& table) {
+  const int ns = (int)(table.size() / SLAB);
+  const int k = p.k, d = p.dim, L = p.L, NN = 2 * k + 1, K1 = k + 1;
+  const int R1 = d == 3 ? NN * K1 : NN;
+  std::vector<int64_t> b(ns, 0);
+  int64_t hi = 0;
+  for (int s = 0; s < ns; ++s) {
+    for (int a = 0; a < d; ++a) {
+      const int rows = a == 0 ? L : R1, span = a == 0 ? NN : K1;
+      for (int64_t f = table[(size_t)s * SLAB + 2 + 2 * a]; f < table[(size_t)s * SLAB + 3 + 2 * a]; ++f) {
+        const int32_t* r = &p.frows[p.rbase[a] + (f - p.fstart[a]) * rows];
+        for (int i = 0; i < rows; ++i) hi = std::max<int64_t>(hi, (int64_t)r[i] + span);
+      }
+    }
+    b[s] = hi;
+  }
+  return b;
+}
+
 std::vector<int32_t> slab_table(const Plan& p, int nslab) {
   std::vector<int32_t> table;
   const int64_t nlift = p.num_lift_cells(), ngroup = (nlift + SLAB_GROUP - 1) / SLAB_GROUP;

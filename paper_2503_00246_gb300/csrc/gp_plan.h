@@ -160,6 +160,9 @@ void build_slabs(Plan& p, int nslab);   // p.slabs = slab_table(p, nslab)
 // For a slab table of ns slabs: ns + 1 compact indices b, b[0] = 0, b[ns] = n_active, such that
 // the entries [b[s], b[s + 1]) of y are final once slabs 0..s are lifted (and the zero fill done).
 std::vector<int64_t> slab_y_bounds(const Plan& p, const std::vector<int32_t>& table);
+// For a slab table of ns slabs: ns compact indices b, b[s] = one past the largest index of x the
+// face launches of slabs 0..s read.
+std::vector<int64_t> slab_x_bounds(const Plan& p, const std::vector<int32_t>& table);
 // Builds crow, cwin and corow (the tables of the mass + stiffness operator).
 void build_cell_table(Plan& p);
 // For each owner cell of `cells` (same mesh), its index in the lift owner list of `faces`

@@ -196,6 +196,24 @@ def test_host_buffers_page_locked(gplib, cuda, prec):
     assert not yh.any().item() and gplib.gp_apply_host_bytes(ctx)[0] == 0
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_buffers_full_size_gyroid(gplib, cuda, prec):
+    """The 128^3 gyroid at k = 4 (the end-to-end workload of bench.py): the pipelined host apply
+    equals the device apply bit for bit."""
+    pr = W.gyroid_3d(k=4, n=128)
+    ctx = gplib.setup_problem(pr, precision=prec)
+    dt = cuda.float32 if prec == 1 else cuda.float64
+    x = W.x_vectors(pr, ctx.n_active)[0]
+    xd = cuda.tensor(x, dtype=dt, device="cuda")
+    yd = cuda.empty_like(xd)
+    gplib.gp_apply(ctx, xd, yd)
+    xh = xd.cpu().pin_memory()
+    yh = cuda.full((ctx.n_active,), float("nan"), dtype=dt).pin_memory()
+    for _ in range(2):
+        gplib.gp_apply_host(ctx, xh, yh)
+        assert cuda.equal(yh, yd.cpu())
+
+
 def _batched_c(gplib):
     """gp_apply_batched as the exported C symbol (ctypes.CDLL on the library file)."""
     import ctypes
