@@ -312,7 +312,7 @@ gp_status gp_kernel_path(const gp_ctx* ctx, int* path, int32_t* bdim, int64_t* c
  * pin_memory) is read by a gather kernel on the DoFs some face patch touches only (the only
  * entries the face kernel reads); other host memory is copied whole.  y is computed in a device
  * buffer owned by the context; a page-locked y comes back in chunks on a second stream while the
- * apply runs as a pipeline of up to 8 slabs (each chunk as soon as the slabs that write it are
+ * apply runs as a pipeline of up to 16 slabs (8 in FP32; each chunk as soon as the slabs that write it are
  * done; x is then gathered slab by slab on a third stream, each slab's face launch waiting for
  * its part), any other y in one copy at the end.  The device buffers, streams and events belong
  * to ctx: calls on one context must not overlap. */

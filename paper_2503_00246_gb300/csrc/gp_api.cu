@@ -98,7 +98,7 @@ cudaError_t ensure_host_pipeline(gp_ctx* c) {
   cudaError_t e = ensure_touched_runs(c);
   if (e != cudaSuccess) return e;
   if (!c->use_brick) {
-    c->hslabs = gp::slab_table(c->plan, HOST_SLABS);
+    c->hslabs = gp::slab_table(c->plan, host_slabs(c->plan.precision));
     c->hbounds = gp::slab_y_bounds(c->plan, c->hslabs);
     // the touched runs slab s gathers: those that start below the x its face launch reads and
     // were not gathered for an earlier slab (the last slab takes the rest)

@@ -94,8 +94,10 @@ constexpr int MAX_SLABS = 64;
 // the runs of touched DoFs (built on first use), and the copy of those runs of x.
 const void* device_view(const void* host);
 cudaError_t ensure_touched_runs(gp_ctx* c);
-// The host-apply slab pipeline of c (HOST_SLABS slabs; none when the plan has too few owners).
-constexpr int HOST_SLABS = 8;
+// The host-apply slab pipeline of c (host_slabs slabs; none when the plan has too few owners):
+// 8 for FP32, 16 for the FP64 forms (measured best on the 128^3 gyroid at k = 4: FP32 35.7 /
+// 38.3 / 37.6 GDoF/s end to end with 16 / 8 / 4 slabs, FP64 19.7 / 19.1 / 17.4).
+inline int host_slabs(int precision) { return precision == GP_FP32 ? 8 : 16; }
 cudaError_t ensure_host_pipeline(gp_ctx* c);
 cudaError_t gather_runs(const void* src, void* dst, const int2* runs, int nruns, int elem, cudaStream_t st);
 // Default faces per chunk of the brick kernel (about 256 threads).
