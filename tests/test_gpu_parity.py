@@ -186,6 +186,16 @@ def test_host_buffers_page_locked(gplib, cuda, prec):
         y_pageable = gplib.gp_apply_host(ctx, xh.numpy().copy())
         assert np.array_equal(y_pageable.astype(np.float64), y_dev)
         assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_active * w, ctx.n_active * w)
+        # mixed: page-locked x with pageable y, and pageable x with page-locked y
+        yp = cuda.full((ctx.n_active,), float("nan"), dtype=dt)
+        gplib.gp_apply_host(ctx, xh, yp)
+        assert np.array_equal(yp.double().numpy(), y_dev)
+        assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_touched * w, ctx.n_active * w)
+        xp = cuda.tensor(x, dtype=dt)                     # pageable
+        yh.fill_(float("nan"))
+        gplib.gp_apply_host(ctx, xp, yh)
+        assert np.array_equal(yh.double().numpy(), y_dev)
+        assert gplib.gp_apply_host_bytes(ctx) == (ctx.n_active * w, ctx.n_active * w)
     # no ghost faces: nothing to gather, y is all zeros
     pr = W.box_problem(3, 4, 2, all_faces=False)      # every cell inside
     ctx = gplib.setup_problem(pr, precision=prec)
