@@ -146,6 +146,27 @@ def test_no_ghost_faces(gplib, cuda):
     assert np.array_equal(_apply(gplib, cuda, ctx, x, 0, add_to=y0), y0)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_empty_domain(gplib, cuda, prec):
+    """A level set negative everywhere: no active DoF, no face.  Every apply is a no-op that
+    returns GP_OK (device, add, no-alloc, host buffers), and so is the autotuner."""
+    pr = W.box_problem(3, 4, 2, all_faces=False)
+    pr.ls_value = -1.0
+    ctx = gplib.setup_problem(pr, precision=prec)
+    assert ctx.n_active == 0 and ctx.n_faces == 0
+    dt = cuda.float32 if prec == 1 else cuda.float64
+    xd = cuda.zeros(1, dtype=dt, device="cuda")
+    yd = cuda.zeros(1, dtype=dt, device="cuda")
+    for fn in (gplib.lib.gp_apply, gplib.lib.gp_apply_add, gplib.lib.gp_apply_noalloc):
+        assert fn(ctx.handle, xd.data_ptr(), yd.data_ptr(), None) == gplib.GP_OK
+    xh = cuda.zeros(1, dtype=dt).pin_memory()
+    yh = cuda.zeros(1, dtype=dt).pin_memory()
+    assert gplib.lib.gp_apply_host(ctx.handle, xh.data_ptr(), yh.data_ptr(), None) == gplib.GP_OK
+    assert gplib.gp_apply_host_bytes(ctx) == (0, 0)
+    gplib.gp_autotune(ctx, 1)
+    cuda.cuda.synchronize()
+
+
 def test_single_face_mesh(gplib, cuda):
     pr = W.box_problem(3, 2, 4, all_faces=True)        # 2x2x2 cells, 12 faces
     o = Oracle(pr)
